@@ -1,0 +1,111 @@
+/*
+ * polyrx oracle: plain FP64 CPU restatement of de Buyl & Nies, "A parallel
+ * algorithm for step- and chain-growth polymerization in Molecular Dynamics"
+ * (arXiv:1409.7498).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check of the
+ * package entry file and the CPU-baseline leg of the benchmark may load this
+ * library.  The CUDA path never links, calls or includes anything from here,
+ * and nothing here includes anything from the CUDA path.
+ *
+ * All arrays are indexed by particle id 0..n-1.  Positions are absolute
+ * coordinates in [0, L) on a periodic orthorhombic box.
+ */
+#ifndef POLYRX_ORACLE_H
+#define POLYRX_ORACLE_H
+#include <stdint.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ENOMEM (-2)
+#define ORC_ECAPACITY (-3)
+#define ORC_EOVERSTRETCH (-4)
+#define ORC_ENONFINITE (-5)
+
+/* Bond styles. FENE: Sec. II.C (Kremer-Grest bond).  Mirror LJ: Sec. II.C,
+ * Eq. 17 (the paper's created-bond potential). */
+#define ORC_BOND_FENE 0
+#define ORC_BOND_MIRROR_LJ 1
+
+/* Counter tags of the keyed Philox draws (fourth counter word, low byte). */
+#define ORC_TAG_THERMO 1u
+#define ORC_TAG_ACCEPT 2u
+#define ORC_TAG_SEL_A 3u
+#define ORC_TAG_SEL_T 4u
+
+typedef struct {
+  double L[3];        /* box edges */
+  double dt;          /* time step */
+  double kT;          /* thermostat temperature */
+  double gamma;       /* Langevin friction (0 = plain velocity Verlet) */
+  double mass;        /* particle mass (all equal, Sec. II.C) */
+  double eps, sigma;  /* WCA parameters, Eq. 15 */
+  double fene_k;      /* FENE spring constant k_F */
+  double fene_r0;     /* FENE maximum extension R_0 */
+  double force_cap;   /* > 0: cap on the WCA pair-force magnitude (warm-up) */
+  uint64_t seed;      /* Philox key */
+} orc_md_params;
+
+typedef struct {
+  uint32_t mask_A;    /* bit t set: type t may act as the active A */
+  uint32_t mask_T;    /* bit t set: type t may act as the target T */
+  int32_t a_lo, a_hi; /* state window of A (inclusive) */
+  int32_t t_lo, t_hi; /* state window of T (inclusive) */
+  int32_t dA, dT;     /* state increments delta_A, delta_T, Eq. 2 */
+  double k;           /* intrinsic rate */
+  int64_t theta;      /* reaction interval Theta in MD steps */
+  double r_react;     /* reaction cutoff */
+  int32_t bond_style; /* style of the created bonds */
+  uint8_t max_valence[8]; /* per type: bonds a particle may hold */
+} orc_rx_params;
+
+typedef struct {
+  int64_t n;          /* particles */
+  int32_t cap;        /* adjacency capacity per particle */
+  int32_t pad_;
+  double* x;          /* [n][3] positions */
+  double* v;          /* [n][3] velocities (half-step, see orc_step) */
+  uint8_t* type;      /* [n] */
+  int8_t* state;      /* [n] */
+  uint8_t* nadj;      /* [n] bonds held */
+  uint32_t* adj;      /* [n][cap] partner ids */
+  uint8_t* adj_style; /* [n][cap] bond style of each entry */
+  int64_t nb;         /* bonds in the list */
+  int64_t nb_cap;     /* capacity of the bond list */
+  uint32_t* bond_a;   /* [nb_cap] id of A (or first particle of an initial bond) */
+  uint32_t* bond_t;   /* [nb_cap] id of T */
+  int64_t* bond_step; /* [nb_cap] step the bond formed (0: initial) */
+  uint8_t* bond_style;/* [nb_cap] */
+  int64_t step;       /* completed MD steps */
+} orc_system;
+
+typedef struct {
+  int64_t candidates;  /* Table I step 1 */
+  int64_t retained;    /* step 2 */
+  int64_t a_winners;   /* step 5 */
+  int64_t formed;      /* step 7 / 9 */
+} orc_rx_trace;
+
+typedef struct {
+  int64_t counts[8][16]; /* particles per (type, state) for state in 0..15 */
+  int64_t bonds;
+  double ke_half;        /* kinetic energy of the stored (half-step) velocities */
+  double epot;           /* WCA + bond potential energy */
+  double momentum[3];
+} orc_obs;
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_u53(uint32_t hi, uint32_t lo);
+double orc_u24(uint32_t w);
+
+int orc_forces(const orc_system* s, const orc_md_params* md, int use_cells,
+               double* f, double* epot);
+int orc_step(orc_system* s, const orc_md_params* md, int use_cells, double* ke_full);
+int orc_check_reaction(const orc_rx_params* rx);
+int orc_react(orc_system* s, const orc_md_params* md, const orc_rx_params* rx,
+              int use_cells, int64_t step, orc_rx_trace* trace);
+int orc_observables(const orc_system* s, const orc_md_params* md, orc_obs* o);
+int orc_run(orc_system* s, const orc_md_params* md, const orc_rx_params* rx,
+            int64_t nsteps, int use_cells, orc_obs* obs_per_reaction, int64_t obs_cap);
+
+#endif

@@ -1,0 +1,169 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the bench.
+
+This module holds no arithmetic of the method: it only places particles,
+draws thermal velocities and assigns types and initial states.  Both the
+oracle and the CUDA path receive its arrays unchanged.
+
+Recipe (stated once here, used everywhere):
+  * box: cubic, edge L = (N / rho)^(1/3) at rho = 0.85;
+  * positions: the N particles occupy a random subset of the sites of a
+    simple cubic lattice of m = ceil(N^(1/3)) sites per edge (spacing L/m,
+    about 1.03-1.05 sigma at rho = 0.85), each displaced by a uniform jitter
+    of +-jitter/2 lattice spacings, so no two particles start closer than
+    about 0.95 sigma and no capped warm-up is needed;
+  * velocities: Maxwell-Boltzmann at kT with the centre-of-mass velocity
+    removed;
+  * types: 0 = B (difunctional monomer / chain monomer M), 1 = A
+    (crosslinker of functionality f, or chain initiator), assigned to a
+    random permutation of the particles.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+TYPE_B = 0
+TYPE_A = 1
+DENSITY = 0.85
+BASE_SEED = 14097498
+
+
+@dataclass
+class Inputs:
+    """One system's initial data, by particle id."""
+    L: float
+    x: np.ndarray       # (n, 3) float64
+    v: np.ndarray       # (n, 3) float64
+    type: np.ndarray    # (n,) uint8
+    state: np.ndarray   # (n,) int8
+    scheme: str         # "step" or "chain"
+    f: int              # crosslinker functionality (step growth), 1 for chain growth
+    seed: int
+
+    @property
+    def n(self) -> int:
+        return len(self.type)
+
+
+def box_edge(n: int, rho: float = DENSITY) -> float:
+    return (n / rho) ** (1.0 / 3.0)
+
+
+def lattice_positions(n: int, L: float, rng: np.random.Generator, jitter: float = 0.05):
+    if n == 0:
+        return np.zeros((0, 3))
+    m = max(1, math.ceil(round(n ** (1.0 / 3.0), 9)))
+    while m ** 3 < n:
+        m += 1
+    a = L / m
+    sites = rng.choice(m ** 3, size=n, replace=False)
+    ijk = np.stack([sites % m, (sites // m) % m, sites // (m * m)], axis=1).astype(np.float64)
+    pos = (ijk + 0.5 + jitter * (rng.random((n, 3)) - 0.5)) * a
+    pos = np.where(pos >= L, pos - L, pos)
+    pos = np.where(pos < 0.0, pos + L, pos)
+    return np.ascontiguousarray(pos)
+
+
+def uniform_positions(n: int, L: float, rng: np.random.Generator):
+    """Uniform random placement (the paper's first protocol step, App. A);
+    such inputs need the capped-force warm-up before production."""
+    return np.ascontiguousarray(rng.random((n, 3)) * L)
+
+
+def maxwell_velocities(n: int, kT: float, mass: float, rng: np.random.Generator):
+    if n == 0:
+        return np.zeros((0, 3))
+    v = rng.standard_normal((n, 3)) * math.sqrt(kT / mass)
+    v -= v.mean(axis=0, keepdims=True)
+    return np.ascontiguousarray(v)
+
+
+def step_growth(n_B: int, n_A: int, f: int, seed: int, rho: float = DENSITY, kT: float = 1.0,
+                jitter: float = 0.05) -> Inputs:
+    """Difunctional B monomers (state 0) and A crosslinkers of functionality
+    f (state f)."""
+    rng = np.random.default_rng(seed)
+    n = n_B + n_A
+    L = box_edge(n, rho)
+    x = lattice_positions(n, L, rng, jitter)
+    v = maxwell_velocities(n, kT, 1.0, rng)
+    typ = np.full(n, TYPE_B, np.uint8)
+    st = np.zeros(n, np.int8)
+    a_ids = rng.permutation(n)[:n_A]
+    typ[a_ids] = TYPE_A
+    st[a_ids] = f
+    return Inputs(L, x, v, typ, st, "step", f, seed)
+
+
+def step_growth_sites(n_total: int, f: int, seed: int, **kw) -> Inputs:
+    """N beads at a 4:1 B:A reactive-site ratio: 2 n_B = 4 f n_A, so
+    n_A = round(N / (1 + 2 f))."""
+    n_A = int(round(n_total / (1 + 2 * f)))
+    return step_growth(n_total - n_A, n_A, f, seed, **kw)
+
+
+def chain_growth(n_M: int, n_init: int, seed: int, rho: float = DENSITY, kT: float = 1.0,
+                 jitter: float = 0.05) -> Inputs:
+    """Monomers M (type B, state 0) and initiators (type A, state 2 = P*)."""
+    rng = np.random.default_rng(seed)
+    n = n_M + n_init
+    L = box_edge(n, rho)
+    x = lattice_positions(n, L, rng, jitter)
+    v = maxwell_velocities(n, kT, 1.0, rng)
+    typ = np.full(n, TYPE_B, np.uint8)
+    st = np.zeros(n, np.int8)
+    ids = rng.permutation(n)[:n_init]
+    typ[ids] = TYPE_A
+    st[ids] = 2
+    return Inputs(L, x, v, typ, st, "chain", 1, seed)
+
+
+def log_uniform_int(rng: np.random.Generator, lo: int, hi: int, size=None):
+    return np.exp(rng.uniform(math.log(lo), math.log(hi), size)).astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Reaction schemes as plain parameter sets (no arithmetic).  Both the oracle
+# and the CUDA library turn one of these into their own parameter struct.
+# ---------------------------------------------------------------------------
+def step_growth_scheme(f: int, k: float, theta: int = 10, r_react: float = 1.1,
+                       bond_style: int = 0) -> dict:
+    """Step growth, Sec. II.B, with difunctional single-bead targets:
+    A crosslinkers start at state f and react while in states 1..f
+    (delta_A = -1); B targets react while in states 0..1 (delta_T = +1), so a
+    B forms at most two bonds and an A at most f."""
+    mv = [0] * 8
+    mv[TYPE_B] = 2
+    mv[TYPE_A] = f
+    return dict(mask_A=1 << TYPE_A, mask_T=1 << TYPE_B, a_lo=1, a_hi=f, t_lo=0, t_hi=1, dA=-1,
+                dT=+1, k=k, theta=theta, r_react=r_react, bond_style=bond_style,
+                max_valence=tuple(mv))
+
+
+def chain_growth_scheme(k: float, theta: int = 10, r_react: float = 1.1,
+                        bond_style: int = 0) -> dict:
+    """Chain growth, Sec. II.A: states M = 0, P = 1, P* = 2.  The active end
+    P* (an initiator of type A or a monomer of type B) binds a monomer M of
+    type B; the old end becomes P (delta_A = -1) and the monomer becomes the
+    new end P* (delta_T = +2)."""
+    mv = [0] * 8
+    mv[TYPE_B] = 2
+    mv[TYPE_A] = 1
+    return dict(mask_A=(1 << TYPE_A) | (1 << TYPE_B), mask_T=1 << TYPE_B, a_lo=2, a_hi=2, t_lo=0,
+                t_hi=0, dA=-1, dT=+2, k=k, theta=theta, r_react=r_react, bond_style=bond_style,
+                max_valence=tuple(mv))
+
+
+# The five workloads, by size.  Physical parameters shared by all of them:
+# sigma = eps = m = 1, kT = 1, gamma = 1, dt = 0.005, FENE k = 30, R0 = 1.5,
+# r_react = 1.1, Theta = 10, rho = 0.85.
+WORKLOADS = {
+    "step_growth_1250_fp64": dict(n_B=1000, n_A=250, f=4, k=0.1, steps=10_000, fp64=True),
+    "chain_growth_33096": dict(n_M=32_768, n_init=328, k=(0.01, 0.1, 1.0), steps=50_000),
+    "step_growth_1m": dict(n_total=1_048_576, f=4, k=0.1, steps=20_000),
+    "ensemble_256": dict(replicas=256, n_lo=1024, n_hi=65_536, k_lo=0.01, k_hi=1.0, steps=20_000),
+    "serving_stream": dict(rate=20.0, n_lo=2048, n_hi=262_144, steps_lo=5000, steps_hi=50_000,
+                           arrivals=512),
+}
