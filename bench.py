@@ -1,0 +1,322 @@
+"""Benchmark: particle-steps/s of the reactive MD hot path on GB300.
+
+Workload (default): 1,048,576-bead step growth (difunctional B monomers and
+A crosslinkers of functionality 4 at a 4:1 B:A site ratio, density 0.85,
+WCA + FENE + Langevin, dt = 0.005, reaction every Theta = 10 steps with
+r_react = 1.1 and k = 0.1), FP32 forces with FP64 integration.
+
+One bench step = one reaction interval: Theta MD steps (fused force +
+integrate kernel, conditional cell-list rebuilds) followed by the reaction
+step and its observables record, i.e. every step of the hot path.  The metric
+counts particles x MD steps.  Inputs are synthetic (seeded lattice placement,
+Maxwell velocities); the L2 cache is flushed between timed bench steps.
+
+Multi-GPU (torchrun): every rank advances its own independent replica (own
+seed); there is no data-path collective ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "step_growth_1m"
+N_BEADS = 1_048_576
+FUNC = 4
+K_RATE = 0.1
+THETA = 10
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="polyrx", choices=["polyrx", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def inputs(rank: int):
+    return synth.step_growth_sites(N_BEADS, FUNC, synth.BASE_SEED + rank)
+
+
+def scheme():
+    return synth.step_growth_scheme(FUNC, k=K_RATE, theta=THETA)
+
+
+class Clocks:
+    """nvidia-smi sampling while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [q.strip() for q in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes_per_particle_step(mean_bonds_per_bead: float) -> float:
+    """Step kernel's share of the per-particle-step traffic: FP64 x and v read
+    and written (96 B) plus the adjacency entries read (4 B per bond end)."""
+    return 96.0 + 4.0 * mean_bonds_per_bead
+
+
+def cpu_baseline(budget_s: float) -> dict:
+    """The oracle as it stands, single-threaded on this host, on a bounded
+    sample of the same workload: MD steps (with the reaction every Theta
+    steps) of the full 1M-bead system until the budget is spent."""
+    import oracle as orc
+    inp = inputs(0)
+    sch = scheme()
+    o = orc.System(inp.x, inp.v, inp.type, inp.state, cap=FUNC)
+    md = orc.MDParams(L=(inp.L,) * 3, seed=synth.BASE_SEED)
+    rx = orc.Reaction(**sch)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        orc.run(o, md, rx, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 10 * THETA:
+            break
+    return {"value": inp.n * steps / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} MD steps of the {inp.n}-bead step-growth workload "
+                      f"(reaction every {THETA} steps), FP64, one thread, {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle, timed on this host's cores; each bench
+    step is one MD step of the same 1M-bead workload (the reaction every
+    Theta steps)."""
+    if rank != 0:
+        return
+    import oracle as orc
+    inp = inputs(0)
+    sch = scheme()
+    o = orc.System(inp.x, inp.v, inp.type, inp.state, cap=FUNC)
+    md = orc.MDParams(L=(inp.L,) * 3, seed=synth.BASE_SEED)
+    rx = orc.Reaction(**sch)
+    for _ in range(args.warmup):
+        orc.run(o, md, rx, 1)
+    t0 = time.perf_counter()
+    done = 0
+    budget = 150.0
+    for _ in range(args.steps):
+        orc.run(o, md, rx, 1)
+        done += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    el = time.perf_counter() - t0
+    v = inp.n * done / el
+    line = {"impl": "reference", "metric": "particle-steps/s", "value": v,
+            "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": done, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / max(done, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "beads": inp.n, "f": FUNC, "k": K_RATE,
+                       "theta": THETA, "sample": "one MD step per bench step"},
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{done} MD steps of the {inp.n}-bead workload, one thread"},
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    from paper_1409_7498_gb300 import build as gbuild
+    from paper_1409_7498_gb300 import polyrx as P
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        gbuild.build()
+    if world > 1:
+        dist.barrier()
+    gbuild.build()
+    stream = torch.cuda.Stream(device=dev)
+
+    inp = inputs(rank)
+    sch = scheme()
+    desc = P.make_desc(inp.n, inp.L, adj_cap=FUNC, seed=synth.BASE_SEED + rank)
+    g = P.System(desc, inp.x, inp.v, inp.type, inp.state, stream=stream.cuda_stream)
+    g.set_reaction(P.make_reaction(**sch))
+
+    # warm-up (also melts the lattice)
+    g.run(args.warmup * THETA)
+    g.sync()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    st0 = g.stats()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = Clocks(local)
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for q in range(args.steps):
+            flush.fill_(q & 0xFF)  # L2 flush between timed bench steps (256 MB > 129 MB L2)
+            starts[q].record(stream)
+            g.run(THETA)
+            ends[q].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = clk.stop()
+    g.sync()
+    st1 = g.stats()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = world * inp.n * THETA * args.steps / (ms_max * 1e-3)
+    launches = int(st1["kernel_launches"] - st0["kernel_launches"])
+    rebins = int(st1["rebins"] - st0["rebins"])
+
+    # roofline of the dominant kernel: per-kernel CUDA-event times on the same
+    # stream over a further stretch of the same run (kernels launched one by one)
+    P.prx_profile_begin(g.h)
+    g.run(10 * THETA)
+    prof = P.prx_profile_end(g.h)
+    top = max(prof, key=lambda r: r["total_ms"])
+    step_rec = next(r for r in prof if r["name"] == "step")
+    nb = g.observables()["bonds"]
+    bpp = algorithmic_bytes_per_particle_step(2.0 * nb / inp.n)
+    avg_ms = step_rec["total_ms"] / step_rec["launches"]
+    achieved = inp.n * bpp / (avg_ms * 1e-3) / 1e9
+    peak = json.load(open(PEAKS))["hbm_gbs"] if os.path.exists(PEAKS) else 6800.0
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if os.path.exists(tr_path):
+        tr = json.load(open(tr_path))
+        if tr.get("kernel_source_digest") == gbuild._digest():
+            traffic = tr.get("bytes_per_launch")
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if rank == 0:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+               for k, a in (("x", inp.x), ("v", inp.v), ("t", inp.type), ("s", inp.state))}
+        h2d = sum(a.nbytes for a in pin.values())
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        ge = P.System(desc, pin["x"], pin["v"], pin["t"], pin["s"], stream=stream.cuda_stream)
+        ge.set_reaction(P.make_reaction(**sch))
+        d2h = 0
+        ke = 8
+        for q in range(ke):
+            ge.run(THETA)
+            ob = ge.observables()  # the step's result: populations, bonds, energy
+            d2h += 8 * (2 + 8 * 16 + 4)
+        stt = ge.states()
+        bd = ge.bonds()
+        d2h += stt.nbytes + bd.nbytes
+        ge.close()
+        e_el = time.perf_counter() - e0
+        e2e = {"value": inp.n * THETA * ke / e_el, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": int(h2d / ke), "d2h_bytes_per_step": int(d2h / ke),
+               "steps": ke, "includes": "create (upload + binning), runs, per-step observables "
+                                        "read-back, final states and bonds, destroy"}
+        del ob
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(args.cpu_budget)
+        line = {
+            "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 forces / f64 integration", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "beads": inp.n, "f": FUNC, "k": K_RATE,
+                       "theta": THETA, "md_steps_per_bench_step": THETA, "box": inp.L,
+                       "cells": list(st1["cells"]), "parallelism": f"replicas x{world}",
+                       "l2": "flushed between bench steps (256 MB write)",
+                       "rebins_in_timed_region": rebins, "wall_s": wall},
+            "clocks": clocks, "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "kernel": "step", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes_per_particle_step": bpp,
+                         "avg_launch_ms": avg_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs"
+                         if os.path.exists(PEAKS) else "fallback",
+                         "top_kernel": top["name"],
+                         "kernel_ms": {r["name"]: round(r["total_ms"], 4) for r in prof},
+                         "kernel_launches": {r["name"]: r["launches"] for r in prof}},
+            "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

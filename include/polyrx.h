@@ -1,0 +1,231 @@
+/*
+ * polyrx: C ABI of the GB300 (sm_103a) reactive coarse-grained MD library.
+ *
+ * It implements the data-parallel hot path of de Buyl & Nies, "A parallel
+ * algorithm for step- and chain-growth polymerization in Molecular
+ * Dynamics" (arXiv:1409.7498):
+ *   - the MD step: WCA pair forces (Sec. II.C, Eq. 15) from a cell list,
+ *     FENE bond forces (Sec. II.C) or mirror-LJ created bonds (Eq. 17), and a
+ *     Langevin velocity-Verlet integrator (velocity Verlet, Sec. II.C);
+ *   - the reaction step run every Theta steps after the integration
+ *     (Sec. III): candidate A/T pairs by type, state and distance, accepted
+ *     with probability k dt Theta (Eqs. 3-4), one T per A and one A per T
+ *     chosen at random (Table I, steps 1-9), bonds appended and states
+ *     shifted by delta_A and delta_T (Eq. 2).
+ *
+ * Conventions for every entry point:
+ *   - Return value: PRX_OK (0) or a negative PRX_E* status.  No C++
+ *     exception crosses this boundary.  prx_last_error() gives a message.
+ *   - Host arrays are indexed by particle id 0..n-1 and are owned by the
+ *     caller; the library copies what it needs and never keeps a pointer to
+ *     them.  All device memory is owned by the library.
+ *   - Work is queued on the system's CUDA stream (the caller's stream when
+ *     one is passed to prx_create, else a library-owned non-blocking
+ *     stream).  Calls that return data to the host synchronise that stream.
+ *     Device-side errors (FENE overstretch, capacity, non-finite values) are
+ *     sticky: they surface at the next synchronising call or prx_sync().
+ *   - Not thread-safe per system: one host thread drives one system.
+ *   - Steps are numbered from 1.  A reaction runs after step s when
+ *     s % Theta == 0, on the positions of step s; new bonds act from the
+ *     next force evaluation.
+ */
+#ifndef POLYRX_H
+#define POLYRX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define PRX_OK 0
+#define PRX_EINVAL (-1)       /* bad argument, descriptor or call order */
+#define PRX_ENOMEM (-2)       /* device or host allocation failed */
+#define PRX_ECAPACITY (-3)    /* adjacency, valence, bond-list or buffer capacity exceeded */
+#define PRX_EOVERSTRETCH (-4) /* a FENE bond reached r >= R0 */
+#define PRX_ENONFINITE (-5)   /* a position, velocity or force became non-finite,
+                                 or a particle crossed more than one cell in a step */
+#define PRX_ETIMEOUT (-6)     /* a bounded device wait gave up */
+#define PRX_ECUDA (-7)        /* a CUDA runtime call failed */
+#define PRX_EIO (-8)          /* checkpoint file could not be read or written */
+
+/* ---- constants ------------------------------------------------------- */
+#define PRX_BOND_FENE 0       /* Kremer-Grest FENE, Sec. II.C */
+#define PRX_BOND_MIRROR_LJ 1  /* mirror Lennard-Jones, Eq. 17 */
+#define PRX_FORCE_FP32 0      /* pair and bond forces in FP32, integration in FP64 */
+#define PRX_FORCE_FP64 1      /* everything in FP64 */
+#define PRX_MAX_TYPES 8
+#define PRX_MAX_STATES 16     /* states tracked by the observables: 0..15 */
+#define PRX_MAX_ADJ 8         /* largest adjacency capacity per particle */
+
+typedef struct prx_system prx_system; /* opaque, library-owned */
+
+/* System descriptor.  Units are reduced LJ units (Sec. II.C). */
+typedef struct {
+  uint32_t n;             /* particles (0 allowed) */
+  uint32_t adj_cap;       /* bonds a particle may hold, 1..PRX_MAX_ADJ */
+  double box[3];          /* periodic box edges */
+  double dt;              /* time step */
+  double kT;              /* thermostat temperature */
+  double gamma;           /* Langevin friction; 0 = plain velocity Verlet */
+  double mass;            /* particle mass */
+  double wca_eps;         /* WCA epsilon (Eq. 15) */
+  double wca_sigma;       /* WCA sigma; cutoff sigma_c = 2^(1/6) sigma */
+  double fene_k;          /* FENE k_F */
+  double fene_r0;         /* FENE R_0 */
+  double force_cap;       /* > 0: cap on the WCA pair-force magnitude (warm-up); 0: off */
+  double skin;            /* cell edge >= cutoff + skin; < 0 selects the default (0.15) */
+  int32_t force_precision;/* PRX_FORCE_FP32 or PRX_FORCE_FP64 */
+  int32_t reserved;       /* must be 0 */
+  uint64_t seed;          /* key of every random draw */
+} prx_system_desc;
+
+/* Reaction scheme T^t + A^a -> T^(t+dT)-A^(a+dA) (Eq. 2).  A particle of
+ * type t is an eligible A when bit t of type_mask_A is set and its state is
+ * in [a_lo, a_hi]; likewise for T.  For a type in both masks the two
+ * windows must be disjoint, so no particle is A and T at once. */
+typedef struct {
+  uint32_t type_mask_A;
+  uint32_t type_mask_T;
+  int32_t a_lo, a_hi;
+  int32_t t_lo, t_hi;
+  int32_t dA, dT;
+  double k;               /* intrinsic rate; acceptance probability p = k dt Theta */
+  double r_react;         /* reaction cutoff (strict: r^2 < r_react^2, FP64) */
+  uint32_t theta;         /* reaction interval Theta >= 1 */
+  int32_t bond_style;     /* style of the created bonds */
+  uint8_t max_valence[PRX_MAX_TYPES]; /* per type: bonds a particle may hold */
+} prx_reaction_desc;
+
+/* One bond of the bond list (the FixedPairList of Sec. III.A).  For a
+ * created bond a is the active A and t the target T. */
+typedef struct {
+  uint32_t a, t;
+  int64_t step;           /* step the bond formed; 0 for bonds given at creation */
+  uint32_t style;
+  uint32_t reserved;
+} prx_bond;
+
+/* Counts of Table I for one reaction step. */
+typedef struct {
+  int64_t candidates;     /* step 1: eligible pairs within the cutoff */
+  int64_t retained;       /* step 2: accepted by u < k dt Theta */
+  int64_t a_winners;      /* step 5: A's left with one T */
+  int64_t formed;         /* steps 7-9: bonds created */
+} prx_rx_trace;
+
+typedef struct {
+  int64_t step;
+  int64_t bonds;
+  int64_t counts[PRX_MAX_TYPES][PRX_MAX_STATES]; /* particles per (type, state) */
+  double ke_half;         /* sum of m v^2 / 2 over the stored half-step velocities */
+  double momentum[3];
+} prx_observables;
+
+/* One record of the per-reaction history kept on the device. */
+typedef struct {
+  int64_t step;
+  int64_t bonds;
+  int32_t counts[PRX_MAX_TYPES][PRX_MAX_STATES];
+} prx_history_record;
+
+typedef struct {
+  uint64_t steps;         /* MD steps completed */
+  uint64_t reactions;     /* reaction steps completed */
+  uint64_t rebins;        /* cell-list rebuilds */
+  uint64_t step_launches; /* step-kernel launches */
+  uint64_t kernel_launches; /* all kernels launched by this system so far */
+  uint32_t cells[3];      /* cell grid */
+  double cell_edge[3];
+} prx_stats;
+
+/* Per-kernel device time recorded with CUDA events while profiling is on. */
+typedef struct {
+  char name[32];
+  uint64_t launches;
+  double total_ms;
+} prx_kernel_time;
+
+/* ---- lifecycle --------------------------------------------------------- */
+
+/* Creates a system.  pos: [n][3] in [0, box) (a coordinate outside is
+ * wrapped once; farther outside is PRX_EINVAL).  vel: [n][3] or NULL for
+ * zero.  type: [n] values < PRX_MAX_TYPES.  state: [n].  bonds: n_bonds
+ * initial bonds (a != t, ids < n) or NULL; they count against adj_cap.
+ * cuda_stream: a cudaStream_t to use, or NULL for a library-owned stream.
+ * On success *out receives the system. */
+int prx_create(const prx_system_desc* desc, const double* pos, const double* vel,
+               const uint8_t* type, const int8_t* state, const prx_bond* bonds,
+               uint64_t n_bonds, void* cuda_stream, prx_system** out);
+
+/* Frees every device and host resource of the system (NULL is a no-op). */
+void prx_destroy(prx_system* sys);
+
+/* Device bytes prx_create would allocate for this descriptor, before any
+ * reaction history. */
+int prx_estimate_bytes(const prx_system_desc* desc, uint64_t* bytes);
+
+/* Sets (or, with rx == NULL, clears) the reaction scheme.  PRX_EINVAL when
+ * the state windows of a type in both masks overlap, theta == 0, k < 0,
+ * r_react <= 0, or a bond style is unknown.  If r_react exceeds the cell
+ * list's cutoff the cell grid is rebuilt. */
+int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx);
+
+/* ---- execution --------------------------------------------------------- */
+
+/* Queues nsteps MD steps (with the reaction every Theta steps) on the
+ * system's stream and returns without waiting. */
+int prx_run(prx_system* sys, uint64_t nsteps);
+
+/* Waits for queued work; returns the sticky device status. */
+int prx_sync(prx_system* sys);
+
+/* Runs only the reaction step (Table I) on the current state, numbering the
+ * draws with `step` (parity entry point; no MD step is taken).  trace may
+ * be NULL.  Synchronises. */
+int prx_react_once(prx_system* sys, uint64_t step, prx_rx_trace* trace);
+
+/* Conservative forces (WCA + bonds, no thermostat) at the current positions,
+ * f_out [n][3] by id, and the potential energy.  Synchronises. */
+int prx_compute_forces(prx_system* sys, double* f_out, double* epot_out);
+
+/* ---- read-back (all synchronise) ------------------------------------------ */
+int prx_get_step(prx_system* sys, uint64_t* step);
+int prx_get_positions(prx_system* sys, double* out /* [n][3] by id, wrapped into [0, box) */);
+int prx_get_velocities(prx_system* sys, double* out /* [n][3] by id, half-step */);
+int prx_get_states(prx_system* sys, int8_t* out /* [n] by id */);
+int prx_get_types(prx_system* sys, uint8_t* out /* [n] by id */);
+/* Bonds in canonical order (step, a, t).  *n_out receives the bond count;
+ * PRX_ECAPACITY if cap is smaller (out then holds the first cap). */
+int prx_get_bonds(prx_system* sys, prx_bond* out, uint64_t cap, uint64_t* n_out);
+int prx_get_observables(prx_system* sys, prx_observables* out);
+/* The last min(cap, recorded) per-reaction records, oldest first.  The
+ * device keeps the most recent `history_cap` records (default 8192). */
+int prx_get_history(prx_system* sys, prx_history_record* out, uint64_t cap, uint64_t* n_out);
+int prx_get_stats(prx_system* sys, prx_stats* out);
+
+/* ---- checkpoint ------------------------------------------------------------ */
+/* Writes positions, velocities, types, states, bonds, step, descriptor and
+ * reaction scheme.  Every random draw is keyed by (seed, step, ids), so a
+ * loaded system continues bit for bit. */
+int prx_save(prx_system* sys, const char* path);
+int prx_load(const char* path, void* cuda_stream, prx_system** out);
+
+/* ---- profiling ------------------------------------------------------------- */
+/* While on, prx_run launches kernels one by one (no CUDA graph), brackets
+ * each with CUDA events on the system's stream, and reads the cell-list
+ * flag after every step to launch a rebuild only when needed. */
+int prx_profile_begin(prx_system* sys);
+/* Ends profiling and returns per-kernel launch counts and device time. */
+int prx_profile_end(prx_system* sys, prx_kernel_time* out, uint32_t cap, uint32_t* n_out);
+
+/* ---- errors ---------------------------------------------------------------- */
+const char* prx_last_error(const prx_system* sys);
+const char* prx_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLYRX_H */

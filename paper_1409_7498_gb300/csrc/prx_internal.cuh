@@ -1,0 +1,260 @@
+// Internal layout and device helpers of the polyrx CUDA library.
+//
+// Data layout in HBM (one system, n particles, slot order = sorted by cell):
+//   two SoA sets (the current one and the rebuild target):
+//     x, y, z, vx, vy, vz : double[n]   absolute positions, half-step velocities
+//     id                  : u32[n]      particle id of the slot
+//     type, state, nadj   : u8/i8/u8[n]
+//     adj                 : u32[n*cap]  partner slots; bit 31 = bond style
+//   off[2]  : int4[n]    position relative to the slot's cell origin in
+//                        2^-29 fixed point (exact differences between any two
+//                        particles), .w = packed cell coordinates (9 bits
+//                        each); double-buffered across steps (neighbours
+//                        read the old copy while the new one is written)
+//   cell_start : u32[ncell+1]  CSR offsets of the cells (z-major)
+// A device control block (Ctl) holds the current set / buffer phase, the
+// step counter, the rebuild flag and the sticky error status, so that one
+// CUDA graph can be replayed without host involvement.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/polyrx.h"
+
+namespace prx {
+
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr uint32_t SLOT_MASK = 0x7FFFFFFFu;
+constexpr int STEP_THREADS = 128;   // FP64-mode kernels
+constexpr int RX_THREADS = 256;
+constexpr int SCAN_TILE = 2048;  // elements per scan tile (256 threads x 8)
+
+// Counter tags of the keyed Philox draws (fourth counter word, low byte).
+constexpr uint32_t TAG_THERMO = 1u, TAG_ACCEPT = 2u, TAG_SEL_A = 3u, TAG_SEL_T = 4u;
+
+struct SoA {
+  double *x, *y, *z, *vx, *vy, *vz;
+  uint32_t* id;
+  uint8_t* type;
+  int8_t* state;
+  uint8_t* nadj;
+  uint32_t* adj;
+};
+
+struct BondRec {
+  uint32_t a, t;
+  int64_t step;
+  uint32_t style, reserved;
+};
+static_assert(sizeof(BondRec) == sizeof(prx_bond), "bond record layout");
+
+struct HistRec {
+  int64_t step;
+  int64_t bonds;
+  int32_t counts[PRX_MAX_TYPES][PRX_MAX_STATES];
+};
+static_assert(sizeof(HistRec) == sizeof(prx_history_record), "history record layout");
+
+struct Ctl {
+  int set;                  // current SoA set
+  int phase;                // current off buffer
+  int rebin_flag;           // a particle left its extended cell
+  int status;               // sticky PRX_E* status (0 = ok)
+  unsigned int done_step;   // last-block counters
+  unsigned int done_rebin;
+  unsigned int done_rx;
+  unsigned int done_obs;
+  unsigned long long step;  // completed MD steps
+  unsigned long long rebins;
+  unsigned long long reactions;
+  unsigned long long nbonds;
+  unsigned long long hist_count;
+  unsigned long long rx_base;  // bond-list offset of the current reaction
+  long long trace[4];          // candidates, retained, a_winners, formed
+};
+
+struct RxParams {
+  uint32_t mask_A, mask_T;
+  int32_t a_lo, a_hi, t_lo, t_hi, dA, dT;
+  double p;         // k dt Theta
+  double rr2;       // r_react^2 (exact test)
+  float rr2_pre;    // (r_react + margin)^2 (FP32 prefilter, always conservative)
+  uint32_t style;
+  uint8_t maxval[PRX_MAX_TYPES];
+};
+
+struct Sys {
+  uint32_t n, cap;
+  int nc[3];
+  int ncell;
+  // geometry
+  double L[3], halfL[3];
+  float Lf[3];
+  float hf[3];            // cell edge as float (prefilter geometry)
+  long long Hfx[3];       // cell edge in 2^-32 fixed point (= 8 H29)
+  int H29[3];             // cell edge in 2^-29 fixed point
+  int corr29[3];          // L in 2^-29 minus n_c H29: periodic-image correction
+  long long lofx[3];      // extended cell: offsets in [lofx, hifx) keep the list valid
+  long long hifx[3];
+  double inv_h[3];
+  // physics (FP32 and FP64 copies)
+  float rc2f, sig2f, eps24f, eps4f, fcapf, fkf, fr02f, rcf, sigf;
+  double rc2, sig2, eps24, eps4, fcap, fk, fr02, rc, sig;
+  double dt, a_fric, b_kick;  // v' = a v + b F ; x' = x + dt v'
+  double gm;                  // gamma m (FP64 mode writes the friction force out)
+  double mass;
+  float b_kickf, cRf;
+  float rc2pre;               // (r_c + 1e-3)^2: conservative FP32 prefilter cutoff
+  double cR;
+  int thermo;                 // gamma > 0
+  uint64_t seed;
+  // buffers
+  SoA s0, s1;
+  int4 *off0, *off1;
+  int tile_y;               // cell rows per block of the FP32 step kernel (1..4)
+  int tiles_y;              // ceil(n_c[1] / tile_y)
+  int tile_threads;         // threads per block
+  int tile_cap;             // staged particles per shared-memory pass
+  uint32_t* cell_start;
+  uint32_t *count, *fill;
+  uint32_t *key, *tmp, *new_of_old, *slot_of_id;
+  uint32_t *win, *fin, *blk_count, *blk_off;
+  BondRec* bonds;
+  unsigned long long bond_cap;
+  HistRec* hist;
+  unsigned int hist_cap;
+  double *fout, *eout;
+  double* red;              // per-block partial sums (observables)
+  Ctl* ctl;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies by the round constants, a word permutation and a xor
+// with the round key, the key advancing by the two Weyl constants.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Counter layout of every keyed draw: (step lo, id a, id b, tag | step hi << 8),
+// key = (seed lo, seed hi).
+__device__ __forceinline__ uint4 keyed_draw(uint64_t seed, unsigned long long step, uint32_t a,
+                                            uint32_t b, uint32_t tag) {
+  return philox4x32_10(make_uint4((uint32_t)step, a, b, tag | ((uint32_t)(step >> 32) << 8)),
+                       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// 53-bit uniform in [0,1): top 53 bits of (hi:lo) times 2^-53 (exact).
+__device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
+  unsigned long long w = ((unsigned long long)hi << 32) | lo;
+  return __dmul_rn(__ull2double_rn(w >> 11), 0x1.0p-53);
+}
+
+// Small unsigned integer v < 2^23 as float, exactly, on the integer and FP32
+// pipes: the bit pattern 0x4B000000 | v is the float 2^23 + v.
+__device__ __forceinline__ float small_u2f(uint32_t v) {
+  return __fsub_rn(__uint_as_float(0x4B000000u | v), 8388608.0f);
+}
+
+// 24-bit uniform in [0,1): (w >> 8) 2^-24, exact in float.
+__device__ __forceinline__ float u24f(uint32_t w) {
+  const uint32_t v = w >> 8;
+  const float half = small_u2f(v >> 1);
+  return __fmul_rn(__fmaf_rn(half, 2.0f, (v & 1u) ? 1.0f : 0.0f), 0x1.0p-24f);
+}
+
+// binary32 -> binary64 by re-biasing the exponent field: exact for normal
+// numbers and zero (binary32 subnormals become zero; the kernels run with
+// flush-to-zero).  Costs integer operations only, no FP64-pipe instruction.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t mag = u & 0x7FFFFFFFu;
+  uint32_t hi = (u & 0x80000000u) | ((mag >> 3) + 0x38000000u);
+  uint32_t lo = u << 29;
+  if (mag < 0x00800000u) {
+    hi = u & 0x80000000u;
+    lo = 0u;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// trunc(x * 2^32) for |x| < 2^29, read off the binary64 fields (integer pipe).
+__device__ __forceinline__ long long fx32(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const long long m = (b & 0x000FFFFFFFFFFFFFLL) | 0x0010000000000000LL;
+  const int sh = 1043 - e;  // x 2^32 = m 2^(e - 1075 + 32)
+  // |x| >= 2^29 (or inf/nan) saturates to 2^62: far outside any cell, which
+  // the callers report as an error
+  long long r = (sh >= 63) ? 0LL : (sh >= 0 ? (m >> sh) : (sh >= -9 ? (m << (-sh)) : (1LL << 62)));
+  return (b < 0) ? -r : r;
+}
+
+// d 2^-32 correctly rounded to float, |d| < 2^34, without an I2F/F2F
+// instruction: d = hi 2^20 + lo with both halves converted exactly, then one
+// rounding in the fused multiply-add.
+__device__ __forceinline__ float fx_to_float(long long d) {
+  const int hi = (int)(d >> 20);                    // [-2^14, 2^14)
+  const uint32_t lo = (uint32_t)d & 0xFFFFFu;       // [0, 2^20)
+  const float hf = __fsub_rn(__uint_as_float(0x4B000000u | (uint32_t)(hi + 16384)), 8404992.0f);
+  const float lf = small_u2f(lo);
+  return __fmul_rn(__fmaf_rn(hf, 1048576.0f, lf), 0x1.0p-32f);
+}
+
+// A 32-bit integer rounded once to float (round to nearest even), on the
+// integer and FP32 pipes: d = hi 2^12 + lo, both halves exact in float.
+__device__ __forceinline__ float i2f_rn(int d) {
+  const int hi = d >> 12;                       // [-2^19, 2^19)
+  const uint32_t lo = (uint32_t)d & 0xFFFu;     // [0, 2^12)
+  const float hf = __fsub_rn(__uint_as_float(0x4B000000u | (uint32_t)(hi + 524288)), 8912896.0f);
+  return __fmaf_rn(hf, 4096.0f, small_u2f(lo));
+}
+// 2^-29 fixed point to float, one rounding.
+__device__ __forceinline__ float fx29_to_float(int d) { return __fmul_rn(i2f_rn(d), 0x1.0p-29f); }
+
+__device__ __forceinline__ uint32_t pack_cell(int cx, int cy, int cz) {
+  return (uint32_t)cx | ((uint32_t)cy << 9) | ((uint32_t)cz << 18);
+}
+__device__ __forceinline__ void unpack_cell(uint32_t w, int& cx, int& cy, int& cz) {
+  cx = (int)(w & 511u);
+  cy = (int)((w >> 9) & 511u);
+  cz = (int)((w >> 18) & 511u);
+}
+__device__ __forceinline__ int wrap_cell(int q, int n) { return q < 0 ? q + n : (q >= n ? q - n : q); }
+
+__device__ __forceinline__ void set_status(Ctl* ctl, int code) { atomicCAS(&ctl->status, 0, code); }
+
+__device__ __forceinline__ const SoA& cur_soa(const Sys& S, int set) { return set ? S.s1 : S.s0; }
+
+// Minimum image of one FP64 separation component by compare-and-shift.
+__device__ __forceinline__ double min_image(double d, double L, double half) {
+  if (d > half) return __dsub_rn(d, L);
+  if (d < -half) return __dadd_rn(d, L);
+  return d;
+}
+
+// ---- host-side launchers (defined in the kernel translation units) ----------
+void launch_step(const Sys& S, cudaStream_t st, int fp64, int forces_only,
+                 cudaGraphConditionalHandle h, int use_cond);
+void launch_bin_full_keys(const Sys& S, cudaStream_t st);
+void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, const char*, int),
+                  void* hook_ctx);
+void launch_rx(const Sys& S, const RxParams& R, cudaStream_t st, long long step_arg,
+               void (*hook)(void*, const char*, int), void* hook_ctx);
+void launch_observables(const Sys& S, cudaStream_t st, int nblocks);
+int rebin_kernel_count();
+int step_kernel_count(int fp64);
+size_t step_tile_smem(const Sys& S);
+int configure_step_kernels(size_t smem_bytes);
+int rx_kernel_count();
+
+}  // namespace prx

@@ -1,0 +1,1065 @@
+// Host runtime of polyrx: the C ABI of include/polyrx.h.
+//
+// A system owns its device buffers (layout in prx_internal.cuh), a private
+// capture stream and three CUDA graphs built once per reaction scheme:
+//   step   : one step kernel followed by an IF node whose body rebuilds the
+//            cell list; the step kernel's last block sets the condition from
+//            the device flag, so a rebuild runs exactly when some particle
+//            left its extended cell, with no host round trip;
+//   chunk  : Theta copies of `step` followed by the reaction kernels (or ten
+//            steps when no reaction is set);
+//   react  : the reaction kernels alone.
+// prx_run replays `chunk` for whole reaction intervals and `step`/`react`
+// for the remainder.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "prx_internal.cuh"
+
+using namespace prx;
+
+namespace {
+constexpr double kDefaultSkin = 0.15;
+constexpr uint32_t kHistCap = 8192;
+constexpr uint64_t kCkptMagic = 0x31305850594C4F50ull;  // "POLYRX01"
+constexpr int kNoRxChunk = 10;
+
+struct ProfEvent {
+  std::string name;
+  cudaEvent_t a, b;
+};
+}  // namespace
+
+struct prx_system {
+  prx_system_desc d{};
+  int has_rx = 0;
+  prx_reaction_desc rxd{};
+  RxParams R{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap = nullptr;
+  Sys S{};
+  Ctl* ctl_host = nullptr;  // pinned mirror for read-back
+  std::vector<void*> dev_allocs;
+  std::vector<void*> grid_allocs;
+  double grid_rcut = 0.0;
+  uint64_t host_step = 0;
+  uint64_t step_launches = 0;      // step kernels (graphs and direct)
+  uint64_t graph_rx_launches = 0;  // reaction sequences replayed inside graphs
+  uint64_t other_launches = 0;     // other kernels launched directly (reaction, forces, observables)
+  cudaGraphExec_t g_step = nullptr, g_chunk = nullptr, g_react = nullptr;
+  bool graphs_valid = false;
+  bool profiling = false;
+  std::vector<ProfEvent> prof;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(prx_system* s, int code, const std::string& msg) {
+  if (s) s->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(sys, PRX_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+template <class T>
+int dalloc(prx_system* sys, std::vector<void*>& list, T** p, size_t count) {
+  void* q = nullptr;
+  size_t bytes = sizeof(T) * (count ? count : 1);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(sys, PRX_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  list.push_back(q);
+  *p = (T*)q;
+  return PRX_OK;
+}
+
+double wca_rc(const prx_system_desc& d) { return std::pow(2.0, 1.0 / 6.0) * d.wca_sigma; }
+
+int validate_desc(prx_system* sys, const prx_system_desc* d) {
+  if (!d) return fail(sys, PRX_EINVAL, "descriptor is NULL");
+  if (d->adj_cap < 1 || d->adj_cap > PRX_MAX_ADJ) return fail(sys, PRX_EINVAL, "adj_cap must be 1..8");
+  for (int k = 0; k < 3; ++k)
+    if (!(d->box[k] > 0.0 && d->box[k] < 1e8)) return fail(sys, PRX_EINVAL, "box edges must be in (0, 1e8)");
+  if (!(d->dt > 0.0) || !(d->mass > 0.0) || !(d->kT >= 0.0) || !(d->gamma >= 0.0))
+    return fail(sys, PRX_EINVAL, "dt, mass must be > 0; kT, gamma >= 0");
+  if (!(d->wca_sigma > 0.0) || !(d->wca_eps >= 0.0) || !(d->fene_r0 > 0.0) || !(d->fene_k >= 0.0))
+    return fail(sys, PRX_EINVAL, "bad potential parameters");
+  if (!(d->force_cap >= 0.0)) return fail(sys, PRX_EINVAL, "force_cap must be >= 0");
+  if (d->force_precision != PRX_FORCE_FP32 && d->force_precision != PRX_FORCE_FP64)
+    return fail(sys, PRX_EINVAL, "unknown force precision");
+  if (d->reserved != 0) return fail(sys, PRX_EINVAL, "reserved field must be 0");
+  if (d->n > 0x7FFFFFF0u) return fail(sys, PRX_EINVAL, "too many particles");
+  return PRX_OK;
+}
+
+int validate_rx(prx_system* sys, const prx_reaction_desc* r) {
+  if (r->a_lo > r->a_hi || r->t_lo > r->t_hi) return fail(sys, PRX_EINVAL, "empty state window");
+  if (r->theta < 1 || !(r->k >= 0.0) || !(r->r_react > 0.0))
+    return fail(sys, PRX_EINVAL, "theta >= 1, k >= 0, r_react > 0 required");
+  if (r->bond_style != PRX_BOND_FENE && r->bond_style != PRX_BOND_MIRROR_LJ)
+    return fail(sys, PRX_EINVAL, "unknown bond style");
+  if ((r->type_mask_A | r->type_mask_T) >> PRX_MAX_TYPES) return fail(sys, PRX_EINVAL, "type mask beyond 8 types");
+  if ((r->type_mask_A & r->type_mask_T) && !(r->a_hi < r->t_lo || r->t_hi < r->a_lo))
+    return fail(sys, PRX_EINVAL, "A and T state windows overlap for a type in both masks");
+  return PRX_OK;
+}
+
+void destroy_graphs(prx_system* s) {
+  if (s->g_step) cudaGraphExecDestroy(s->g_step);
+  if (s->g_chunk) cudaGraphExecDestroy(s->g_chunk);
+  if (s->g_react) cudaGraphExecDestroy(s->g_react);
+  s->g_step = s->g_chunk = s->g_react = nullptr;
+  s->graphs_valid = false;
+}
+
+void free_list(std::vector<void*>& l) {
+  for (void* p : l) cudaFree(p);
+  l.clear();
+}
+
+// Cell grid for cutoff rc: n_c = floor(L / (rc + skin)) cells per edge (at
+// least 3; at most 511, the packing limit), extended-cell tolerance
+// delta = (h - rc)/2 on each side.
+int setup_grid(prx_system* sys, double rc) {
+  Sys& S = sys->S;
+  const double skin = sys->d.skin < 0.0 ? kDefaultSkin : sys->d.skin;
+  long long ncell = 1;
+  for (int k = 0; k < 3; ++k) {
+    const double L = sys->d.box[k];
+    int nc = (int)std::floor(L / (rc + skin));
+    if (nc < 3) nc = (int)std::floor(L / (rc * (1.0 + 1e-9)));
+    if (nc < 3) return fail(sys, PRX_EINVAL, "box edge below three interaction cutoffs");
+    if (nc > 511) nc = 511;
+    const double h = L / nc;
+    if (h > 2.4) return fail(sys, PRX_EINVAL, "box edge too large for the 511-cell grid");
+    S.nc[k] = nc;
+    S.inv_h[k] = 1.0 / h;
+    S.H29[k] = (int)std::llround(h * 536870912.0);
+    S.Hfx[k] = 8LL * S.H29[k];
+    S.corr29[k] = (int)(std::llround(L * 536870912.0) - (long long)nc * S.H29[k]);
+    S.hf[k] = (float)((double)S.H29[k] / 536870912.0);
+    const double delta = 0.5 * (h - rc) - 1e-6;
+    const long long dfx = delta > 0.0 ? (long long)std::floor(delta * 4294967296.0) : 0LL;
+    S.lofx[k] = -dfx;
+    S.hifx[k] = S.Hfx[k] + dfx;
+    ncell *= nc;
+  }
+  S.ncell = (int)ncell;
+  sys->grid_rcut = rc;
+  {
+    // FP32 step kernel tiling: about 300 particles per block, all neighbour
+    // rows staged in one shared-memory pass in the common case
+    const double per_row = (double)S.n / ((double)S.nc[1] * S.nc[2]);
+    const double per_cell = (double)S.n / (double)ncell;
+    // largest tile (1..4 rows) whose particle count stays within 256 threads
+    int ty = 1;
+    for (int c = 2; c <= 4; ++c)
+      if (c * per_row + 3.0 * std::sqrt(c * per_row) + 16.0 <= 256.0) ty = c;
+    ty = std::max(1, std::min(ty, S.nc[1]));
+    S.tile_y = ty;
+    S.tiles_y = (S.nc[1] + ty - 1) / ty;
+    const double mean_tile = ty * per_row;
+    int t = (int)std::ceil((mean_tile + 3.0 * std::sqrt(mean_tile) + 16.0) / 32.0) * 32;
+    S.tile_threads = std::max(64, std::min(256, t));
+    const double mean_tot = 3.0 * (ty + 2) * (per_row + 2.0 * per_cell);
+    int cap = (int)std::ceil((mean_tot + 3.5 * std::sqrt(mean_tot) + 32.0) / 32.0) * 32;
+    S.tile_cap = 0;
+    const size_t fixed = step_tile_smem(S);
+    const size_t budget = 200 * 1024;
+    if (fixed + 32 * (size_t)cap > budget) cap = (int)((budget - fixed) / 32);
+    S.tile_cap = std::max(64, cap);
+    if (configure_step_kernels(step_tile_smem(S)))
+      return fail(sys, PRX_ECUDA, "cannot set the step kernel's shared-memory size");
+  }
+  free_list(sys->grid_allocs);
+  int rc2;
+  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.cell_start, (size_t)ncell + 1))) return rc2;
+  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.count, (size_t)ncell))) return rc2;
+  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.fill, (size_t)ncell))) return rc2;
+  const size_t nblk = std::max<size_t>((S.n + RX_THREADS - 1) / RX_THREADS,
+                                       ((size_t)ncell + SCAN_TILE - 1) / SCAN_TILE) + 1;
+  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.blk_count, nblk))) return rc2;
+  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.blk_off, nblk))) return rc2;
+  return PRX_OK;
+}
+
+int read_ctl(prx_system* sys) {
+  CK(cudaMemcpyAsync(sys->ctl_host, sys->S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, sys->stream));
+  CK(cudaStreamSynchronize(sys->stream));
+  return PRX_OK;
+}
+
+int sync_status(prx_system* sys) {
+  int rc = read_ctl(sys);
+  if (rc) return rc;
+  const int st = sys->ctl_host->status;
+  if (st) return fail(sys, st, std::string("device reported ") + prx_status_string(st));
+  return PRX_OK;
+}
+
+// Event hook used while profiling: records an event before and after each launch.
+void prof_hook(void* ctx, const char* name, int phase) {
+  prx_system* s = (prx_system*)ctx;
+  if (phase == 0) {
+    ProfEvent e;
+    e.name = name;
+    cudaEventCreate(&e.a);
+    cudaEventCreate(&e.b);
+    cudaEventRecord(e.a, s->stream);
+    s->prof.push_back(e);
+  } else {
+    cudaEventRecord(s->prof.back().b, s->stream);
+  }
+}
+
+int full_rebin(prx_system* sys, int mode) {
+  launch_rebin(sys->S, sys->stream, mode, nullptr, nullptr);
+  CK(cudaGetLastError());
+  return PRX_OK;
+}
+
+int build_graph(prx_system* sys, int nsteps, bool with_rx, cudaGraphExec_t* out) {
+  cudaGraph_t g;
+  CK(cudaGraphCreate(&g, 0));
+  std::vector<cudaGraph_t> bodies;
+  CK(cudaStreamBeginCaptureToGraph(sys->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  for (int s = 0; s < nsteps; ++s) {
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    launch_step(sys->S, sys->cap, sys->d.force_precision == PRX_FORCE_FP64, 0, h, 1);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t gcap;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(sys->cap, &cs, nullptr, &gcap, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t cn;
+    CK(cudaGraphAddNode(&cn, gcap, deps, nullptr, ndeps, &np));
+    bodies.push_back(np.conditional.phGraph_out[0]);
+    CK(cudaStreamUpdateCaptureDependencies(sys->cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  }
+  if (with_rx) launch_rx(sys->S, sys->R, sys->cap, -1, nullptr, nullptr);
+  CK(cudaStreamEndCapture(sys->cap, &g));
+  for (cudaGraph_t body : bodies) {
+    CK(cudaStreamBeginCaptureToGraph(sys->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_rebin(sys->S, sys->cap, 0, nullptr, nullptr);
+    cudaGraph_t tmp;
+    CK(cudaStreamEndCapture(sys->cap, &tmp));
+  }
+  CK(cudaGraphInstantiate(out, g, 0));
+  CK(cudaGraphDestroy(g));
+  return PRX_OK;
+}
+
+int ensure_graphs(prx_system* sys) {
+  if (sys->graphs_valid) return PRX_OK;
+  destroy_graphs(sys);
+  int rc;
+  if ((rc = build_graph(sys, 1, false, &sys->g_step))) return rc;
+  if (sys->has_rx) {
+    if ((rc = build_graph(sys, (int)sys->rxd.theta, true, &sys->g_chunk))) return rc;
+    if ((rc = build_graph(sys, 0, true, &sys->g_react))) return rc;
+  } else {
+    if ((rc = build_graph(sys, kNoRxChunk, false, &sys->g_chunk))) return rc;
+  }
+  sys->graphs_valid = true;
+  return PRX_OK;
+}
+
+// One step launched directly (profiling): the flag is read back after the
+// step to decide on the rebuild.
+int direct_step(prx_system* sys) {
+  prof_hook(sys, "step", 0);
+  launch_step(sys->S, sys->stream, sys->d.force_precision == PRX_FORCE_FP64, 0, 0, 0);
+  prof_hook(sys, "step", 1);
+  sys->step_launches++;
+  CK(cudaGetLastError());
+  int rc = read_ctl(sys);
+  if (rc) return rc;
+  if (sys->ctl_host->rebin_flag) launch_rebin(sys->S, sys->stream, 0, prof_hook, sys);
+  sys->host_step++;
+  if (sys->has_rx && sys->host_step % sys->rxd.theta == 0) {
+    launch_rx(sys->S, sys->R, sys->stream, -1, prof_hook, sys);
+    sys->other_launches += rx_kernel_count();
+  }
+  CK(cudaGetLastError());
+  return PRX_OK;
+}
+
+// Host copies of the current per-slot arrays.
+struct HostSlots {
+  std::vector<double> x, y, z, vx, vy, vz;
+  std::vector<uint32_t> id, adj;
+  std::vector<uint8_t> type, nadj;
+  std::vector<int8_t> state;
+  std::vector<int4> off;
+};
+
+int fetch_slots(prx_system* sys, HostSlots& h, bool pos, bool vel, bool topo) {
+  int rc = read_ctl(sys);
+  if (rc) return rc;
+  const size_t n = sys->S.n;
+  const SoA& B = sys->ctl_host->set ? sys->S.s1 : sys->S.s0;
+  h.id.resize(n);
+  if (n) CK(cudaMemcpyAsync(h.id.data(), B.id, 4 * n, cudaMemcpyDeviceToHost, sys->stream));
+  if (pos && n) {
+    h.x.resize(n); h.y.resize(n); h.z.resize(n);
+    CK(cudaMemcpyAsync(h.x.data(), B.x, 8 * n, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemcpyAsync(h.y.data(), B.y, 8 * n, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemcpyAsync(h.z.data(), B.z, 8 * n, cudaMemcpyDeviceToHost, sys->stream));
+  }
+  if (vel && n) {
+    h.vx.resize(n); h.vy.resize(n); h.vz.resize(n);
+    CK(cudaMemcpyAsync(h.vx.data(), B.vx, 8 * n, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemcpyAsync(h.vy.data(), B.vy, 8 * n, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemcpyAsync(h.vz.data(), B.vz, 8 * n, cudaMemcpyDeviceToHost, sys->stream));
+  }
+  if (topo && n) {
+    h.type.resize(n); h.state.resize(n); h.nadj.resize(n); h.adj.resize(n * sys->S.cap);
+    h.off.resize(n);
+    const int4* off = sys->ctl_host->phase ? sys->S.off1 : sys->S.off0;
+    CK(cudaMemcpyAsync(h.type.data(), B.type, n, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemcpyAsync(h.state.data(), B.state, n, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemcpyAsync(h.nadj.data(), B.nadj, n, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemcpyAsync(h.adj.data(), B.adj, 4 * n * sys->S.cap, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemcpyAsync(h.off.data(), off, sizeof(int4) * n, cudaMemcpyDeviceToHost, sys->stream));
+  }
+  CK(cudaStreamSynchronize(sys->stream));
+  return PRX_OK;
+}
+
+double wrap_host(double v, double L) {
+  if (v >= L) v -= L;
+  if (v < 0.0) v += L;
+  return v;
+}
+
+// Creates the device system from per-slot arrays.  `cells` (optional) gives
+// each slot's cell; without it the slots are binned from their positions.
+int create_impl(const prx_system_desc* desc, const double* pos, const double* vel,
+                const uint8_t* type, const int8_t* state, const prx_bond* bonds, uint64_t n_bonds,
+                void* stream, const uint32_t* slot_ids, const uint32_t* slot_cells,
+                const uint32_t* slot_adj_ids, const uint8_t* slot_nadj, uint64_t step0,
+                double grid_rc, prx_system** out) {
+  prx_system* sys = nullptr;
+  if (!out) return PRX_EINVAL;
+  *out = nullptr;
+  sys = new (std::nothrow) prx_system();
+  if (!sys) return PRX_ENOMEM;
+  auto bail = [&](int rc) {
+    if (rc) {
+      g_create_error = sys->err;
+      prx_destroy(sys);
+    }
+    return rc;
+  };
+  int rc = validate_desc(sys, desc);
+  if (rc) return bail(rc);
+  const uint32_t n = desc->n;
+  if (n && (!pos || !type || !state)) return bail(fail(sys, PRX_EINVAL, "pos, type and state are required"));
+  if (n_bonds && !bonds) return bail(fail(sys, PRX_EINVAL, "bonds is NULL"));
+  sys->d = *desc;
+  Sys& S = sys->S;
+  S.n = n;
+  S.cap = desc->adj_cap;
+  for (int k = 0; k < 3; ++k) {
+    S.L[k] = desc->box[k];
+    S.halfL[k] = 0.5 * desc->box[k];
+    S.Lf[k] = (float)desc->box[k];
+  }
+  const double rc_w = wca_rc(*desc);
+  S.rc = rc_w;
+  S.rc2 = rc_w * rc_w;
+  S.rcf = (float)rc_w;
+  S.rc2f = (float)S.rc2;
+  S.rc2pre = (float)((rc_w + 1e-3) * (rc_w + 1e-3));
+  S.sig = desc->wca_sigma;
+  S.sigf = (float)S.sig;
+  S.sig2 = desc->wca_sigma * desc->wca_sigma;
+  S.sig2f = (float)S.sig2;
+  S.eps24 = 24.0 * desc->wca_eps;
+  S.eps24f = (float)S.eps24;
+  S.eps4 = 4.0 * desc->wca_eps;
+  S.eps4f = (float)S.eps4;
+  S.fcap = desc->force_cap;
+  S.fcapf = (float)desc->force_cap;
+  S.fk = desc->fene_k;
+  S.fkf = (float)desc->fene_k;
+  S.fr02 = desc->fene_r0 * desc->fene_r0;
+  S.fr02f = (float)S.fr02;
+  S.dt = desc->dt;
+  S.mass = desc->mass;
+  S.b_kick = desc->dt / desc->mass;
+  S.b_kickf = (float)S.b_kick;
+  S.gm = desc->gamma * desc->mass;
+  S.a_fric = 1.0 - S.b_kick * S.gm;
+  S.cR = std::sqrt(24.0 * desc->gamma * desc->kT * desc->mass / desc->dt);
+  S.cRf = (float)S.cR;
+  S.thermo = desc->gamma > 0.0 ? 1 : 0;
+  S.seed = desc->seed;
+  S.hist_cap = kHistCap;
+  S.bond_cap = std::max<unsigned long long>(1ull, ((unsigned long long)n * S.cap) / 2ull);
+
+  if (stream) {
+    sys->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&sys->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(fail(sys, PRX_ECUDA, "stream creation failed"));
+    sys->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&sys->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(sys, PRX_ECUDA, "capture stream creation failed"));
+  if (cudaMallocHost(&sys->ctl_host, sizeof(Ctl)) != cudaSuccess)
+    return bail(fail(sys, PRX_ENOMEM, "pinned control block"));
+  memset(sys->ctl_host, 0, sizeof(Ctl));
+
+  auto& L = sys->dev_allocs;
+  SoA* sets[2] = {&S.s0, &S.s1};
+  for (SoA* B : sets) {
+    if ((rc = dalloc(sys, L, &B->x, n)) || (rc = dalloc(sys, L, &B->y, n)) || (rc = dalloc(sys, L, &B->z, n)) ||
+        (rc = dalloc(sys, L, &B->vx, n)) || (rc = dalloc(sys, L, &B->vy, n)) || (rc = dalloc(sys, L, &B->vz, n)) ||
+        (rc = dalloc(sys, L, &B->id, n)) || (rc = dalloc(sys, L, &B->type, n)) ||
+        (rc = dalloc(sys, L, &B->state, n)) || (rc = dalloc(sys, L, &B->nadj, n)) ||
+        (rc = dalloc(sys, L, &B->adj, (size_t)n * S.cap)))
+      return bail(rc);
+  }
+  if ((rc = dalloc(sys, L, &S.off0, n)) || (rc = dalloc(sys, L, &S.off1, n)) || (rc = dalloc(sys, L, &S.key, n)) ||
+      (rc = dalloc(sys, L, &S.tmp, n)) || (rc = dalloc(sys, L, &S.new_of_old, n)) ||
+      (rc = dalloc(sys, L, &S.slot_of_id, n)) || (rc = dalloc(sys, L, &S.win, n)) ||
+      (rc = dalloc(sys, L, &S.fin, n)) || (rc = dalloc(sys, L, &S.bonds, (size_t)S.bond_cap)) ||
+      (rc = dalloc(sys, L, &S.hist, (size_t)S.hist_cap + 1)) || (rc = dalloc(sys, L, &S.ctl, 1)) ||
+      (rc = dalloc(sys, L, &S.red, 4 * ((size_t)(n + RX_THREADS - 1) / RX_THREADS + 1))) ||
+      (rc = dalloc(sys, L, &S.fout, 3 * (size_t)n)) || (rc = dalloc(sys, L, &S.eout, (size_t)n)))
+    return bail(rc);
+  if ((rc = setup_grid(sys, grid_rc > rc_w ? grid_rc : rc_w))) return bail(rc);
+
+  // host staging in slot order
+  std::vector<uint32_t> ids(n);
+  for (uint32_t s = 0; s < n; ++s) ids[s] = slot_ids ? slot_ids[s] : s;
+  std::vector<uint32_t> slot_of(n, 0xFFFFFFFFu);
+  for (uint32_t s = 0; s < n; ++s) {
+    if (ids[s] >= n || slot_of[ids[s]] != 0xFFFFFFFFu) return bail(fail(sys, PRX_EINVAL, "bad slot order"));
+    slot_of[ids[s]] = s;
+  }
+  std::vector<double> hx(n), hy(n), hz(n), hvx(n, 0.0), hvy(n, 0.0), hvz(n, 0.0);
+  std::vector<uint8_t> ht(n), hn(n, 0);
+  std::vector<int8_t> hs(n);
+  std::vector<uint32_t> hadj((size_t)n * S.cap, 0u);
+  for (uint32_t s = 0; s < n; ++s) {
+    const uint32_t p = ids[s];
+    double c[3];
+    for (int k = 0; k < 3; ++k) {
+      const double v = pos[3 * (size_t)p + k];
+      if (!std::isfinite(v)) return bail(fail(sys, PRX_EINVAL, "non-finite position"));
+      c[k] = slot_cells ? v : wrap_host(v, desc->box[k]);
+      if (!slot_cells && !(c[k] >= 0.0 && c[k] < desc->box[k]))
+        return bail(fail(sys, PRX_EINVAL, "position more than one box edge outside the box"));
+    }
+    hx[s] = c[0];
+    hy[s] = c[1];
+    hz[s] = c[2];
+    if (vel) {
+      hvx[s] = vel[3 * (size_t)p];
+      hvy[s] = vel[3 * (size_t)p + 1];
+      hvz[s] = vel[3 * (size_t)p + 2];
+    }
+    if (type[p] >= PRX_MAX_TYPES) return bail(fail(sys, PRX_EINVAL, "type >= 8"));
+    ht[s] = type[p];
+    hs[s] = state[p];
+  }
+  if (slot_adj_ids) {
+    for (uint32_t s = 0; s < n; ++s) {
+      if (slot_nadj[s] > S.cap) return bail(fail(sys, PRX_ECAPACITY, "adjacency row beyond capacity"));
+      hn[s] = slot_nadj[s];
+      for (uint32_t b = 0; b < slot_nadj[s]; ++b) {
+        const uint32_t e = slot_adj_ids[(size_t)s * S.cap + b];
+        if ((e & SLOT_MASK) >= n) return bail(fail(sys, PRX_EINVAL, "bad adjacency entry"));
+        hadj[(size_t)s * S.cap + b] = slot_of[e & SLOT_MASK] | (e & ~SLOT_MASK);
+      }
+    }
+  } else {
+    for (uint64_t b = 0; b < n_bonds; ++b) {
+      const prx_bond& bd = bonds[b];
+      if (bd.a >= n || bd.t >= n || bd.a == bd.t || bd.style > 1u)
+        return bail(fail(sys, PRX_EINVAL, "bad initial bond"));
+      const uint32_t pa = slot_of[bd.a], pt = slot_of[bd.t];
+      if (hn[pa] >= S.cap || hn[pt] >= S.cap) return bail(fail(sys, PRX_ECAPACITY, "initial bonds exceed adj_cap"));
+      hadj[(size_t)pa * S.cap + hn[pa]++] = pt | (bd.style << 31);
+      hadj[(size_t)pt * S.cap + hn[pt]++] = pa | (bd.style << 31);
+    }
+  }
+  if (n_bonds > S.bond_cap) return bail(fail(sys, PRX_ECAPACITY, "more bonds than the bond list holds"));
+
+  const SoA& B = S.s0;
+  auto up = [&](void* dst, const void* src, size_t bytes) -> int {
+    if (!bytes) return PRX_OK;
+    if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, sys->stream) != cudaSuccess)
+      return fail(sys, PRX_ECUDA, "upload failed");
+    return PRX_OK;
+  };
+  if ((rc = up(B.x, hx.data(), 8ull * n)) || (rc = up(B.y, hy.data(), 8ull * n)) || (rc = up(B.z, hz.data(), 8ull * n)) ||
+      (rc = up(B.vx, hvx.data(), 8ull * n)) || (rc = up(B.vy, hvy.data(), 8ull * n)) ||
+      (rc = up(B.vz, hvz.data(), 8ull * n)) || (rc = up(B.id, ids.data(), 4ull * n)) ||
+      (rc = up(B.type, ht.data(), n)) || (rc = up(B.state, hs.data(), n)) || (rc = up(B.nadj, hn.data(), n)) ||
+      (rc = up(B.adj, hadj.data(), 4ull * n * S.cap)))
+    return bail(rc);
+  if (n_bonds) {
+    if ((rc = up(S.bonds, bonds, sizeof(prx_bond) * n_bonds))) return bail(rc);
+  }
+  Ctl c0;
+  memset(&c0, 0, sizeof(c0));
+  c0.nbonds = n_bonds;
+  c0.step = step0;
+  if ((rc = up(S.ctl, &c0, sizeof(Ctl)))) return bail(rc);
+  sys->host_step = step0;
+  if (cudaMemsetAsync(S.hist, 0, sizeof(HistRec) * (S.hist_cap + 1), sys->stream) != cudaSuccess)
+    return bail(fail(sys, PRX_ECUDA, "memset failed"));
+
+  if (slot_cells) {
+    // restore the saved cell of every slot: with the keys given, the counting
+    // sort keeps the slot order because the saved order is sorted by cell
+    for (uint32_t s = 0; s < n; ++s)
+      if (slot_cells[s] >= (uint32_t)S.ncell || (s && slot_cells[s] < slot_cells[s - 1]))
+        return bail(fail(sys, PRX_EINVAL, "checkpoint cells out of order"));
+    if ((rc = up(S.key, slot_cells, 4ull * n))) return bail(rc);
+  }
+  // bin into set 1 (full keys from positions, or the restored cells)
+  if ((rc = full_rebin(sys, slot_cells ? 2 : 1))) return bail(rc);
+  if ((rc = sync_status(sys))) return bail(rc);
+  *out = sys;
+  return PRX_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* prx_status_string(int st) {
+  switch (st) {
+    case PRX_OK: return "ok";
+    case PRX_EINVAL: return "invalid argument";
+    case PRX_ENOMEM: return "out of memory";
+    case PRX_ECAPACITY: return "capacity exceeded";
+    case PRX_EOVERSTRETCH: return "FENE bond overstretched";
+    case PRX_ENONFINITE: return "non-finite value or particle jump";
+    case PRX_ETIMEOUT: return "device wait timed out";
+    case PRX_ECUDA: return "CUDA error";
+    case PRX_EIO: return "I/O error";
+    default: return "unknown status";
+  }
+}
+
+// With sys == NULL: the message of the last failed prx_create / prx_load on this thread.
+const char* prx_last_error(const prx_system* sys) { return sys ? sys->err.c_str() : g_create_error.c_str(); }
+
+int prx_estimate_bytes(const prx_system_desc* desc, uint64_t* bytes) {
+  if (!desc || !bytes) return PRX_EINVAL;
+  const uint64_t n = desc->n, cap = desc->adj_cap ? desc->adj_cap : 1;
+  const double rc = std::pow(2.0, 1.0 / 6.0) * desc->wca_sigma;
+  const double skin = desc->skin < 0.0 ? kDefaultSkin : desc->skin;
+  uint64_t ncell = 1;
+  for (int k = 0; k < 3; ++k) {
+    int nc = (int)std::floor(desc->box[k] / (rc + skin));
+    nc = std::max(3, std::min(511, nc));
+    ncell *= (uint64_t)nc;
+  }
+  const uint64_t per_set = n * (6 * 8 + 4 + 3 + 4 * cap);
+  *bytes = 2 * per_set + n * (2 * 16 + 6 * 4) + (n * cap / 2 + 1) * sizeof(prx_bond) +
+           ncell * 12 + (kHistCap + 1ull) * sizeof(prx_history_record) + 4 * 8 * (n / 256 + 2);
+  return PRX_OK;
+}
+
+int prx_create(const prx_system_desc* desc, const double* pos, const double* vel, const uint8_t* type,
+               const int8_t* state, const prx_bond* bonds, uint64_t n_bonds, void* cuda_stream,
+               prx_system** out) {
+  return create_impl(desc, pos, vel, type, state, bonds, n_bonds, cuda_stream, nullptr, nullptr, nullptr,
+                     nullptr, 0, 0.0, out);
+}
+
+void prx_destroy(prx_system* sys) {
+  if (!sys) return;
+  if (sys->stream) cudaStreamSynchronize(sys->stream);
+  destroy_graphs(sys);
+  for (auto& e : sys->prof) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  free_list(sys->grid_allocs);
+  free_list(sys->dev_allocs);
+  if (sys->ctl_host) cudaFreeHost(sys->ctl_host);
+  if (sys->cap) cudaStreamDestroy(sys->cap);
+  if (sys->own_stream && sys->stream) cudaStreamDestroy(sys->stream);
+  delete sys;
+}
+
+int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx) {
+  if (!sys) return PRX_EINVAL;
+  if (!rx) {
+    sys->has_rx = 0;
+    destroy_graphs(sys);
+    return PRX_OK;
+  }
+  int rc = validate_rx(sys, rx);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(sys->stream));
+  sys->rxd = *rx;
+  RxParams& R = sys->R;
+  R.mask_A = rx->type_mask_A;
+  R.mask_T = rx->type_mask_T;
+  R.a_lo = rx->a_lo;
+  R.a_hi = rx->a_hi;
+  R.t_lo = rx->t_lo;
+  R.t_hi = rx->t_hi;
+  R.dA = rx->dA;
+  R.dT = rx->dT;
+  R.p = rx->k * sys->d.dt * (double)rx->theta;
+  R.rr2 = rx->r_react * rx->r_react;
+  R.rr2_pre = (float)((rx->r_react + 1e-3) * (rx->r_react + 1e-3));
+  R.style = (uint32_t)rx->bond_style;
+  for (int t = 0; t < PRX_MAX_TYPES; ++t) R.maxval[t] = rx->max_valence[t];
+  sys->has_rx = 1;
+  destroy_graphs(sys);
+  const double need = std::max(wca_rc(sys->d), rx->r_react);
+  if (need > sys->grid_rcut) {
+    if ((rc = setup_grid(sys, need))) return rc;
+    if ((rc = full_rebin(sys, 1))) return rc;
+    if ((rc = sync_status(sys))) return rc;
+  }
+  return PRX_OK;
+}
+
+int prx_run(prx_system* sys, uint64_t nsteps) {
+  if (!sys) return PRX_EINVAL;
+  if (sys->S.n == 0) {
+    sys->host_step += nsteps;
+    return PRX_OK;
+  }
+  if (sys->profiling) {
+    for (uint64_t q = 0; q < nsteps; ++q) {
+      int rc = direct_step(sys);
+      if (rc) return rc;
+    }
+    return PRX_OK;
+  }
+  int rc = ensure_graphs(sys);
+  if (rc) return rc;
+  const uint64_t theta = sys->has_rx ? sys->rxd.theta : (uint64_t)kNoRxChunk;
+  while (nsteps > 0) {
+    if (sys->host_step % theta == 0 && nsteps >= theta) {
+      CK(cudaGraphLaunch(sys->g_chunk, sys->stream));
+      sys->host_step += theta;
+      sys->step_launches += theta;
+      if (sys->has_rx) sys->graph_rx_launches++;
+      nsteps -= theta;
+    } else {
+      CK(cudaGraphLaunch(sys->g_step, sys->stream));
+      sys->host_step++;
+      sys->step_launches++;
+      nsteps--;
+      if (sys->has_rx && sys->host_step % theta == 0) {
+        CK(cudaGraphLaunch(sys->g_react, sys->stream));
+        sys->graph_rx_launches++;
+      }
+    }
+  }
+  return PRX_OK;
+}
+
+int prx_sync(prx_system* sys) {
+  if (!sys) return PRX_EINVAL;
+  return sync_status(sys);
+}
+
+int prx_react_once(prx_system* sys, uint64_t step, prx_rx_trace* trace) {
+  if (!sys) return PRX_EINVAL;
+  if (!sys->has_rx) return fail(sys, PRX_EINVAL, "no reaction scheme set");
+  if (sys->S.n) {
+    launch_rx(sys->S, sys->R, sys->stream, (long long)step, sys->profiling ? prof_hook : nullptr, sys);
+    sys->other_launches += rx_kernel_count();
+    CK(cudaGetLastError());
+  }
+  int rc = sync_status(sys);
+  if (trace) {
+    trace->candidates = sys->ctl_host->trace[0];
+    trace->retained = sys->ctl_host->trace[1];
+    trace->a_winners = sys->ctl_host->trace[2];
+    trace->formed = sys->ctl_host->trace[3];
+    if (!sys->S.n) memset(trace, 0, sizeof(*trace));
+  }
+  return rc;
+}
+
+int prx_compute_forces(prx_system* sys, double* f_out, double* epot_out) {
+  if (!sys || (!f_out && sys->S.n)) return PRX_EINVAL;
+  const size_t n = sys->S.n;
+  if (!n) {
+    if (epot_out) *epot_out = 0.0;
+    return PRX_OK;
+  }
+  launch_step(sys->S, sys->stream, sys->d.force_precision == PRX_FORCE_FP64, 1, 0, 0);
+  sys->other_launches++;
+  CK(cudaGetLastError());
+  std::vector<double> f(3 * n), e(n);
+  CK(cudaMemcpyAsync(f.data(), sys->S.fout, 24 * n, cudaMemcpyDeviceToHost, sys->stream));
+  CK(cudaMemcpyAsync(e.data(), sys->S.eout, 8 * n, cudaMemcpyDeviceToHost, sys->stream));
+  HostSlots h;
+  int rc = fetch_slots(sys, h, false, false, false);
+  if (rc) return rc;
+  std::vector<double> e_by_id(n);
+  for (size_t s = 0; s < n; ++s) {
+    const uint32_t p = h.id[s];
+    for (int k = 0; k < 3; ++k) f_out[3 * (size_t)p + k] = f[3 * s + k];
+    e_by_id[p] = e[s];
+  }
+  if (epot_out) {
+    double t = 0.0;
+    for (size_t p = 0; p < n; ++p) t += e_by_id[p];
+    *epot_out = t;
+  }
+  return sync_status(sys);
+}
+
+int prx_get_step(prx_system* sys, uint64_t* step) {
+  if (!sys || !step) return PRX_EINVAL;
+  int rc = sync_status(sys);
+  *step = sys->ctl_host->step;
+  return rc;
+}
+
+int prx_get_positions(prx_system* sys, double* out) {
+  if (!sys || (!out && sys->S.n)) return PRX_EINVAL;
+  HostSlots h;
+  int rc = fetch_slots(sys, h, true, false, false);
+  if (rc) return rc;
+  for (size_t s = 0; s < h.id.size(); ++s) {
+    const size_t p = h.id[s];
+    out[3 * p] = wrap_host(h.x[s], sys->d.box[0]);
+    out[3 * p + 1] = wrap_host(h.y[s], sys->d.box[1]);
+    out[3 * p + 2] = wrap_host(h.z[s], sys->d.box[2]);
+  }
+  return sync_status(sys);
+}
+
+int prx_get_velocities(prx_system* sys, double* out) {
+  if (!sys || (!out && sys->S.n)) return PRX_EINVAL;
+  HostSlots h;
+  int rc = fetch_slots(sys, h, false, true, false);
+  if (rc) return rc;
+  for (size_t s = 0; s < h.id.size(); ++s) {
+    const size_t p = h.id[s];
+    out[3 * p] = h.vx[s];
+    out[3 * p + 1] = h.vy[s];
+    out[3 * p + 2] = h.vz[s];
+  }
+  return sync_status(sys);
+}
+
+int prx_get_states(prx_system* sys, int8_t* out) {
+  if (!sys || (!out && sys->S.n)) return PRX_EINVAL;
+  HostSlots h;
+  int rc = fetch_slots(sys, h, false, false, true);
+  if (rc) return rc;
+  for (size_t s = 0; s < h.id.size(); ++s) out[h.id[s]] = h.state[s];
+  return sync_status(sys);
+}
+
+int prx_get_types(prx_system* sys, uint8_t* out) {
+  if (!sys || (!out && sys->S.n)) return PRX_EINVAL;
+  HostSlots h;
+  int rc = fetch_slots(sys, h, false, false, true);
+  if (rc) return rc;
+  for (size_t s = 0; s < h.id.size(); ++s) out[h.id[s]] = h.type[s];
+  return sync_status(sys);
+}
+
+int prx_get_bonds(prx_system* sys, prx_bond* out, uint64_t cap, uint64_t* n_out) {
+  if (!sys || !n_out) return PRX_EINVAL;
+  int rc = read_ctl(sys);
+  if (rc) return rc;
+  const uint64_t nb = sys->ctl_host->nbonds;
+  *n_out = nb;
+  std::vector<prx_bond> b(nb);
+  if (nb) {
+    CK(cudaMemcpyAsync(b.data(), sys->S.bonds, sizeof(prx_bond) * nb, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+  }
+  std::stable_sort(b.begin(), b.end(), [](const prx_bond& x, const prx_bond& y) {
+    if (x.step != y.step) return x.step < y.step;
+    if (x.a != y.a) return x.a < y.a;
+    return x.t < y.t;
+  });
+  const uint64_t m = std::min(cap, nb);
+  if (m && out) memcpy(out, b.data(), sizeof(prx_bond) * m);
+  rc = sync_status(sys);
+  if (rc) return rc;
+  return cap < nb ? fail(sys, PRX_ECAPACITY, "bond buffer too small") : PRX_OK;
+}
+
+int prx_get_observables(prx_system* sys, prx_observables* out) {
+  if (!sys || !out) return PRX_EINVAL;
+  memset(out, 0, sizeof(*out));
+  const uint32_t n = sys->S.n;
+  const int nblk = (int)((n + RX_THREADS - 1) / RX_THREADS);
+  if (n) {
+    launch_observables(sys->S, sys->stream, nblk);
+    sys->other_launches += 2;
+    CK(cudaGetLastError());
+    std::vector<double> red(4 * (size_t)nblk);
+    HistRec rec;
+    CK(cudaMemcpyAsync(red.data(), sys->S.red, sizeof(double) * red.size(), cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemcpyAsync(&rec, &sys->S.hist[sys->S.hist_cap], sizeof(HistRec), cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    for (int b = 0; b < nblk; ++b) {
+      out->ke_half += red[4 * b];
+      for (int k = 0; k < 3; ++k) out->momentum[k] += red[4 * b + 1 + k];
+    }
+    for (int t = 0; t < PRX_MAX_TYPES; ++t)
+      for (int s = 0; s < PRX_MAX_STATES; ++s) out->counts[t][s] = rec.counts[t][s];
+  }
+  int rc = sync_status(sys);
+  out->step = (int64_t)sys->ctl_host->step;
+  out->bonds = (int64_t)sys->ctl_host->nbonds;
+  return rc;
+}
+
+int prx_get_history(prx_system* sys, prx_history_record* out, uint64_t cap, uint64_t* n_out) {
+  if (!sys || !n_out) return PRX_EINVAL;
+  int rc = read_ctl(sys);
+  if (rc) return rc;
+  const uint64_t total = sys->ctl_host->hist_count;
+  const uint64_t kept = std::min<uint64_t>(total, sys->S.hist_cap);
+  const uint64_t m = std::min(cap, kept);
+  *n_out = m;
+  if (m && out) {
+    std::vector<HistRec> all(sys->S.hist_cap);
+    CK(cudaMemcpyAsync(all.data(), sys->S.hist, sizeof(HistRec) * sys->S.hist_cap, cudaMemcpyDeviceToHost,
+                       sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    const uint64_t first = total - m;
+    for (uint64_t q = 0; q < m; ++q) memcpy(&out[q], &all[(first + q) % sys->S.hist_cap], sizeof(HistRec));
+  }
+  return sync_status(sys);
+}
+
+int prx_get_stats(prx_system* sys, prx_stats* out) {
+  if (!sys || !out) return PRX_EINVAL;
+  int rc = read_ctl(sys);
+  if (rc) return rc;
+  memset(out, 0, sizeof(*out));
+  out->steps = sys->ctl_host->step;
+  out->reactions = sys->ctl_host->reactions;
+  out->rebins = sys->ctl_host->rebins;
+  out->step_launches = sys->step_launches;
+  // every rebuild, inside a graph's IF node or launched directly, is the same
+  // sequence of kernels and increments the device counter once
+  out->kernel_launches = sys->step_launches * (uint64_t)step_kernel_count(sys->d.force_precision) +
+                         sys->ctl_host->rebins * (uint64_t)rebin_kernel_count() +
+                         sys->graph_rx_launches * (uint64_t)rx_kernel_count() + sys->other_launches;
+  for (int k = 0; k < 3; ++k) {
+    out->cells[k] = (uint32_t)sys->S.nc[k];
+    out->cell_edge[k] = sys->d.box[k] / sys->S.nc[k];
+  }
+  return sync_status(sys);
+}
+
+int prx_profile_begin(prx_system* sys) {
+  if (!sys) return PRX_EINVAL;
+  CK(cudaStreamSynchronize(sys->stream));
+  for (auto& e : sys->prof) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  sys->prof.clear();
+  sys->profiling = true;
+  return PRX_OK;
+}
+
+int prx_profile_end(prx_system* sys, prx_kernel_time* out, uint32_t cap, uint32_t* n_out) {
+  if (!sys || !n_out) return PRX_EINVAL;
+  CK(cudaStreamSynchronize(sys->stream));
+  std::map<std::string, std::pair<uint64_t, double>> agg;
+  std::vector<std::string> order;
+  for (auto& e : sys->prof) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e.a, e.b);
+    if (!agg.count(e.name)) order.push_back(e.name);
+    agg[e.name].first += 1;
+    agg[e.name].second += ms;
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  sys->prof.clear();
+  sys->profiling = false;
+  *n_out = (uint32_t)order.size();
+  for (uint32_t q = 0; q < order.size() && q < cap && out; ++q) {
+    memset(&out[q], 0, sizeof(prx_kernel_time));
+    strncpy(out[q].name, order[q].c_str(), sizeof(out[q].name) - 1);
+    out[q].launches = agg[order[q]].first;
+    out[q].total_ms = agg[order[q]].second;
+  }
+  return sync_status(sys);
+}
+
+// Checkpoint: descriptor, reaction, step, then per-slot arrays in slot order
+// (ids, cells, positions, velocities, types, states, adjacency as partner
+// ids) and the bond list.  Restoring the slot order and the cell of every
+// slot makes the continued run identical bit for bit.
+int prx_save(prx_system* sys, const char* path) {
+  if (!sys || !path) return PRX_EINVAL;
+  HostSlots h;
+  int rc = fetch_slots(sys, h, true, true, true);
+  if (rc) return rc;
+  rc = sync_status(sys);
+  if (rc) return rc;
+  const uint64_t n = sys->S.n, cap = sys->S.cap, nb = sys->ctl_host->nbonds;
+  std::vector<prx_bond> bonds(nb);
+  if (nb) {
+    CK(cudaMemcpy(bonds.data(), sys->S.bonds, sizeof(prx_bond) * nb, cudaMemcpyDeviceToHost));
+  }
+  std::vector<uint32_t> cells(n), adj_ids(n * cap, 0u);
+  for (uint64_t s = 0; s < n; ++s) {
+    int cx, cy, cz;
+    const uint32_t w = (uint32_t)h.off[s].w;
+    cx = (int)(w & 511u);
+    cy = (int)((w >> 9) & 511u);
+    cz = (int)((w >> 18) & 511u);
+    cells[s] = (uint32_t)((cz * sys->S.nc[1] + cy) * sys->S.nc[0] + cx);
+    for (uint32_t b = 0; b < h.nadj[s]; ++b) {
+      const uint32_t e = h.adj[s * cap + b];
+      adj_ids[s * cap + b] = h.id[e & SLOT_MASK] | (e & ~SLOT_MASK);
+    }
+  }
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(sys, PRX_EIO, std::string("cannot open ") + path);
+  bool ok = true;
+  auto W = [&](const void* p, size_t sz) {
+    if (sz && fwrite(p, 1, sz, f) != sz) ok = false;
+  };
+  const uint64_t magic = kCkptMagic, step = sys->ctl_host->step;
+  W(&magic, 8);
+  W(&sys->d, sizeof(sys->d));
+  W(&sys->has_rx, sizeof(int));
+  W(&sys->rxd, sizeof(sys->rxd));
+  W(&step, 8);
+  W(&nb, 8);
+  W(&sys->grid_rcut, 8);
+  W(h.id.data(), 4 * n);
+  W(cells.data(), 4 * n);
+  W(h.x.data(), 8 * n);
+  W(h.y.data(), 8 * n);
+  W(h.z.data(), 8 * n);
+  W(h.vx.data(), 8 * n);
+  W(h.vy.data(), 8 * n);
+  W(h.vz.data(), 8 * n);
+  W(h.type.data(), n);
+  W(h.state.data(), n);
+  W(h.nadj.data(), n);
+  W(adj_ids.data(), 4 * n * cap);
+  W(bonds.data(), sizeof(prx_bond) * nb);
+  if (fclose(f) != 0) ok = false;
+  return ok ? PRX_OK : fail(sys, PRX_EIO, "write failed");
+}
+
+int prx_load(const char* path, void* cuda_stream, prx_system** out) {
+  if (!path || !out) return PRX_EINVAL;
+  FILE* f = fopen(path, "rb");
+  if (!f) return PRX_EIO;
+  bool ok = true;
+  auto R = [&](void* p, size_t sz) {
+    if (sz && fread(p, 1, sz, f) != sz) ok = false;
+  };
+  uint64_t magic = 0, step = 0, nb = 0;
+  prx_system_desc d;
+  prx_reaction_desc rxd;
+  int has_rx = 0;
+  double grid_rcut = 0.0;
+  R(&magic, 8);
+  if (!ok || magic != kCkptMagic) {
+    fclose(f);
+    return PRX_EIO;
+  }
+  R(&d, sizeof(d));
+  R(&has_rx, sizeof(int));
+  R(&rxd, sizeof(rxd));
+  R(&step, 8);
+  R(&nb, 8);
+  R(&grid_rcut, 8);
+  const uint64_t n = d.n, cap = d.adj_cap;
+  if (!ok || cap < 1 || cap > PRX_MAX_ADJ || n > 0x7FFFFFF0ull) {
+    fclose(f);
+    return PRX_EIO;
+  }
+  std::vector<uint32_t> ids(n), cells(n), adj_ids(n * cap);
+  std::vector<double> x(n), y(n), z(n), vx(n), vy(n), vz(n), pos(3 * n), vel(3 * n);
+  std::vector<uint8_t> type(n), nadj(n), type_id(n);
+  std::vector<int8_t> state(n), state_id(n);
+  std::vector<prx_bond> bonds(nb);
+  R(ids.data(), 4 * n);
+  R(cells.data(), 4 * n);
+  R(x.data(), 8 * n);
+  R(y.data(), 8 * n);
+  R(z.data(), 8 * n);
+  R(vx.data(), 8 * n);
+  R(vy.data(), 8 * n);
+  R(vz.data(), 8 * n);
+  R(type.data(), n);
+  R(state.data(), n);
+  R(nadj.data(), n);
+  R(adj_ids.data(), 4 * n * cap);
+  R(bonds.data(), sizeof(prx_bond) * nb);
+  fclose(f);
+  if (!ok) return PRX_EIO;
+  for (uint64_t s = 0; s < n; ++s) {
+    const uint32_t p = ids[s];
+    if (p >= n) return PRX_EIO;
+    pos[3 * p] = x[s];
+    pos[3 * p + 1] = y[s];
+    pos[3 * p + 2] = z[s];
+    vel[3 * p] = vx[s];
+    vel[3 * p + 1] = vy[s];
+    vel[3 * p + 2] = vz[s];
+    type_id[p] = type[s];
+    state_id[p] = state[s];
+  }
+  // recreate with the reaction's grid so that the saved cells are valid
+  prx_system* sys = nullptr;
+  int rc = create_impl(&d, pos.data(), vel.data(), type_id.data(), state_id.data(), bonds.data(), nb, cuda_stream,
+                       ids.data(), cells.data(), adj_ids.data(), nadj.data(), step, grid_rcut, &sys);
+  if (rc) return rc;
+  if (has_rx) {
+    rc = prx_set_reaction(sys, &rxd);
+    if (rc) {
+      prx_destroy(sys);
+      return rc;
+    }
+  }
+  *out = sys;
+  return PRX_OK;
+}
+
+}  // extern "C"

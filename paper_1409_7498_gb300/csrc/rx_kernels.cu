@@ -1,0 +1,386 @@
+// Reaction step (Sec. III, Table I) and observables.
+//
+// The three selection stages are atomic-free and independent of thread
+// scheduling: every random choice is the minimum of Philox keys that depend
+// only on (seed, step, particle ids), so the outcome is a function of the
+// state alone.
+//   rx_find      steps 1-5: each eligible A scans its 27 neighbour cells for
+//                eligible T (type mask, state window, not yet bonded to A) with
+//                r^2 < r_react^2 tested in FP64 on absolute positions (after an
+//                FP32 prefilter that can only widen the set), accepts each with
+//                u < k dt Theta (Eq. 4) and keeps the accepted T of smallest
+//                key Philox(step, id_A, id_T): one T per A.
+//   rx_select_T  steps 6-7: each A winner scans the cells around its T for the
+//                other A's that picked the same T and keeps the pair only if
+//                its key Philox(step, id_T, id_A) is the smallest: one A per T.
+//   rx_scan      offsets of the surviving pairs in the bond list (block
+//                counts scanned in one block: ordered by slot, no atomics).
+//   rx_apply     step 9: append the bonds, both adjacency rows, shift states.
+//   obs_hist     populations per (type, state) into the history ring.
+#include <cuda_runtime.h>
+
+#include "prx_internal.cuh"
+
+namespace prx {
+
+namespace {
+
+__device__ __forceinline__ bool in_window(uint32_t mask, int lo, int hi, uint32_t t, int s) {
+  return ((mask >> t) & 1u) && s >= lo && s <= hi;
+}
+
+__device__ __forceinline__ unsigned long long key64(uint4 w) {
+  return ((unsigned long long)w.x << 32) | w.y;
+}
+
+__device__ __forceinline__ bool last_block_rx(unsigned int* counter) {
+  __shared__ bool is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  return is_last && threadIdx.x == 0;
+}
+
+__device__ __forceinline__ long long block_sum_ll(long long v) {
+  __shared__ long long part[RX_THREADS / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) part[wid] = v;
+  __syncthreads();
+  long long t = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < RX_THREADS / 32; ++w) t += part[w];
+  return t;
+}
+
+__global__ void __launch_bounds__(RX_THREADS) k_rx_find(Sys S, RxParams R, long long step_arg) {
+  Ctl* ctl = S.ctl;
+  const unsigned long long step = step_arg >= 0 ? (unsigned long long)step_arg : ctl->step;
+  const SoA B = ctl->set ? S.s1 : S.s0;
+  const int4* off = ctl->phase ? S.off1 : S.off0;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  long long ncand = 0, nret = 0;
+  if (i < S.n) {
+    uint32_t best = NONE;
+    const uint32_t ti = B.type[i];
+    const int si = B.state[i];
+    if (in_window(R.mask_A, R.a_lo, R.a_hi, ti, si)) {
+      const int4 oi = off[i];
+      int cx, cy, cz;
+      unpack_cell((uint32_t)oi.w, cx, cy, cz);
+      const double xi = B.x[i], yi = B.y[i], zi = B.z[i];
+      const uint32_t idi = B.id[i];
+      const uint32_t nb = B.nadj[i];
+      unsigned long long bestkey = 0ull;
+      uint32_t bestid = 0u;
+      for (int dz = -1; dz <= 1; ++dz) {
+        int qz = cz + dz;
+        uint32_t shz = (uint32_t)(dz * S.H29[2]);
+        if (qz < 0) { qz += S.nc[2]; shz -= (uint32_t)S.corr29[2]; }
+        else if (qz >= S.nc[2]) { qz -= S.nc[2]; shz += (uint32_t)S.corr29[2]; }
+        for (int dy = -1; dy <= 1; ++dy) {
+          int qy = cy + dy;
+          uint32_t shy = (uint32_t)(dy * S.H29[1]);
+          if (qy < 0) { qy += S.nc[1]; shy -= (uint32_t)S.corr29[1]; }
+          else if (qy >= S.nc[1]) { qy -= S.nc[1]; shy += (uint32_t)S.corr29[1]; }
+          const int rowbase = (qz * S.nc[1] + qy) * S.nc[0];
+          for (int dx = -1; dx <= 1; ++dx) {
+            int qx = cx + dx;
+            uint32_t shx = (uint32_t)(dx * S.H29[0]);
+            if (qx < 0) { qx += S.nc[0]; shx -= (uint32_t)S.corr29[0]; }
+            else if (qx >= S.nc[0]) { qx -= S.nc[0]; shx += (uint32_t)S.corr29[0]; }
+            const int q = rowbase + qx;
+            const uint32_t s0 = S.cell_start[q], s1 = S.cell_start[q + 1];
+            for (uint32_t j = s0; j < s1; ++j) {
+              if (j == i) continue;
+              if (!in_window(R.mask_T, R.t_lo, R.t_hi, B.type[j], B.state[j])) continue;
+              // FP32 prefilter on the exact fixed-point displacement: it can only
+              // widen the set that the exact FP64 test below decides on
+              const int4 oj = off[j];
+              const float ex = fx29_to_float((int)((uint32_t)oj.x - (uint32_t)oi.x + shx));
+              const float ey = fx29_to_float((int)((uint32_t)oj.y - (uint32_t)oi.y + shy));
+              const float ez = fx29_to_float((int)((uint32_t)oj.z - (uint32_t)oi.z + shz));
+              if (!(fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < R.rr2_pre)) continue;
+              // exact test, Table I step 1: d = x_T - x_A under the minimum image,
+              // r^2 = fma(dz, dz, fma(dy, dy, dx dx)), strict r^2 < r_react^2
+              const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
+              const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
+              const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
+              const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
+              if (!(r2 < R.rr2)) continue;
+              bool bonded = false;
+              for (uint32_t b = 0; b < nb; ++b)
+                bonded |= (B.adj[(size_t)i * S.cap + b] & SLOT_MASK) == j;
+              if (bonded) continue;
+              ++ncand;
+              const uint32_t idj = B.id[j];
+              // step 2: retained when u < k dt Theta (Eq. 4)
+              const uint4 wa = keyed_draw(S.seed, step, idi, idj, TAG_ACCEPT);
+              if (!(u53(wa.x, wa.y) < R.p)) continue;
+              ++nret;
+              // step 5: one T per A, uniformly at random
+              const unsigned long long k = key64(keyed_draw(S.seed, step, idi, idj, TAG_SEL_A));
+              if (best == NONE || k < bestkey || (k == bestkey && idj < bestid)) {
+                best = j;
+                bestkey = k;
+                bestid = idj;
+              }
+            }
+          }
+        }
+      }
+    }
+    S.win[i] = best;
+  }
+  const long long c = block_sum_ll(ncand);
+  const long long r = block_sum_ll(nret);
+  if (threadIdx.x == 0 && (c | r)) {
+    atomicAdd((unsigned long long*)&ctl->trace[0], (unsigned long long)c);
+    atomicAdd((unsigned long long*)&ctl->trace[1], (unsigned long long)r);
+  }
+}
+
+__global__ void __launch_bounds__(RX_THREADS) k_rx_select_T(Sys S, long long step_arg) {
+  Ctl* ctl = S.ctl;
+  const unsigned long long step = step_arg >= 0 ? (unsigned long long)step_arg : ctl->step;
+  const SoA B = ctl->set ? S.s1 : S.s0;
+  const int4* off = ctl->phase ? S.off1 : S.off0;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t fin = NONE;
+  bool winner = false;
+  if (i < S.n) {
+    const uint32_t T = S.win[i];
+    if (T != NONE) {
+      winner = true;
+      const uint32_t idi = B.id[i], idT = B.id[T];
+      const unsigned long long mine = key64(keyed_draw(S.seed, step, idT, idi, TAG_SEL_T));
+      bool keep = true;
+      int cx, cy, cz;
+      unpack_cell((uint32_t)off[T].w, cx, cy, cz);
+      for (int dz = -1; dz <= 1 && keep; ++dz) {
+        const int qz = wrap_cell(cz + dz, S.nc[2]);
+        for (int dy = -1; dy <= 1 && keep; ++dy) {
+          const int qy = wrap_cell(cy + dy, S.nc[1]);
+          const int rowbase = (qz * S.nc[1] + qy) * S.nc[0];
+          for (int dx = -1; dx <= 1 && keep; ++dx) {
+            const int q = rowbase + wrap_cell(cx + dx, S.nc[0]);
+            const uint32_t s0 = S.cell_start[q], s1 = S.cell_start[q + 1];
+            for (uint32_t k = s0; k < s1; ++k) {
+              if (k == i || S.win[k] != T) continue;
+              const uint32_t idk = B.id[k];
+              const unsigned long long other = key64(keyed_draw(S.seed, step, idT, idk, TAG_SEL_T));
+              if (other < mine || (other == mine && idk < idi)) {
+                keep = false;
+                break;
+              }
+            }
+          }
+        }
+      }
+      if (keep) fin = T;
+    }
+    S.fin[i] = fin;
+  }
+  const int nfin = __syncthreads_count(fin != NONE);
+  const int nwin = __syncthreads_count(winner);
+  if (threadIdx.x == 0) {
+    S.blk_count[blockIdx.x] = (uint32_t)nfin;
+    if (nwin) atomicAdd((unsigned long long*)&ctl->trace[2], (unsigned long long)nwin);
+  }
+}
+
+// One block: exclusive scan of the per-block counts, bond-list base, and a
+// cleared history record for this reaction step.
+__global__ void k_rx_scan(Sys S, uint32_t nblk) {
+  Ctl* ctl = S.ctl;
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t carry_s;
+  if (threadIdx.x == 0) carry_s = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint32_t base = 0; base < nblk; base += blockDim.x) {
+    const uint32_t idx = base + threadIdx.x;
+    const uint32_t v = idx < nblk ? S.blk_count[idx] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (int w = 0; w < nw; ++w) {
+        const uint32_t t = warp_tot[w];
+        warp_tot[w] = run;
+        run += t;
+      }
+    }
+    __syncthreads();
+    if (idx < nblk) S.blk_off[idx] = carry_s + warp_tot[wid] + x - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry_s += warp_tot[wid] + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long total = carry_s;
+    const unsigned long long base = ctl->nbonds;
+    ctl->rx_base = base;
+    if (base + total > S.bond_cap) {
+      set_status(ctl, PRX_ECAPACITY);
+      ctl->nbonds = S.bond_cap;
+    } else {
+      ctl->nbonds = base + total;
+    }
+    ctl->trace[3] = (long long)total;
+  }
+  // clear the history record this reaction will fill
+  HistRec* rec = &S.hist[ctl->hist_count % S.hist_cap];
+  int32_t* cnt = &rec->counts[0][0];
+  for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x) cnt[k] = 0;
+}
+
+__global__ void __launch_bounds__(RX_THREADS) k_rx_apply(Sys S, RxParams R, long long step_arg) {
+  Ctl* ctl = S.ctl;
+  const unsigned long long step = step_arg >= 0 ? (unsigned long long)step_arg : ctl->step;
+  const SoA B = ctl->set ? S.s1 : S.s0;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t T = i < S.n ? S.fin[i] : NONE;
+  const bool has = T != NONE;
+  // rank of this pair among the block's pairs (ballot + warp prefix)
+  __shared__ uint32_t wcount[RX_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t bal = __ballot_sync(0xFFFFFFFFu, has);
+  if (lane == 0) wcount[wid] = __popc(bal);
+  __syncthreads();
+  uint32_t before = 0;
+  for (int w = 0; w < wid; ++w) before += wcount[w];
+  const uint32_t rank = before + __popc(bal & ((1u << lane) - 1u));
+  if (!has) return;
+  const unsigned long long pos = ctl->rx_base + S.blk_off[blockIdx.x] + rank;
+  const uint32_t ta = B.type[i], tt = B.type[T];
+  const uint32_t capA = R.maxval[ta] < S.cap ? R.maxval[ta] : S.cap;
+  const uint32_t capT = R.maxval[tt] < S.cap ? R.maxval[tt] : S.cap;
+  const uint32_t na = B.nadj[i], nt = B.nadj[T];
+  if (na >= capA || nt >= capT || pos >= S.bond_cap) {
+    set_status(ctl, PRX_ECAPACITY);
+    return;
+  }
+  const uint32_t sbit = R.style << 31;
+  B.adj[(size_t)i * S.cap + na] = T | sbit;
+  B.nadj[i] = (uint8_t)(na + 1);
+  B.adj[(size_t)T * S.cap + nt] = i | sbit;
+  B.nadj[T] = (uint8_t)(nt + 1);
+  B.state[i] = (int8_t)(B.state[i] + R.dA);
+  B.state[T] = (int8_t)(B.state[T] + R.dT);
+  BondRec rec;
+  rec.a = B.id[i];
+  rec.t = B.id[T];
+  rec.step = (int64_t)step;
+  rec.style = R.style;
+  rec.reserved = 0u;
+  S.bonds[pos] = rec;
+}
+
+// Populations per (type, state) into history record hist_count % hist_cap
+// (integer atomics: the counts do not depend on their order).
+__global__ void __launch_bounds__(RX_THREADS) k_obs_hist(Sys S, long long step_arg, int record) {
+  Ctl* ctl = S.ctl;
+  const SoA B = ctl->set ? S.s1 : S.s0;
+  __shared__ int32_t h[PRX_MAX_TYPES * PRX_MAX_STATES];
+  for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x) h[k] = 0;
+  __syncthreads();
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < S.n) {
+    const uint32_t t = B.type[i];
+    const int s = B.state[i];
+    if (t < PRX_MAX_TYPES && s >= 0 && s < PRX_MAX_STATES) atomicAdd(&h[t * PRX_MAX_STATES + s], 1);
+  }
+  __syncthreads();
+  const unsigned long long slot = record ? ctl->hist_count % S.hist_cap : S.hist_cap;
+  HistRec* rec = &S.hist[slot];
+  for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x)
+    if (h[k]) atomicAdd(&rec->counts[0][0] + k, h[k]);
+  if (last_block_rx(&ctl->done_obs)) {
+    ctl->done_obs = 0u;
+    rec->step = step_arg >= 0 ? step_arg : (long long)ctl->step;
+    rec->bonds = (long long)ctl->nbonds;
+    if (record) {
+      ctl->hist_count += 1ull;
+      ctl->reactions += 1ull;
+    }
+  }
+}
+
+// Per-block FP64 partial sums of m v^2 / 2 and m v (fixed-order tree).
+__global__ void __launch_bounds__(RX_THREADS) k_obs_sums(Sys S, double mass) {
+  Ctl* ctl = S.ctl;
+  const SoA B = ctl->set ? S.s1 : S.s0;
+  __shared__ double red[4][RX_THREADS];
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  double ke = 0.0, px = 0.0, py = 0.0, pz = 0.0;
+  if (i < S.n) {
+    const double vx = B.vx[i], vy = B.vy[i], vz = B.vz[i];
+    ke = 0.5 * mass * (vx * vx + vy * vy + vz * vz);
+    px = mass * vx;
+    py = mass * vy;
+    pz = mass * vz;
+  }
+  red[0][threadIdx.x] = ke;
+  red[1][threadIdx.x] = px;
+  red[2][threadIdx.x] = py;
+  red[3][threadIdx.x] = pz;
+  __syncthreads();
+  for (int w = RX_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) S.red[4 * (size_t)blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+inline unsigned blocks_rx(uint32_t n) { return n ? (n + RX_THREADS - 1) / RX_THREADS : 1u; }
+
+}  // namespace
+
+int rx_kernel_count() { return 5; }
+
+void launch_rx(const Sys& S, const RxParams& R, cudaStream_t st, long long step_arg,
+               void (*hook)(void*, const char*, int), void* ctx) {
+  const unsigned g = blocks_rx(S.n);
+  auto H = [&](const char* nm, int p) {
+    if (hook) hook(ctx, nm, p);
+  };
+  cudaMemsetAsync(&S.ctl->trace[0], 0, sizeof(long long) * 4, st);
+  H("rx_find", 0);
+  k_rx_find<<<g, RX_THREADS, 0, st>>>(S, R, step_arg);
+  H("rx_find", 1);
+  H("rx_select_T", 0);
+  k_rx_select_T<<<g, RX_THREADS, 0, st>>>(S, step_arg);
+  H("rx_select_T", 1);
+  H("rx_scan", 0);
+  k_rx_scan<<<1, 1024, 0, st>>>(S, g);
+  H("rx_scan", 1);
+  H("rx_apply", 0);
+  k_rx_apply<<<g, RX_THREADS, 0, st>>>(S, R, step_arg);
+  H("rx_apply", 1);
+  H("obs_hist", 0);
+  k_obs_hist<<<g, RX_THREADS, 0, st>>>(S, step_arg, 1);
+  H("obs_hist", 1);
+}
+
+// On-demand observables: the spare history slot (index hist_cap) receives the
+// populations; S.red the per-block sums.
+void launch_observables(const Sys& S, cudaStream_t st, int nblocks) {
+  cudaMemsetAsync(&S.hist[S.hist_cap], 0, sizeof(HistRec), st);
+  k_obs_hist<<<nblocks, RX_THREADS, 0, st>>>(S, -1, 0);
+  k_obs_sums<<<nblocks, RX_THREADS, 0, st>>>(S, S.mass);
+}
+
+}  // namespace prx

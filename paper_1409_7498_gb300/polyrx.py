@@ -1,0 +1,381 @@
+"""Python binding of the polyrx C ABI (include/polyrx.h): argument marshalling only.
+
+Every function keeps the C name and forwards to libpolyrx.so, which runs the
+whole path in hand-written CUDA kernels.  There is no CPU fallback: if the
+library is missing or fails to load, the import-time call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpolyrx.so")
+
+PRX_OK = 0
+PRX_EINVAL, PRX_ENOMEM, PRX_ECAPACITY, PRX_EOVERSTRETCH = -1, -2, -3, -4
+PRX_ENONFINITE, PRX_ETIMEOUT, PRX_ECUDA, PRX_EIO = -5, -6, -7, -8
+PRX_BOND_FENE, PRX_BOND_MIRROR_LJ = 0, 1
+PRX_FORCE_FP32, PRX_FORCE_FP64 = 0, 1
+PRX_MAX_TYPES, PRX_MAX_STATES, PRX_MAX_ADJ = 8, 16, 8
+
+
+class PolyrxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"polyrx status {code}: {msg}")
+        self.code = code
+
+
+class prx_system_desc(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("adj_cap", C.c_uint32), ("box", C.c_double * 3),
+                ("dt", C.c_double), ("kT", C.c_double), ("gamma", C.c_double),
+                ("mass", C.c_double), ("wca_eps", C.c_double), ("wca_sigma", C.c_double),
+                ("fene_k", C.c_double), ("fene_r0", C.c_double), ("force_cap", C.c_double),
+                ("skin", C.c_double), ("force_precision", C.c_int32), ("reserved", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
+class prx_reaction_desc(C.Structure):
+    _fields_ = [("type_mask_A", C.c_uint32), ("type_mask_T", C.c_uint32), ("a_lo", C.c_int32),
+                ("a_hi", C.c_int32), ("t_lo", C.c_int32), ("t_hi", C.c_int32), ("dA", C.c_int32),
+                ("dT", C.c_int32), ("k", C.c_double), ("r_react", C.c_double),
+                ("theta", C.c_uint32), ("bond_style", C.c_int32),
+                ("max_valence", C.c_uint8 * PRX_MAX_TYPES)]
+
+
+class prx_bond(C.Structure):
+    _fields_ = [("a", C.c_uint32), ("t", C.c_uint32), ("step", C.c_int64), ("style", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+BOND_DTYPE = np.dtype([("a", "<u4"), ("t", "<u4"), ("step", "<i8"), ("style", "<u4"),
+                       ("reserved", "<u4")])
+
+
+class prx_rx_trace(C.Structure):
+    _fields_ = [("candidates", C.c_int64), ("retained", C.c_int64), ("a_winners", C.c_int64),
+                ("formed", C.c_int64)]
+
+
+class prx_observables(C.Structure):
+    _fields_ = [("step", C.c_int64), ("bonds", C.c_int64),
+                ("counts", (C.c_int64 * PRX_MAX_STATES) * PRX_MAX_TYPES),
+                ("ke_half", C.c_double), ("momentum", C.c_double * 3)]
+
+
+HISTORY_DTYPE = np.dtype([("step", "<i8"), ("bonds", "<i8"),
+                          ("counts", "<i4", (PRX_MAX_TYPES, PRX_MAX_STATES))])
+
+
+class prx_stats(C.Structure):
+    _fields_ = [("steps", C.c_uint64), ("reactions", C.c_uint64), ("rebins", C.c_uint64),
+                ("step_launches", C.c_uint64), ("kernel_launches", C.c_uint64),
+                ("cells", C.c_uint32 * 3), ("cell_edge", C.c_double * 3)]
+
+
+class prx_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libpolyrx.so (built by paper_1409_7498_gb300.build); raises when absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_1409_7498_gb300.build.build() first")
+    L = C.CDLL(LIB_PATH)
+    P, VP, U64, I = C.POINTER, C.c_void_p, C.c_uint64, C.c_int
+    sig = {
+        "prx_create": ([P(prx_system_desc), VP, VP, VP, VP, VP, U64, VP, P(VP)], I),
+        "prx_destroy": ([VP], None),
+        "prx_estimate_bytes": ([P(prx_system_desc), P(U64)], I),
+        "prx_set_reaction": ([VP, P(prx_reaction_desc)], I),
+        "prx_run": ([VP, U64], I),
+        "prx_sync": ([VP], I),
+        "prx_react_once": ([VP, U64, P(prx_rx_trace)], I),
+        "prx_compute_forces": ([VP, VP, P(C.c_double)], I),
+        "prx_get_step": ([VP, P(U64)], I),
+        "prx_get_positions": ([VP, VP], I),
+        "prx_get_velocities": ([VP, VP], I),
+        "prx_get_states": ([VP, VP], I),
+        "prx_get_types": ([VP, VP], I),
+        "prx_get_bonds": ([VP, VP, U64, P(U64)], I),
+        "prx_get_observables": ([VP, P(prx_observables)], I),
+        "prx_get_history": ([VP, VP, U64, P(U64)], I),
+        "prx_get_stats": ([VP, P(prx_stats)], I),
+        "prx_save": ([VP, C.c_char_p], I),
+        "prx_load": ([C.c_char_p, VP, P(VP)], I),
+        "prx_profile_begin": ([VP], I),
+        "prx_profile_end": ([VP, P(prx_kernel_time), C.c_uint32, P(C.c_uint32)], I),
+        "prx_last_error": ([VP], C.c_char_p),
+        "prx_status_string": ([I], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(rc: int, handle=None):
+    if rc != PRX_OK:
+        msg = lib().prx_last_error(handle)
+        raise PolyrxError(rc, (msg or b"").decode() or lib().prx_status_string(rc).decode())
+
+
+def make_desc(n, box, *, adj_cap=4, dt=0.005, kT=1.0, gamma=1.0, mass=1.0, wca_eps=1.0,
+              wca_sigma=1.0, fene_k=30.0, fene_r0=1.5, force_cap=0.0, skin=-1.0, fp64=False,
+              seed=14097498) -> prx_system_desc:
+    b = (box,) * 3 if np.isscalar(box) else tuple(box)
+    return prx_system_desc(int(n), int(adj_cap), (C.c_double * 3)(*map(float, b)), dt, kT, gamma,
+                           mass, wca_eps, wca_sigma, fene_k, fene_r0, force_cap, skin,
+                           PRX_FORCE_FP64 if fp64 else PRX_FORCE_FP32, 0,
+                           int(seed) & 0xFFFFFFFFFFFFFFFF)
+
+
+def make_reaction(mask_A, mask_T, a_lo, a_hi, t_lo, t_hi, dA, dT, k, theta=10, r_react=1.1,
+                  bond_style=PRX_BOND_FENE, max_valence=(8,) * 8) -> prx_reaction_desc:
+    mv = list(max_valence) + [0] * (8 - len(max_valence))
+    return prx_reaction_desc(mask_A, mask_T, a_lo, a_hi, t_lo, t_hi, dA, dT, float(k),
+                             float(r_react), int(theta), int(bond_style),
+                             (C.c_uint8 * 8)(*mv[:8]))
+
+
+# ---- the C entry points -----------------------------------------------------
+
+def prx_create(desc: prx_system_desc, pos, vel, type_, state, bonds=None, stream=None):
+    n = desc.n
+    pos = np.ascontiguousarray(pos, np.float64).reshape(n, 3)
+    vel = None if vel is None else np.ascontiguousarray(vel, np.float64).reshape(n, 3)
+    type_ = np.ascontiguousarray(type_, np.uint8)
+    state = np.ascontiguousarray(state, np.int8)
+    nb = 0
+    if bonds is not None and len(bonds):
+        bonds = np.ascontiguousarray(bonds, BOND_DTYPE)
+        nb = len(bonds)
+    else:
+        bonds = None
+    out = C.c_void_p()
+    rc = lib().prx_create(C.byref(desc), _ptr(pos), _ptr(vel), _ptr(type_), _ptr(state),
+                          _ptr(bonds), nb, C.c_void_p(stream) if stream else None, C.byref(out))
+    _check(rc, None)
+    return out
+
+
+def prx_destroy(h):
+    lib().prx_destroy(h)
+
+
+def prx_estimate_bytes(desc: prx_system_desc) -> int:
+    b = C.c_uint64()
+    _check(lib().prx_estimate_bytes(C.byref(desc), C.byref(b)))
+    return b.value
+
+
+def prx_set_reaction(h, rx):
+    _check(lib().prx_set_reaction(h, C.byref(rx) if rx is not None else None), h)
+
+
+def prx_run(h, nsteps: int):
+    _check(lib().prx_run(h, int(nsteps)), h)
+
+
+def prx_sync(h):
+    _check(lib().prx_sync(h), h)
+
+
+def prx_react_once(h, step: int) -> dict:
+    t = prx_rx_trace()
+    _check(lib().prx_react_once(h, int(step), C.byref(t)), h)
+    return dict(candidates=t.candidates, retained=t.retained, a_winners=t.a_winners,
+                formed=t.formed)
+
+
+def prx_compute_forces(h, n: int):
+    f = np.zeros((n, 3), np.float64)
+    e = C.c_double()
+    _check(lib().prx_compute_forces(h, _ptr(f), C.byref(e)), h)
+    return f, e.value
+
+
+def prx_get_step(h) -> int:
+    s = C.c_uint64()
+    _check(lib().prx_get_step(h, C.byref(s)), h)
+    return s.value
+
+
+def prx_get_positions(h, n: int):
+    out = np.zeros((n, 3), np.float64)
+    _check(lib().prx_get_positions(h, _ptr(out)), h)
+    return out
+
+
+def prx_get_velocities(h, n: int):
+    out = np.zeros((n, 3), np.float64)
+    _check(lib().prx_get_velocities(h, _ptr(out)), h)
+    return out
+
+
+def prx_get_states(h, n: int):
+    out = np.zeros(n, np.int8)
+    _check(lib().prx_get_states(h, _ptr(out)), h)
+    return out
+
+
+def prx_get_types(h, n: int):
+    out = np.zeros(n, np.uint8)
+    _check(lib().prx_get_types(h, _ptr(out)), h)
+    return out
+
+
+def prx_get_bonds(h):
+    n = C.c_uint64()
+    rc = lib().prx_get_bonds(h, None, 0, C.byref(n))
+    if rc not in (PRX_OK, PRX_ECAPACITY):
+        _check(rc, h)
+    out = np.zeros(n.value, BOND_DTYPE)
+    _check(lib().prx_get_bonds(h, _ptr(out), n.value, C.byref(n)), h)
+    return out
+
+
+def prx_get_observables(h) -> dict:
+    o = prx_observables()
+    _check(lib().prx_get_observables(h, C.byref(o)), h)
+    return dict(step=o.step, bonds=o.bonds,
+                counts=np.array([[o.counts[t][s] for s in range(16)] for t in range(8)], np.int64),
+                ke_half=o.ke_half, momentum=np.array(list(o.momentum)))
+
+
+def prx_get_history(h, cap: int = 1 << 20):
+    n = C.c_uint64()
+    _check(lib().prx_get_history(h, None, 0, C.byref(n)), h)
+    out = np.zeros(cap, HISTORY_DTYPE)
+    _check(lib().prx_get_history(h, _ptr(out), cap, C.byref(n)), h)
+    return out[: n.value]
+
+
+def prx_get_stats(h) -> dict:
+    s = prx_stats()
+    _check(lib().prx_get_stats(h, C.byref(s)), h)
+    return dict(steps=s.steps, reactions=s.reactions, rebins=s.rebins,
+                step_launches=s.step_launches, kernel_launches=s.kernel_launches,
+                cells=tuple(s.cells), cell_edge=tuple(s.cell_edge))
+
+
+def prx_save(h, path: str):
+    _check(lib().prx_save(h, path.encode()), h)
+
+
+def prx_load(path: str, stream=None):
+    out = C.c_void_p()
+    _check(lib().prx_load(path.encode(), C.c_void_p(stream) if stream else None, C.byref(out)),
+           None)
+    return out
+
+
+def prx_profile_begin(h):
+    _check(lib().prx_profile_begin(h), h)
+
+
+def prx_profile_end(h) -> list:
+    out = (prx_kernel_time * 64)()
+    n = C.c_uint32()
+    _check(lib().prx_profile_end(h, out, 64, C.byref(n)), h)
+    return [dict(name=out[i].name.decode(), launches=out[i].launches, total_ms=out[i].total_ms)
+            for i in range(min(n.value, 64))]
+
+
+class System:
+    """Owning handle over one prx_system (calls prx_destroy when closed)."""
+
+    def __init__(self, desc: prx_system_desc, pos, vel, type_, state, bonds=None, stream=None,
+                 _handle=None):
+        self.n = desc.n
+        self.desc = desc
+        self.h = _handle if _handle is not None else prx_create(desc, pos, vel, type_, state,
+                                                                bonds, stream)
+
+    @classmethod
+    def load(cls, path: str, stream=None):
+        desc = prx_system_desc()
+        with open(path, "rb") as f:
+            f.read(8)  # magic
+            C.memmove(C.byref(desc), f.read(C.sizeof(desc)), C.sizeof(desc))
+        obj = cls.__new__(cls)
+        obj.h = prx_load(path, stream)
+        obj.desc = desc
+        obj.n = desc.n
+        return obj
+
+    def close(self):
+        if getattr(self, "h", None):
+            prx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_reaction(self, rx):
+        prx_set_reaction(self.h, rx)
+
+    def run(self, nsteps):
+        prx_run(self.h, nsteps)
+
+    def sync(self):
+        prx_sync(self.h)
+
+    def react_once(self, step):
+        return prx_react_once(self.h, step)
+
+    def forces(self):
+        return prx_compute_forces(self.h, self.n)
+
+    def step(self):
+        return prx_get_step(self.h)
+
+    def positions(self):
+        return prx_get_positions(self.h, self.n)
+
+    def velocities(self):
+        return prx_get_velocities(self.h, self.n)
+
+    def states(self):
+        return prx_get_states(self.h, self.n)
+
+    def types(self):
+        return prx_get_types(self.h, self.n)
+
+    def bonds(self):
+        return prx_get_bonds(self.h)
+
+    def observables(self):
+        return prx_get_observables(self.h)
+
+    def history(self):
+        return prx_get_history(self.h)
+
+    def stats(self):
+        return prx_get_stats(self.h)
+
+    def save(self, path):
+        prx_save(self.h, path)
