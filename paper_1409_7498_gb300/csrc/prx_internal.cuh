@@ -1,17 +1,24 @@
 // Internal layout and device helpers of the polyrx CUDA library.
 //
-// Data layout in HBM (one system, n particles, slot order = sorted by cell):
+// Data layout in HBM (one system, n particles, slot order = sorted by cell at
+// the last rebuild):
 //   two SoA sets (the current one and the rebuild target):
 //     x, y, z, vx, vy, vz : double[n]   absolute positions, half-step velocities
 //     id                  : u32[n]      particle id of the slot
 //     type, state, nadj   : u8/i8/u8[n]
 //     adj                 : u32[n*cap]  partner slots; bit 31 = bond style
-//   off[2]  : int4[n]    position relative to the slot's cell origin in
-//                        2^-29 fixed point (exact differences between any two
-//                        particles), .w = packed cell coordinates (9 bits
-//                        each); double-buffered across steps (neighbours
-//                        read the old copy while the new one is written)
-//   cell_start : u32[ncell+1]  CSR offsets of the cells (z-major)
+//   P[2] : uint4[n]  periodic fixed-point position X = floor(x / L 2^32) mod
+//                    2^32 per axis (the int32 difference of two X is the
+//                    minimum-image displacement, exactly, in units L / 2^32),
+//                    .w = coarse copy of X at the last list build (3 x 10 bits,
+//                    for the displacement trigger); double-buffered across
+//                    steps (neighbours read the old copy while the new one is
+//                    written)
+//   nl  : Verlet neighbour list, column-major [list_cap][n], entries are the
+//         neighbour's slot relative to the owner's (mod n, 16-bit when every
+//         offset fits, else 32-bit); nn : u8[n] entry counts
+//   cell_start : u32[ncell+1]  CSR offsets of the cells (z-major), valid at
+//         the last rebuild; used only to build the lists
 // A device control block (Ctl) holds the current set / buffer phase, the
 // step counter, the rebuild flag and the sticky error status, so that one
 // CUDA graph can be replayed without host involvement.
@@ -25,7 +32,7 @@ namespace prx {
 
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr uint32_t SLOT_MASK = 0x7FFFFFFFu;
-constexpr int STEP_THREADS = 128;   // FP64-mode kernels
+constexpr int STEP_THREADS = 128;
 constexpr int RX_THREADS = 256;
 constexpr int SCAN_TILE = 2048;  // elements per scan tile (256 threads x 8)
 
@@ -71,6 +78,8 @@ struct Ctl {
   unsigned long long hist_count;
   unsigned long long rx_base;  // bond-list offset of the current reaction
   long long trace[4];          // candidates, retained, a_winners, formed
+  unsigned int n_active;       // eligible A's of the current reaction step
+  unsigned int pad_;
 };
 
 struct RxParams {
@@ -89,14 +98,21 @@ struct Sys {
   int ncell;
   // geometry
   double L[3], halfL[3];
-  float Lf[3];
-  float hf[3];            // cell edge as float (prefilter geometry)
-  long long Hfx[3];       // cell edge in 2^-32 fixed point (= 8 H29)
-  int H29[3];             // cell edge in 2^-29 fixed point
-  int corr29[3];          // L in 2^-29 minus n_c H29: periodic-image correction
-  long long lofx[3];      // extended cell: offsets in [lofx, hifx) keep the list valid
-  long long hifx[3];
-  double inv_h[3];
+  long long Lfx[3];               // L in 2^-32 units
+  unsigned long long M64[3];      // round(2^64 / L): X = hi64((x + L) 2^32 M64)
+  float scale[3];                 // L / 2^32 (physical length of one X unit)
+  float scale_sq_ref;             // (L_0 / 2^32)^2
+  int wshift[3];                  // coarse reference: bits (X >> wshift) & 1023
+  float wunit[3];                 // physical length of one coarse unit
+  float disp2_max;                // (skin/2 - margin)^2: rebuild when exceeded
+  // Verlet list
+  void* nl;                       // u16 or u32 entries, [list_cap][n]
+  uint8_t* nn;
+  int nl16;                       // 1: 16-bit entries
+  int list_cap;
+  float rv2_build;                // (r_c + skin + margin)^2, list build test
+  // list-build tiling (cells of edge >= r_c + skin)
+  int tile_y, tiles_y, tile_threads, tile_cap;
   // physics (FP32 and FP64 copies)
   float rc2f, sig2f, eps24f, eps4f, fcapf, fkf, fr02f, rcf, sigf;
   double rc2, sig2, eps24, eps4, fcap, fk, fr02, rc, sig;
@@ -104,17 +120,12 @@ struct Sys {
   double gm;                  // gamma m (FP64 mode writes the friction force out)
   double mass;
   float b_kickf, cRf;
-  float rc2pre;               // (r_c + 1e-3)^2: conservative FP32 prefilter cutoff
   double cR;
   int thermo;                 // gamma > 0
   uint64_t seed;
   // buffers
   SoA s0, s1;
-  int4 *off0, *off1;
-  int tile_y;               // cell rows per block of the FP32 step kernel (1..4)
-  int tiles_y;              // ceil(n_c[1] / tile_y)
-  int tile_threads;         // threads per block
-  int tile_cap;             // staged particles per shared-memory pass
+  uint4 *P0, *P1;
   uint32_t* cell_start;
   uint32_t *count, *fill;
   uint32_t *key, *tmp, *new_of_old, *slot_of_id;
@@ -221,6 +232,21 @@ __device__ __forceinline__ float i2f_rn(int d) {
 // 2^-29 fixed point to float, one rounding.
 __device__ __forceinline__ float fx29_to_float(int d) { return __fmul_rn(i2f_rn(d), 0x1.0p-29f); }
 
+// Periodic fixed point of a coordinate: floor(x / L 2^32) mod 2^32, from
+// the binary64 fields and one 64x64 high multiply (integer pipe only).
+// Valid for -L < x < 2^29.
+__device__ __forceinline__ uint32_t periodic_fx(double x, long long Lfx, unsigned long long M) {
+  const unsigned long long a = (unsigned long long)(fx32(x) + Lfx);
+  return (uint32_t)__umul64hi(a, M);
+}
+
+// Minimum-image displacement X_j - X_i of two periodic coordinates, in X units.
+__device__ __forceinline__ int pdiff(uint32_t xj, uint32_t xi) { return (int)(xj - xi); }
+
+__device__ __forceinline__ uint32_t coarse_ref(uint32_t X, uint32_t Y, uint32_t Z, const int* sh) {
+  return ((X >> sh[0]) & 1023u) | (((Y >> sh[1]) & 1023u) << 10) | (((Z >> sh[2]) & 1023u) << 20);
+}
+
 __device__ __forceinline__ uint32_t pack_cell(int cx, int cy, int cz) {
   return (uint32_t)cx | ((uint32_t)cy << 9) | ((uint32_t)cz << 18);
 }
@@ -245,16 +271,15 @@ __device__ __forceinline__ double min_image(double d, double L, double half) {
 // ---- host-side launchers (defined in the kernel translation units) ----------
 void launch_step(const Sys& S, cudaStream_t st, int fp64, int forces_only,
                  cudaGraphConditionalHandle h, int use_cond);
-void launch_bin_full_keys(const Sys& S, cudaStream_t st);
 void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, const char*, int),
                   void* hook_ctx);
 void launch_rx(const Sys& S, const RxParams& R, cudaStream_t st, long long step_arg,
                void (*hook)(void*, const char*, int), void* hook_ctx);
 void launch_observables(const Sys& S, cudaStream_t st, int nblocks);
 int rebin_kernel_count();
-int step_kernel_count(int fp64);
-size_t step_tile_smem(const Sys& S);
-int configure_step_kernels(size_t smem_bytes);
 int rx_kernel_count();
+int step_kernel_count(int fp64);
+size_t build_tile_smem(const Sys& S);
+int configure_build_kernel(size_t smem_bytes);
 
 }  // namespace prx

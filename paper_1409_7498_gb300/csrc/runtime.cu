@@ -27,7 +27,7 @@
 using namespace prx;
 
 namespace {
-constexpr double kDefaultSkin = 0.15;
+constexpr double kDefaultSkin = 0.3;
 constexpr uint32_t kHistCap = 8192;
 constexpr uint64_t kCkptMagic = 0x31305850594C4F50ull;  // "POLYRX01"
 constexpr int kNoRxChunk = 10;
@@ -51,6 +51,7 @@ struct prx_system {
   std::vector<void*> dev_allocs;
   std::vector<void*> grid_allocs;
   double grid_rcut = 0.0;
+  double skin_used = 0.0;
   uint64_t host_step = 0;
   uint64_t step_launches = 0;      // step kernels (graphs and direct)
   uint64_t graph_rx_launches = 0;  // reaction sequences replayed inside graphs
@@ -136,41 +137,74 @@ void free_list(std::vector<void*>& l) {
   l.clear();
 }
 
-// Cell grid for cutoff rc: n_c = floor(L / (rc + skin)) cells per edge (at
-// least 3; at most 511, the packing limit), extended-cell tolerance
-// delta = (h - rc)/2 on each side.
+// Grid, fixed-point constants and Verlet-list layout for list cutoff rc
+// (the larger of the WCA and reaction cutoffs):
+//   list radius r_v = rc + skin; cells of edge >= r_v (only used to build the
+//   lists); a rebuild is triggered when some particle moved more than skin/2
+//   since the last build; X = floor(x / L 2^32) mod 2^32 per axis.
 int setup_grid(prx_system* sys, double rc) {
   Sys& S = sys->S;
-  const double skin = sys->d.skin < 0.0 ? kDefaultSkin : sys->d.skin;
+  double skin = sys->d.skin < 0.0 ? kDefaultSkin : sys->d.skin;
+  if (!(skin > 0.0)) return fail(sys, PRX_EINVAL, "skin must be positive");
+  // small boxes: shrink the skin until three list radii fit along every edge
+  const double Lmin = std::min(sys->d.box[0], std::min(sys->d.box[1], sys->d.box[2]));
+  if (Lmin / (rc + skin) < 3.0 * (1.0 + 1e-9)) skin = Lmin / (3.0 * (1.0 + 2e-9)) - rc;
+  if (!(skin >= 0.02)) return fail(sys, PRX_EINVAL, "box edge below three interaction cutoffs plus skin");
+  sys->skin_used = skin;
+  const double rv = rc + skin;
   long long ncell = 1;
   for (int k = 0; k < 3; ++k) {
     const double L = sys->d.box[k];
-    int nc = (int)std::floor(L / (rc + skin));
-    if (nc < 3) nc = (int)std::floor(L / (rc * (1.0 + 1e-9)));
-    if (nc < 3) return fail(sys, PRX_EINVAL, "box edge below three interaction cutoffs");
-    if (nc > 511) nc = 511;
-    const double h = L / nc;
-    if (h > 2.4) return fail(sys, PRX_EINVAL, "box edge too large for the 511-cell grid");
+    int nc = (int)std::floor(L / (rv * (1.0 + 1e-9)));
+    if (nc < 3) return fail(sys, PRX_EINVAL, "box edge below three list radii (cutoff + skin)");
+    if (nc > 1023) nc = 1023;
     S.nc[k] = nc;
-    S.inv_h[k] = 1.0 / h;
-    S.H29[k] = (int)std::llround(h * 536870912.0);
-    S.Hfx[k] = 8LL * S.H29[k];
-    S.corr29[k] = (int)(std::llround(L * 536870912.0) - (long long)nc * S.H29[k]);
-    S.hf[k] = (float)((double)S.H29[k] / 536870912.0);
-    const double delta = 0.5 * (h - rc) - 1e-6;
-    const long long dfx = delta > 0.0 ? (long long)std::floor(delta * 4294967296.0) : 0LL;
-    S.lofx[k] = -dfx;
-    S.hifx[k] = S.Hfx[k] + dfx;
+    S.Lfx[k] = (long long)std::llround(L * 4294967296.0);
+    S.M64[k] = (unsigned long long)(std::ldexp((long double)1.0, 64) / (long double)L + 0.5L);
+    S.scale[k] = (float)(L / 4294967296.0);
+    int sh = 0;
+    while (sh < 22 && std::ldexp(1.0, sh + 9) * (L / 4294967296.0) < skin) ++sh;
+    S.wshift[k] = sh;
+    S.wunit[k] = (float)(std::ldexp(1.0, sh) * (L / 4294967296.0));
     ncell *= nc;
   }
+  const double wmax = std::max((double)S.wunit[0], std::max((double)S.wunit[1], (double)S.wunit[2]));
+  const double dmax = 0.5 * skin - 2.0 * std::sqrt(3.0) * wmax - 1e-6;
+  if (!(dmax > 0.0)) return fail(sys, PRX_EINVAL, "skin too small for the displacement trigger");
+  S.disp2_max = (float)(dmax * dmax);
+  S.rv2_build = (float)((rv * (1.0 + 1e-5)) * (rv * (1.0 + 1e-5)));
   S.ncell = (int)ncell;
   sys->grid_rcut = rc;
+  free_list(sys->grid_allocs);
+  int rc2;
+  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.cell_start, (size_t)ncell + 1))) return rc2;
+  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.count, (size_t)ncell))) return rc2;
+  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.fill, (size_t)ncell))) return rc2;
+  const size_t nblk = std::max<size_t>((S.n + RX_THREADS - 1) / RX_THREADS,
+                                       ((size_t)ncell + SCAN_TILE - 1) / SCAN_TILE) + 1;
+  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.blk_count, nblk))) return rc2;
+  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.blk_off, nblk))) return rc2;
+  // Verlet list: capacity from the mean count at this density, 16-bit
+  // relative entries when every neighbour is within 32767 slots (mod n)
+  const double V = sys->d.box[0] * sys->d.box[1] * sys->d.box[2];
+  const double rho = (double)S.n / V;
+  const double mean_nb = rho * 4.0 / 3.0 * M_PI * rv * rv * rv;
+  S.list_cap = std::max(32, std::min(255, (int)std::ceil(2.5 * mean_nb + 16.0)));
+  const double per_cell = (double)S.n / (double)ncell;
+  const double span = ((double)S.nc[0] * S.nc[1] + S.nc[0] + 1.0) * per_cell * 1.3 + 64.0;
+  S.nl16 = (S.n < 32768 || span < 30000.0) ? 1 : 0;
   {
-    // FP32 step kernel tiling: about 300 particles per block, all neighbour
-    // rows staged in one shared-memory pass in the common case
+    void* nl = nullptr;
+    if ((rc2 = dalloc(sys, sys->grid_allocs, (uint8_t**)&nl,
+                      (size_t)S.list_cap * S.n * (S.nl16 ? 2 : 4))))
+      return rc2;
+    S.nl = nl;
+  }
+  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.nn, (size_t)S.n))) return rc2;
+  {
+    // list-build tiling: the largest tile of 1..4 cell rows whose particles
+    // fit 256 threads; staging buffer sized for all neighbour rows at once
     const double per_row = (double)S.n / ((double)S.nc[1] * S.nc[2]);
-    const double per_cell = (double)S.n / (double)ncell;
-    // largest tile (1..4 rows) whose particle count stays within 256 threads
     int ty = 1;
     for (int c = 2; c <= 4; ++c)
       if (c * per_row + 3.0 * std::sqrt(c * per_row) + 16.0 <= 256.0) ty = c;
@@ -181,24 +215,15 @@ int setup_grid(prx_system* sys, double rc) {
     int t = (int)std::ceil((mean_tile + 3.0 * std::sqrt(mean_tile) + 16.0) / 32.0) * 32;
     S.tile_threads = std::max(64, std::min(256, t));
     const double mean_tot = 3.0 * (ty + 2) * (per_row + 2.0 * per_cell);
-    int cap = (int)std::ceil((mean_tot + 3.5 * std::sqrt(mean_tot) + 32.0) / 32.0) * 32;
+    int cap = (int)std::ceil((mean_tot + 4.0 * std::sqrt(mean_tot) + 64.0) / 32.0) * 32;
     S.tile_cap = 0;
-    const size_t fixed = step_tile_smem(S);
-    const size_t budget = 200 * 1024;
-    if (fixed + 32 * (size_t)cap > budget) cap = (int)((budget - fixed) / 32);
-    S.tile_cap = std::max(64, cap);
-    if (configure_step_kernels(step_tile_smem(S)))
-      return fail(sys, PRX_ECUDA, "cannot set the step kernel's shared-memory size");
+    const size_t fixed = build_tile_smem(S);
+    const size_t budget = 160 * 1024;
+    if (fixed + 16 * (size_t)cap > budget) cap = (int)((budget - fixed) / 16);
+    S.tile_cap = std::max(64, std::min(cap, 65535));
+    if (configure_build_kernel(build_tile_smem(S)))
+      return fail(sys, PRX_ECUDA, "cannot set the list-build kernel's shared-memory size");
   }
-  free_list(sys->grid_allocs);
-  int rc2;
-  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.cell_start, (size_t)ncell + 1))) return rc2;
-  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.count, (size_t)ncell))) return rc2;
-  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.fill, (size_t)ncell))) return rc2;
-  const size_t nblk = std::max<size_t>((S.n + RX_THREADS - 1) / RX_THREADS,
-                                       ((size_t)ncell + SCAN_TILE - 1) / SCAN_TILE) + 1;
-  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.blk_count, nblk))) return rc2;
-  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.blk_off, nblk))) return rc2;
   return PRX_OK;
 }
 
@@ -314,7 +339,7 @@ struct HostSlots {
   std::vector<uint32_t> id, adj;
   std::vector<uint8_t> type, nadj;
   std::vector<int8_t> state;
-  std::vector<int4> off;
+  std::vector<uint4> P;
 };
 
 int fetch_slots(prx_system* sys, HostSlots& h, bool pos, bool vel, bool topo) {
@@ -338,13 +363,13 @@ int fetch_slots(prx_system* sys, HostSlots& h, bool pos, bool vel, bool topo) {
   }
   if (topo && n) {
     h.type.resize(n); h.state.resize(n); h.nadj.resize(n); h.adj.resize(n * sys->S.cap);
-    h.off.resize(n);
-    const int4* off = sys->ctl_host->phase ? sys->S.off1 : sys->S.off0;
+    h.P.resize(n);
+    const uint4* Pd = sys->ctl_host->phase ? sys->S.P1 : sys->S.P0;
     CK(cudaMemcpyAsync(h.type.data(), B.type, n, cudaMemcpyDeviceToHost, sys->stream));
     CK(cudaMemcpyAsync(h.state.data(), B.state, n, cudaMemcpyDeviceToHost, sys->stream));
     CK(cudaMemcpyAsync(h.nadj.data(), B.nadj, n, cudaMemcpyDeviceToHost, sys->stream));
     CK(cudaMemcpyAsync(h.adj.data(), B.adj, 4 * n * sys->S.cap, cudaMemcpyDeviceToHost, sys->stream));
-    CK(cudaMemcpyAsync(h.off.data(), off, sizeof(int4) * n, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemcpyAsync(h.P.data(), Pd, sizeof(uint4) * n, cudaMemcpyDeviceToHost, sys->stream));
   }
   CK(cudaStreamSynchronize(sys->stream));
   return PRX_OK;
@@ -362,7 +387,8 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
                 const uint8_t* type, const int8_t* state, const prx_bond* bonds, uint64_t n_bonds,
                 void* stream, const uint32_t* slot_ids, const uint32_t* slot_cells,
                 const uint32_t* slot_adj_ids, const uint8_t* slot_nadj, uint64_t step0,
-                double grid_rc, prx_system** out) {
+                double grid_rc, const uint32_t* slot_w, const uint8_t* slot_nn,
+                const int32_t* slot_nl, int nl_cap_saved, prx_system** out) {
   prx_system* sys = nullptr;
   if (!out) return PRX_EINVAL;
   *out = nullptr;
@@ -387,14 +413,12 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
   for (int k = 0; k < 3; ++k) {
     S.L[k] = desc->box[k];
     S.halfL[k] = 0.5 * desc->box[k];
-    S.Lf[k] = (float)desc->box[k];
   }
   const double rc_w = wca_rc(*desc);
   S.rc = rc_w;
   S.rc2 = rc_w * rc_w;
   S.rcf = (float)rc_w;
   S.rc2f = (float)S.rc2;
-  S.rc2pre = (float)((rc_w + 1e-3) * (rc_w + 1e-3));
   S.sig = desc->wca_sigma;
   S.sigf = (float)S.sig;
   S.sig2 = desc->wca_sigma * desc->wca_sigma;
@@ -445,7 +469,7 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
         (rc = dalloc(sys, L, &B->adj, (size_t)n * S.cap)))
       return bail(rc);
   }
-  if ((rc = dalloc(sys, L, &S.off0, n)) || (rc = dalloc(sys, L, &S.off1, n)) || (rc = dalloc(sys, L, &S.key, n)) ||
+  if ((rc = dalloc(sys, L, &S.P0, n)) || (rc = dalloc(sys, L, &S.P1, n)) || (rc = dalloc(sys, L, &S.key, n)) ||
       (rc = dalloc(sys, L, &S.tmp, n)) || (rc = dalloc(sys, L, &S.new_of_old, n)) ||
       (rc = dalloc(sys, L, &S.slot_of_id, n)) || (rc = dalloc(sys, L, &S.win, n)) ||
       (rc = dalloc(sys, L, &S.fin, n)) || (rc = dalloc(sys, L, &S.bonds, (size_t)S.bond_cap)) ||
@@ -548,6 +572,29 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
   // bin into set 1 (full keys from positions, or the restored cells)
   if ((rc = full_rebin(sys, slot_cells ? 2 : 1))) return bail(rc);
   if ((rc = sync_status(sys))) return bail(rc);
+  if (slot_cells && slot_w && slot_nn && slot_nl) {
+    // a checkpoint also restores the displacement references and the exact
+    // Verlet lists, so the rebuilds happen at the same steps as before
+    if (nl_cap_saved != S.list_cap) return bail(fail(sys, PRX_EIO, "checkpoint list capacity differs"));
+    std::vector<uint4> Ph(n);
+    uint4* Pd = sys->ctl_host->phase ? S.P1 : S.P0;
+    if (n) {
+      if (cudaMemcpy(Ph.data(), Pd, sizeof(uint4) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return bail(fail(sys, PRX_ECUDA, "download failed"));
+      for (uint32_t q = 0; q < n; ++q) Ph[q].w = slot_w[q];
+      if ((rc = up(Pd, Ph.data(), sizeof(uint4) * n))) return bail(rc);
+      if ((rc = up(S.nn, slot_nn, n))) return bail(rc);
+      const size_t ne = (size_t)S.list_cap * n;
+      if (S.nl16) {
+        std::vector<int16_t> v(ne);
+        for (size_t q = 0; q < ne; ++q) v[q] = (int16_t)slot_nl[q];
+        if ((rc = up(S.nl, v.data(), 2 * ne))) return bail(rc);
+      } else {
+        if ((rc = up(S.nl, slot_nl, 4 * ne))) return bail(rc);
+      }
+    }
+    if ((rc = sync_status(sys))) return bail(rc);
+  }
   *out = sys;
   return PRX_OK;
 }
@@ -598,7 +645,7 @@ int prx_create(const prx_system_desc* desc, const double* pos, const double* vel
                const int8_t* state, const prx_bond* bonds, uint64_t n_bonds, void* cuda_stream,
                prx_system** out) {
   return create_impl(desc, pos, vel, type, state, bonds, n_bonds, cuda_stream, nullptr, nullptr, nullptr,
-                     nullptr, 0, 0.0, out);
+                     nullptr, 0, 0.0, nullptr, nullptr, nullptr, 0, out);
 }
 
 void prx_destroy(prx_system* sys) {
@@ -941,17 +988,30 @@ int prx_save(prx_system* sys, const char* path) {
   if (nb) {
     CK(cudaMemcpy(bonds.data(), sys->S.bonds, sizeof(prx_bond) * nb, cudaMemcpyDeviceToHost));
   }
-  std::vector<uint32_t> cells(n), adj_ids(n * cap, 0u);
-  for (uint64_t s = 0; s < n; ++s) {
-    int cx, cy, cz;
-    const uint32_t w = (uint32_t)h.off[s].w;
-    cx = (int)(w & 511u);
-    cy = (int)((w >> 9) & 511u);
-    cz = (int)((w >> 18) & 511u);
-    cells[s] = (uint32_t)((cz * sys->S.nc[1] + cy) * sys->S.nc[0] + cx);
-    for (uint32_t b = 0; b < h.nadj[s]; ++b) {
-      const uint32_t e = h.adj[s * cap + b];
-      adj_ids[s * cap + b] = h.id[e & SLOT_MASK] | (e & ~SLOT_MASK);
+  std::vector<uint32_t> cells(n), adj_ids(n * cap, 0u), wref(n);
+  std::vector<uint32_t> cs((size_t)sys->S.ncell + 1);
+  std::vector<uint8_t> nn(n);
+  const int lcap = sys->S.list_cap;
+  std::vector<int32_t> nl((size_t)lcap * n);
+  if (n) {
+    CK(cudaMemcpy(cs.data(), sys->S.cell_start, 4 * cs.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(nn.data(), sys->S.nn, n, cudaMemcpyDeviceToHost));
+    if (sys->S.nl16) {
+      std::vector<int16_t> v((size_t)lcap * n);
+      CK(cudaMemcpy(v.data(), sys->S.nl, 2 * v.size(), cudaMemcpyDeviceToHost));
+      for (size_t q = 0; q < v.size(); ++q) nl[q] = v[q];
+    } else {
+      CK(cudaMemcpy(nl.data(), sys->S.nl, 4 * nl.size(), cudaMemcpyDeviceToHost));
+    }
+  }
+  uint32_t c = 0;
+  for (uint64_t q = 0; q < n; ++q) {
+    while (cs[c + 1] <= q) ++c;  // slot q lies in cell c of the last rebuild
+    cells[q] = c;
+    wref[q] = h.P[q].w;
+    for (uint32_t b = 0; b < h.nadj[q]; ++b) {
+      const uint32_t e = h.adj[q * cap + b];
+      adj_ids[q * cap + b] = h.id[e & SLOT_MASK] | (e & ~SLOT_MASK);
     }
   }
   FILE* f = fopen(path, "wb");
@@ -981,6 +1041,10 @@ int prx_save(prx_system* sys, const char* path) {
   W(h.nadj.data(), n);
   W(adj_ids.data(), 4 * n * cap);
   W(bonds.data(), sizeof(prx_bond) * nb);
+  W(&lcap, sizeof(int));
+  W(wref.data(), 4 * n);
+  W(nn.data(), n);
+  W(nl.data(), 4 * (size_t)lcap * n);
   if (fclose(f) != 0) ok = false;
   return ok ? PRX_OK : fail(sys, PRX_EIO, "write failed");
 }
@@ -1032,6 +1096,18 @@ int prx_load(const char* path, void* cuda_stream, prx_system** out) {
   R(nadj.data(), n);
   R(adj_ids.data(), 4 * n * cap);
   R(bonds.data(), sizeof(prx_bond) * nb);
+  int lcap = 0;
+  R(&lcap, sizeof(int));
+  if (!ok || lcap < 1 || lcap > 255) {
+    fclose(f);
+    return PRX_EIO;
+  }
+  std::vector<uint32_t> wref(n);
+  std::vector<uint8_t> nn(n);
+  std::vector<int32_t> nl((size_t)lcap * n);
+  R(wref.data(), 4 * n);
+  R(nn.data(), n);
+  R(nl.data(), 4 * (size_t)lcap * n);
   fclose(f);
   if (!ok) return PRX_EIO;
   for (uint64_t s = 0; s < n; ++s) {
@@ -1049,7 +1125,8 @@ int prx_load(const char* path, void* cuda_stream, prx_system** out) {
   // recreate with the reaction's grid so that the saved cells are valid
   prx_system* sys = nullptr;
   int rc = create_impl(&d, pos.data(), vel.data(), type_id.data(), state_id.data(), bonds.data(), nb, cuda_stream,
-                       ids.data(), cells.data(), adj_ids.data(), nadj.data(), step, grid_rcut, &sys);
+                       ids.data(), cells.data(), adj_ids.data(), nadj.data(), step, grid_rcut,
+                       wref.data(), nn.data(), nl.data(), lcap, &sys);
   if (rc) return rc;
   if (has_rx) {
     rc = prx_set_reaction(sys, &rxd);

@@ -58,80 +58,102 @@ __device__ __forceinline__ long long block_sum_ll(long long v) {
   return t;
 }
 
+template <bool NL16>
+__device__ __forceinline__ uint32_t nl_get_rx(const Sys& S, int k, uint32_t i) {
+  int r;
+  if constexpr (NL16) r = ((const int16_t*)S.nl)[(size_t)k * S.n + i];
+  else r = ((const int32_t*)S.nl)[(size_t)k * S.n + i];
+  int j = (int)i + r;
+  if (j < 0) j += (int)S.n;
+  else if (j >= (int)S.n) j -= (int)S.n;
+  return (uint32_t)j;
+}
+
+// Work list of the eligible A's (their order does not matter: each A's
+// result goes to its own slot), and win[] cleared for every slot.
+__global__ void __launch_bounds__(RX_THREADS) k_rx_compact(Sys S, RxParams R) {
+  Ctl* ctl = S.ctl;
+  const SoA B = ctl->set ? S.s1 : S.s0;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool el = false;
+  if (i < S.n) {
+    S.win[i] = NONE;
+    el = in_window(R.mask_A, R.a_lo, R.a_hi, B.type[i], B.state[i]);
+  }
+  // one atomic per block: warp ballots, block prefix in shared memory
+  __shared__ uint32_t wcnt[RX_THREADS / 32];
+  __shared__ uint32_t bbase;
+  const uint32_t bal = __ballot_sync(0xFFFFFFFFu, el);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wcnt[wid] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < RX_THREADS / 32; ++w) {
+      const uint32_t c = wcnt[w];
+      wcnt[w] = t;
+      t += c;
+    }
+    bbase = t ? atomicAdd(&ctl->n_active, t) : 0u;
+  }
+  __syncthreads();
+  if (el) S.tmp[bbase + wcnt[wid] + __popc(bal & ((1u << lane) - 1u))] = i;
+}
+
+// Steps 1-5 for one eligible A: its Verlet list holds every particle within
+// the force cutoff, hence every candidate within r_react <= r_c.  Grid-stride
+// over the work list of eligible A's.
+template <bool NL16>
 __global__ void __launch_bounds__(RX_THREADS) k_rx_find(Sys S, RxParams R, long long step_arg) {
   Ctl* ctl = S.ctl;
   const unsigned long long step = step_arg >= 0 ? (unsigned long long)step_arg : ctl->step;
   const SoA B = ctl->set ? S.s1 : S.s0;
-  const int4* off = ctl->phase ? S.off1 : S.off0;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint4* P = ctl->phase ? S.P1 : S.P0;
+  const uint32_t nact = ctl->n_active;
   long long ncand = 0, nret = 0;
-  if (i < S.n) {
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nact; w += gridDim.x * blockDim.x) {
+    const uint32_t i = S.tmp[w];
     uint32_t best = NONE;
-    const uint32_t ti = B.type[i];
-    const int si = B.state[i];
-    if (in_window(R.mask_A, R.a_lo, R.a_hi, ti, si)) {
-      const int4 oi = off[i];
-      int cx, cy, cz;
-      unpack_cell((uint32_t)oi.w, cx, cy, cz);
+    {
+      const uint4 pi = P[i];
       const double xi = B.x[i], yi = B.y[i], zi = B.z[i];
       const uint32_t idi = B.id[i];
       const uint32_t nb = B.nadj[i];
       unsigned long long bestkey = 0ull;
       uint32_t bestid = 0u;
-      for (int dz = -1; dz <= 1; ++dz) {
-        int qz = cz + dz;
-        uint32_t shz = (uint32_t)(dz * S.H29[2]);
-        if (qz < 0) { qz += S.nc[2]; shz -= (uint32_t)S.corr29[2]; }
-        else if (qz >= S.nc[2]) { qz -= S.nc[2]; shz += (uint32_t)S.corr29[2]; }
-        for (int dy = -1; dy <= 1; ++dy) {
-          int qy = cy + dy;
-          uint32_t shy = (uint32_t)(dy * S.H29[1]);
-          if (qy < 0) { qy += S.nc[1]; shy -= (uint32_t)S.corr29[1]; }
-          else if (qy >= S.nc[1]) { qy -= S.nc[1]; shy += (uint32_t)S.corr29[1]; }
-          const int rowbase = (qz * S.nc[1] + qy) * S.nc[0];
-          for (int dx = -1; dx <= 1; ++dx) {
-            int qx = cx + dx;
-            uint32_t shx = (uint32_t)(dx * S.H29[0]);
-            if (qx < 0) { qx += S.nc[0]; shx -= (uint32_t)S.corr29[0]; }
-            else if (qx >= S.nc[0]) { qx -= S.nc[0]; shx += (uint32_t)S.corr29[0]; }
-            const int q = rowbase + qx;
-            const uint32_t s0 = S.cell_start[q], s1 = S.cell_start[q + 1];
-            for (uint32_t j = s0; j < s1; ++j) {
-              if (j == i) continue;
-              if (!in_window(R.mask_T, R.t_lo, R.t_hi, B.type[j], B.state[j])) continue;
-              // FP32 prefilter on the exact fixed-point displacement: it can only
-              // widen the set that the exact FP64 test below decides on
-              const int4 oj = off[j];
-              const float ex = fx29_to_float((int)((uint32_t)oj.x - (uint32_t)oi.x + shx));
-              const float ey = fx29_to_float((int)((uint32_t)oj.y - (uint32_t)oi.y + shy));
-              const float ez = fx29_to_float((int)((uint32_t)oj.z - (uint32_t)oi.z + shz));
-              if (!(fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < R.rr2_pre)) continue;
-              // exact test, Table I step 1: d = x_T - x_A under the minimum image,
-              // r^2 = fma(dz, dz, fma(dy, dy, dx dx)), strict r^2 < r_react^2
-              const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
-              const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
-              const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
-              const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
-              if (!(r2 < R.rr2)) continue;
-              bool bonded = false;
-              for (uint32_t b = 0; b < nb; ++b)
-                bonded |= (B.adj[(size_t)i * S.cap + b] & SLOT_MASK) == j;
-              if (bonded) continue;
-              ++ncand;
-              const uint32_t idj = B.id[j];
-              // step 2: retained when u < k dt Theta (Eq. 4)
-              const uint4 wa = keyed_draw(S.seed, step, idi, idj, TAG_ACCEPT);
-              if (!(u53(wa.x, wa.y) < R.p)) continue;
-              ++nret;
-              // step 5: one T per A, uniformly at random
-              const unsigned long long k = key64(keyed_draw(S.seed, step, idi, idj, TAG_SEL_A));
-              if (best == NONE || k < bestkey || (k == bestkey && idj < bestid)) {
-                best = j;
-                bestkey = k;
-                bestid = idj;
-              }
-            }
-          }
+      const int cnt = S.nn[i];
+      for (int k = 0; k < cnt; ++k) {
+        const uint32_t j = nl_get_rx<NL16>(S, k, i);
+        if (!in_window(R.mask_T, R.t_lo, R.t_hi, B.type[j], B.state[j])) continue;
+        // FP32 prefilter on the fixed-point displacement (error ~1e-7): it can
+        // only widen the set that the exact FP64 test below decides on
+        const uint4 pj = P[j];
+        const float ex = __int2float_rn(pdiff(pj.x, pi.x)) * S.scale[0];
+        const float ey = __int2float_rn(pdiff(pj.y, pi.y)) * S.scale[1];
+        const float ez = __int2float_rn(pdiff(pj.z, pi.z)) * S.scale[2];
+        if (!(fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < R.rr2_pre)) continue;
+        // exact test, Table I step 1: d = x_T - x_A under the minimum image,
+        // r^2 = fma(dz, dz, fma(dy, dy, dx dx)), strict r^2 < r_react^2
+        const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
+        const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
+        const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
+        const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
+        if (!(r2 < R.rr2)) continue;
+        bool bonded = false;
+        for (uint32_t b = 0; b < nb; ++b) bonded |= (B.adj[(size_t)i * S.cap + b] & SLOT_MASK) == j;
+        if (bonded) continue;
+        ++ncand;
+        const uint32_t idj = B.id[j];
+        // step 2: retained when u < k dt Theta (Eq. 4)
+        const uint4 wa = keyed_draw(S.seed, step, idi, idj, TAG_ACCEPT);
+        if (!(u53(wa.x, wa.y) < R.p)) continue;
+        ++nret;
+        // step 5: one T per A, uniformly at random
+        const unsigned long long key = key64(keyed_draw(S.seed, step, idi, idj, TAG_SEL_A));
+        if (best == NONE || key < bestkey || (key == bestkey && idj < bestid)) {
+          best = j;
+          bestkey = key;
+          bestid = idj;
         }
       }
     }
@@ -145,11 +167,13 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_find(Sys S, RxParams R, long 
   }
 }
 
+// Steps 6-7 for one A winner: every other A that picked the same T lies
+// within r_react of T, hence in T's Verlet list.
+template <bool NL16>
 __global__ void __launch_bounds__(RX_THREADS) k_rx_select_T(Sys S, long long step_arg) {
   Ctl* ctl = S.ctl;
   const unsigned long long step = step_arg >= 0 ? (unsigned long long)step_arg : ctl->step;
   const SoA B = ctl->set ? S.s1 : S.s0;
-  const int4* off = ctl->phase ? S.off1 : S.off0;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t fin = NONE;
   bool winner = false;
@@ -160,26 +184,15 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_select_T(Sys S, long long ste
       const uint32_t idi = B.id[i], idT = B.id[T];
       const unsigned long long mine = key64(keyed_draw(S.seed, step, idT, idi, TAG_SEL_T));
       bool keep = true;
-      int cx, cy, cz;
-      unpack_cell((uint32_t)off[T].w, cx, cy, cz);
-      for (int dz = -1; dz <= 1 && keep; ++dz) {
-        const int qz = wrap_cell(cz + dz, S.nc[2]);
-        for (int dy = -1; dy <= 1 && keep; ++dy) {
-          const int qy = wrap_cell(cy + dy, S.nc[1]);
-          const int rowbase = (qz * S.nc[1] + qy) * S.nc[0];
-          for (int dx = -1; dx <= 1 && keep; ++dx) {
-            const int q = rowbase + wrap_cell(cx + dx, S.nc[0]);
-            const uint32_t s0 = S.cell_start[q], s1 = S.cell_start[q + 1];
-            for (uint32_t k = s0; k < s1; ++k) {
-              if (k == i || S.win[k] != T) continue;
-              const uint32_t idk = B.id[k];
-              const unsigned long long other = key64(keyed_draw(S.seed, step, idT, idk, TAG_SEL_T));
-              if (other < mine || (other == mine && idk < idi)) {
-                keep = false;
-                break;
-              }
-            }
-          }
+      const int cnt = S.nn[T];
+      for (int k = 0; k < cnt; ++k) {
+        const uint32_t a = nl_get_rx<NL16>(S, k, T);
+        if (a == i || S.win[a] != T) continue;
+        const uint32_t ida = B.id[a];
+        const unsigned long long other = key64(keyed_draw(S.seed, step, idT, ida, TAG_SEL_T));
+        if (other < mine || (other == mine && ida < idi)) {
+          keep = false;
+          break;
         }
       }
       if (keep) fin = T;
@@ -349,7 +362,7 @@ inline unsigned blocks_rx(uint32_t n) { return n ? (n + RX_THREADS - 1) / RX_THR
 
 }  // namespace
 
-int rx_kernel_count() { return 5; }
+int rx_kernel_count() { return 6; }
 
 void launch_rx(const Sys& S, const RxParams& R, cudaStream_t st, long long step_arg,
                void (*hook)(void*, const char*, int), void* ctx) {
@@ -357,12 +370,18 @@ void launch_rx(const Sys& S, const RxParams& R, cudaStream_t st, long long step_
   auto H = [&](const char* nm, int p) {
     if (hook) hook(ctx, nm, p);
   };
-  cudaMemsetAsync(&S.ctl->trace[0], 0, sizeof(long long) * 4, st);
+  cudaMemsetAsync(&S.ctl->trace[0], 0, sizeof(long long) * 4 + sizeof(unsigned int), st);
+  H("rx_compact", 0);
+  k_rx_compact<<<g, RX_THREADS, 0, st>>>(S, R);
+  H("rx_compact", 1);
+  const unsigned gf = g < 1216u ? g : 1216u;
   H("rx_find", 0);
-  k_rx_find<<<g, RX_THREADS, 0, st>>>(S, R, step_arg);
+  if (S.nl16) k_rx_find<true><<<gf, RX_THREADS, 0, st>>>(S, R, step_arg);
+  else k_rx_find<false><<<gf, RX_THREADS, 0, st>>>(S, R, step_arg);
   H("rx_find", 1);
   H("rx_select_T", 0);
-  k_rx_select_T<<<g, RX_THREADS, 0, st>>>(S, step_arg);
+  if (S.nl16) k_rx_select_T<true><<<g, RX_THREADS, 0, st>>>(S, step_arg);
+  else k_rx_select_T<false><<<g, RX_THREADS, 0, st>>>(S, step_arg);
   H("rx_select_T", 1);
   H("rx_scan", 0);
   k_rx_scan<<<1, 1024, 0, st>>>(S, g);

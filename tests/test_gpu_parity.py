@@ -359,7 +359,7 @@ def test_observables_and_history_consistent(P):
 
 def test_ragged_sizes_profile_and_launch_counts(P):
     for n in (1, 2, 127, 128, 129, 4097):
-        L = max(4.0, synth.box_edge(n))
+        L = max(4.4, synth.box_edge(n))
         inp = synth.step_growth(n - max(1, n // 9), max(1, n // 9), 4, n, rho=n / L ** 3)
         with gpu_system(P, L, inp.x, inp.v, inp.type, inp.state, cap=4, seed=n) as g:
             g.set_reaction(gpu_reaction(P, synth.step_growth_scheme(4, 1.0)))
