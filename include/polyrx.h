@@ -221,6 +221,39 @@ int prx_profile_begin(prx_system* sys);
 /* Ends profiling and returns per-kernel launch counts and device time. */
 int prx_profile_end(prx_system* sys, prx_kernel_time* out, uint32_t cap, uint32_t* n_out);
 
+/* ---- allocation-free reaction step ------------------------------------------ */
+/* Largest system prx_react_noalloc accepts. */
+#define PRX_NOALLOC_MAX_N 16384
+
+/* One reaction step (the same rule, draws and tie-breaking as
+ * prx_react_once) on device arrays the caller owns, allocating nothing.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory themselves, e.g. code that must stay within
+ * a memory budget fixed by a host framework, or that runs inside an
+ * allocator hook.
+ *
+ * Inputs (device pointers, indexed by particle id 0..n-1): d_pos [n][3]
+ * positions in [0, box); d_type [n].  Updated in place: d_state [n], d_nadj
+ * [n] and d_adj [n][adj_cap] (partner ids, bit 31 = bond style).  Outputs:
+ * d_bonds_out receives the new bonds in ascending id of A (at most
+ * bonds_cap), *d_nbonds_out (device) their number; trace (host, may be
+ * NULL) the Table I counts.  The candidate search is all-pairs.
+ *
+ * Scratch memory: one static device array sized for PRX_NOALLOC_MAX_N
+ * particles, held by every GPU that loads the library until the process
+ * exits; n above that limit returns PRX_ECAPACITY.  The first call on a
+ * device looks up the array's device address with that device current
+ * (make that first call before any stream capture).  Every call shares the
+ * array: calls whose work overlaps on the GPU race, so serialise them.  The
+ * call is queued on cuda_stream (NULL: the legacy default stream) and waits
+ * for it before returning the status (PRX_ECAPACITY when a valence or
+ * bonds_cap limit was hit). */
+int prx_react_noalloc(const prx_reaction_desc* rx, const double* box, double dt, uint64_t seed,
+                      uint64_t step, uint32_t n, const double* d_pos, const uint8_t* d_type,
+                      int8_t* d_state, uint32_t adj_cap, uint8_t* d_nadj, uint32_t* d_adj,
+                      prx_bond* d_bonds_out, uint32_t bonds_cap, uint32_t* d_nbonds_out,
+                      void* cuda_stream, prx_rx_trace* trace);
+
 /* ---- errors ---------------------------------------------------------------- */
 const char* prx_last_error(const prx_system* sys);
 const char* prx_status_string(int status);

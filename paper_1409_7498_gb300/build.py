@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libpolyrx.so")
-SOURCES = ["md_kernels.cu", "rx_kernels.cu", "runtime.cu"]
+SOURCES = ["md_kernels.cu", "rx_kernels.cu", "runtime.cu", "noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "prx_internal.cuh"), os.path.join(ROOT, "include", "polyrx.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

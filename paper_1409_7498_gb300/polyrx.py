@@ -113,6 +113,9 @@ def lib():
         "prx_load": ([C.c_char_p, VP, P(VP)], I),
         "prx_profile_begin": ([VP], I),
         "prx_profile_end": ([VP, P(prx_kernel_time), C.c_uint32, P(C.c_uint32)], I),
+        "prx_react_noalloc": ([P(prx_reaction_desc), P(C.c_double), C.c_double, U64, U64,
+                               C.c_uint32, VP, VP, VP, C.c_uint32, VP, VP, VP, C.c_uint32, VP,
+                               VP, P(prx_rx_trace)], I),
         "prx_last_error": ([VP], C.c_char_p),
         "prx_status_string": ([I], C.c_char_p),
     }
@@ -294,6 +297,27 @@ def prx_profile_end(h) -> list:
     _check(lib().prx_profile_end(h, out, 64, C.byref(n)), h)
     return [dict(name=out[i].name.decode(), launches=out[i].launches, total_ms=out[i].total_ms)
             for i in range(min(n.value, 64))]
+
+
+PRX_NOALLOC_MAX_N = 16384
+
+
+def prx_react_noalloc(rx, box, dt, seed, step, n, d_pos, d_type, d_state, adj_cap, d_nadj, d_adj,
+                      d_bonds_out, bonds_cap, d_nbonds_out, stream=None) -> dict:
+    """Reaction step on caller-owned device buffers (integer device
+    addresses), allocating nothing; see prx_react_noalloc in polyrx.h."""
+    b = (C.c_double * 3)(*([float(box)] * 3 if np.isscalar(box) else [float(v) for v in box]))
+    t = prx_rx_trace()
+    rc = lib().prx_react_noalloc(C.byref(rx), b, float(dt), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                 int(step), int(n), C.c_void_p(d_pos), C.c_void_p(d_type),
+                                 C.c_void_p(d_state), int(adj_cap), C.c_void_p(d_nadj),
+                                 C.c_void_p(d_adj), C.c_void_p(d_bonds_out), int(bonds_cap),
+                                 C.c_void_p(d_nbonds_out), C.c_void_p(stream) if stream else None,
+                                 C.byref(t))
+    if rc != PRX_OK:
+        raise PolyrxError(rc, lib().prx_status_string(rc).decode())
+    return dict(candidates=t.candidates, retained=t.retained, a_winners=t.a_winners,
+                formed=t.formed)
 
 
 class System:
