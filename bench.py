@@ -17,6 +17,7 @@ seed); there is no data-path collective ("scaling": "weak").
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -47,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="polyrx", choices=["polyrx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
+    ap.add_argument("--direct", action="store_true",
+                    help="launch kernels one by one instead of CUDA graphs (for ncu launch lists)")
     return ap.parse_args()
 
 
@@ -219,6 +222,8 @@ def main():
     clk = Clocks(local)
     time.sleep(0.3)
     wall0 = time.perf_counter()
+    if args.direct:
+        P.prx_profile_begin(g.h)
     with torch.cuda.stream(stream):
         for q in range(args.steps):
             flush.fill_(q & 0xFF)  # L2 flush between timed bench steps (256 MB > 129 MB L2)
@@ -226,6 +231,8 @@ def main():
             g.run(THETA)
             ends[q].record(stream)
     torch.cuda.synchronize()
+    if args.direct:
+        P.prx_profile_end(g.h)
     wall = time.perf_counter() - wall0
     clocks = clk.stop()
     g.sync()
@@ -254,8 +261,14 @@ def main():
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if os.path.exists(tr_path):
+        # DRAM bytes of one step-kernel launch from an ncu capture, valid only
+        # while the step kernel's sources are unchanged since the capture
         tr = json.load(open(tr_path))
-        if tr.get("kernel_source_digest") == gbuild._digest():
+        h = hashlib.sha256()
+        for rel in tr.get("digest_of", []):
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                h.update(f.read())
+        if tr.get("kernel_source_digest") == h.hexdigest():
             traffic = tr.get("bytes_per_launch")
 
     # end to end through the C ABI with host buffers

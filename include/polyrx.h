@@ -4,9 +4,10 @@
  * It implements the data-parallel hot path of de Buyl & Nies, "A parallel
  * algorithm for step- and chain-growth polymerization in Molecular
  * Dynamics" (arXiv:1409.7498):
- *   - the MD step: WCA pair forces (Sec. II.C, Eq. 15) from a cell list,
- *     FENE bond forces (Sec. II.C) or mirror-LJ created bonds (Eq. 17), and a
- *     Langevin velocity-Verlet integrator (velocity Verlet, Sec. II.C);
+ *   - the MD step: WCA pair forces (Sec. II.C, Eq. 15) from Verlet
+ *     neighbour lists built on a cell grid, FENE bond forces (Sec. II.C) or
+ *     mirror-LJ created bonds (Eq. 17), and a Langevin velocity-Verlet
+ *     integrator (velocity Verlet, Sec. II.C);
  *   - the reaction step run every Theta steps after the integration
  *     (Sec. III): candidate A/T pairs by type, state and distance, accepted
  *     with probability k dt Theta (Eqs. 3-4), one T per A and one A per T
@@ -76,7 +77,9 @@ typedef struct {
   double fene_k;          /* FENE k_F */
   double fene_r0;         /* FENE R_0 */
   double force_cap;       /* > 0: cap on the WCA pair-force magnitude (warm-up); 0: off */
-  double skin;            /* cell edge >= cutoff + skin; < 0 selects the default (0.15) */
+  double skin;            /* Verlet-list skin: list radius = cutoff + skin, lists rebuilt
+                             when a particle moved skin/2; < 0 selects the default (0.3);
+                             shrunk automatically in boxes shorter than 3 list radii */
   int32_t force_precision;/* PRX_FORCE_FP32 or PRX_FORCE_FP64 */
   int32_t reserved;       /* must be 0 */
   uint64_t seed;          /* key of every random draw */
@@ -134,7 +137,7 @@ typedef struct {
 typedef struct {
   uint64_t steps;         /* MD steps completed */
   uint64_t reactions;     /* reaction steps completed */
-  uint64_t rebins;        /* cell-list rebuilds */
+  uint64_t rebins;        /* neighbour-list rebuilds (sort + lists), including the first */
   uint64_t step_launches; /* step-kernel launches */
   uint64_t kernel_launches; /* all kernels launched by this system so far */
   uint32_t cells[3];      /* cell grid */
