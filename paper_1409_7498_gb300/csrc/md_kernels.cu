@@ -105,14 +105,15 @@ __device__ __forceinline__ bool bond64(const Sys& S, uint32_t style, double dx, 
   return true;
 }
 
-// Last block of a grid: returns true in thread 0 of the block that finished last.
-__device__ __forceinline__ bool last_block(unsigned int* counter) {
+// Last of the nb blocks that run a system's part of a grid: true in thread 0
+// of the block that finished last.
+__device__ __forceinline__ bool last_block(unsigned int* counter, uint32_t nb) {
   __shared__ bool is_last;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int prev = atomicAdd(counter, 1u);
-    is_last = (prev == gridDim.x - 1);
+    is_last = (prev == nb - 1);
   }
   __syncthreads();
   return is_last && threadIdx.x == 0;
@@ -124,32 +125,48 @@ __device__ __forceinline__ bool last_block(unsigned int* counter) {
 // count before the block's work starts.
 // The only data the last warp reads is the rebuild flag, whose setters
 // fence after setting it; warps therefore fence only once per block.
-__device__ __forceinline__ bool last_warp(unsigned int* counter, unsigned int* warps_left) {
+__device__ __forceinline__ bool last_warp(unsigned int* counter, unsigned int* warps_left,
+                                          uint32_t nb) {
   __syncwarp();
   bool last = false;
   if ((threadIdx.x & 31) == 0) {
     if (atomicSub(warps_left, 1u) == 1u) {
       __threadfence();
-      last = atomicAdd(counter, 1u) == gridDim.x - 1;
+      last = atomicAdd(counter, 1u) == nb - 1;
     }
   }
   return last;
 }
 
-__device__ __forceinline__ void raise_rebuild(Ctl* ctl) {
-  atomicExch(&ctl->rebin_flag, 1);
+// A particle moved more than skin/2: flag the system (and its batch).
+__device__ __forceinline__ void raise_rebuild(const Sys& S) {
+  atomicExch(&S.ctl->rebin_flag, 1);
+  if (S.in_batch) atomicExch(&S.batch->any_rebuild, 1);
   __threadfence();
 }
 
-__device__ __forceinline__ void step_epilogue(Ctl* ctl, int ph, unsigned long long step,
+// End of a step: the system's last warp advances its step counter and
+// buffer phase; for a single system it also sets the graph's rebuild
+// condition, for a batch the last system to finish sets it for all.
+__device__ __forceinline__ void step_epilogue(const Sys& S, int ph, unsigned long long step,
                                               cudaGraphConditionalHandle cond, int use_cond,
-                                              unsigned int* warps_left) {
-  if (last_warp(&ctl->done_step, warps_left)) {
+                                              unsigned int* warps_left, uint32_t nb) {
+  Ctl* ctl = S.ctl;
+  if (last_warp(&ctl->done_step, warps_left, nb)) {
     ctl->done_step = 0u;
     ctl->phase = ph ^ 1;
     ctl->step = step;
-    const int flag = atomicAdd(&ctl->rebin_flag, 0);
-    if (use_cond) cudaGraphSetConditional(cond, flag ? 1u : 0u);
+    if (!S.in_batch) {
+      const int flag = atomicAdd(&ctl->rebin_flag, 0);
+      if (use_cond) cudaGraphSetConditional(cond, flag ? 1u : 0u);
+    } else {
+      __threadfence();
+      if (atomicAdd(&S.batch->done_step, 1u) == S.n_members - 1) {
+        S.batch->done_step = 0u;
+        const int flag = atomicExch(&S.batch->any_rebuild, 0);
+        if (use_cond) cudaGraphSetConditional(cond, flag ? 1u : 0u);
+      }
+    }
   }
 }
 
@@ -216,7 +233,7 @@ __device__ __forceinline__ void integrate32(const Sys& S, Ctl* ctl, const SoA& B
   const uint32_t X = periodic_fx(nx, S.Lfx[0], S.M64[0]);
   const uint32_t Y = periodic_fx(ny, S.Lfx[1], S.M64[1]);
   const uint32_t Z = periodic_fx(nz, S.Lfx[2], S.M64[2]);
-  if (moved_beyond_skin(S, X, Y, Z, W)) raise_rebuild(ctl);
+  if (moved_beyond_skin(S, X, Y, Z, W)) raise_rebuild(S);
   B.vx[i] = vx;
   B.vy[i] = vy;
   B.vz[i] = vz;
@@ -230,8 +247,8 @@ __device__ __forceinline__ void integrate32(const Sys& S, Ctl* ctl, const SoA& B
 // FP32 step kernel: one thread per slot, WCA over the Verlet list.
 // ---------------------------------------------------------------------------
 template <bool NL16, bool FORCES_ONLY>
-__global__ void __launch_bounds__(256, 4)
-    k_step_nl(Sys S, cudaGraphConditionalHandle cond, int use_cond) {
+__device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
+                                             cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ unsigned int warps_left;
   if (threadIdx.x == 0) warps_left = blockDim.x >> 5;
   __syncthreads();
@@ -242,7 +259,7 @@ __global__ void __launch_bounds__(256, 4)
   const SoA B = set ? S.s1 : S.s0;
   const uint4* __restrict__ P = ph ? S.P1 : S.P0;
   uint4* __restrict__ Pn = ph ? S.P0 : S.P1;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t i = blk.b * blockDim.x + threadIdx.x;
   if (i < S.n) {
     // every load that does not depend on another goes out first
     const int cnt = __ldg(S.nn + i);
@@ -301,7 +318,22 @@ __global__ void __launch_bounds__(256, 4)
       integrate32(S, ctl, B, Pn, i, pid, pi.w, step, fx, fy, fz, xi, yi, zi, vx, vy, vz);
     }
   }
-  if constexpr (!FORCES_ONLY) step_epilogue(ctl, ph, step, cond, use_cond, &warps_left);
+  if constexpr (!FORCES_ONLY) step_epilogue(S, ph, step, cond, use_cond, &warps_left, blk.nb);
+}
+
+template <bool NL16, bool FORCES_ONLY>
+__global__ void __launch_bounds__(256, 4)
+    k_step_nl(Sys S, cudaGraphConditionalHandle cond, int use_cond) {
+  step_nl_body<NL16, FORCES_ONLY>(S, Blk{blockIdx.x, gridDim.x}, cond, use_cond);
+}
+// Members of a batch may differ in list width: the branch is uniform per block.
+__global__ void __launch_bounds__(256, 4)
+    kb_step_nl(const Sys* __restrict__ T, const BlkMap* __restrict__ M,
+               cudaGraphConditionalHandle cond, int use_cond) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (S.nl16) step_nl_body<true, false>(S, Blk{m.b, m.nb}, cond, use_cond);
+  else step_nl_body<false, false>(S, Blk{m.b, m.nb}, cond, use_cond);
 }
 
 // ---------------------------------------------------------------------------
@@ -383,10 +415,10 @@ __global__ void __launch_bounds__(STEP_THREADS)
       xs[d][i] = xn;
       Xn[d] = periodic_fx(xn, S.Lfx[d], S.M64[d]);
     }
-    if (moved_beyond_skin(S, Xn[0], Xn[1], Xn[2], W)) raise_rebuild(ctl);
+    if (moved_beyond_skin(S, Xn[0], Xn[1], Xn[2], W)) raise_rebuild(S);
     Pn[i] = make_uint4(Xn[0], Xn[1], Xn[2], W);
   }
-  step_epilogue(ctl, ph, step, cond, use_cond, &warps_left);
+  step_epilogue(S, ph, step, cond, use_cond, &warps_left, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -401,10 +433,10 @@ __device__ __forceinline__ double wrap_into_box(double v, double L) {
   return v;
 }
 
-__global__ void k_rebin_keys(Sys S) {
+__device__ __forceinline__ void rebin_keys_body(const Sys& S, const Blk blk) {
   Ctl* ctl = S.ctl;
   const SoA B = ctl->set ? S.s1 : S.s0;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t i = blk.b * blockDim.x + threadIdx.x;
   if (i >= S.n) return;
   double* xs[3] = {B.x, B.y, B.z};
   int c[3];
@@ -421,17 +453,35 @@ __global__ void k_rebin_keys(Sys S) {
   atomicAdd(&S.count[k], 1u);
 }
 
+__global__ void k_rebin_keys(Sys S) { rebin_keys_body(S, Blk{blockIdx.x, gridDim.x}); }
+__global__ void kb_rebin_keys(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
+  rebin_keys_body(S, Blk{m.b, m.nb});
+}
+
 // Restore: keys were uploaded (a checkpoint's cells); only count them.
-__global__ void k_count_keys(Sys S) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void count_keys_body(const Sys& S, const Blk blk) {
+  const uint32_t i = blk.b * blockDim.x + threadIdx.x;
   if (i >= S.n) return;
   atomicAdd(&S.count[S.key[i]], 1u);
 }
 
+__global__ void k_count_keys(Sys S) { count_keys_body(S, Blk{blockIdx.x, gridDim.x}); }
+__global__ void kb_count_keys(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
+  count_keys_body(S, Blk{m.b, m.nb});
+}
+
 // Exclusive scan of count[0..ncell) into cell_start[0..ncell], three passes.
-__global__ void k_scan_tiles(const uint32_t* __restrict__ in, uint32_t n, uint32_t* __restrict__ tsum) {
+__device__ __forceinline__ void scan_tiles_body(const Sys& S, const Blk blk) {
   __shared__ uint32_t red[256];
-  const uint32_t base = blockIdx.x * SCAN_TILE;
+  const uint32_t* __restrict__ in = S.count;
+  const uint32_t n = (uint32_t)S.ncell;
+  const uint32_t base = blk.b * SCAN_TILE;
   uint32_t s = 0;
   for (int k = 0; k < SCAN_TILE / 256; ++k) {
     const uint32_t idx = base + k * 256 + threadIdx.x;
@@ -443,7 +493,14 @@ __global__ void k_scan_tiles(const uint32_t* __restrict__ in, uint32_t n, uint32
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) tsum[blockIdx.x] = red[0];
+  if (threadIdx.x == 0) S.blk_off[blk.b] = red[0];
+}
+__global__ void k_scan_tiles(Sys S) { scan_tiles_body(S, Blk{blockIdx.x, gridDim.x}); }
+__global__ void kb_scan_tiles(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.ctl->rebin_flag) return;
+  scan_tiles_body(S, Blk{m.b, m.nb});
 }
 
 __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t& total) {
@@ -474,7 +531,9 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_
 }
 
 // Single block: exclusive scan of the tile sums in place.
-__global__ void k_scan_top(uint32_t* tsum, uint32_t ntiles) {
+__device__ __forceinline__ void scan_top_body(const Sys& S) {
+  uint32_t* tsum = S.blk_off;
+  const uint32_t ntiles = ((uint32_t)S.ncell + SCAN_TILE - 1) / SCAN_TILE;
   uint32_t carry = 0;
   for (uint32_t base = 0; base < ntiles; base += 256) {
     const uint32_t idx = base + threadIdx.x;
@@ -485,10 +544,18 @@ __global__ void k_scan_top(uint32_t* tsum, uint32_t ntiles) {
     carry += total;
   }
 }
+__global__ void k_scan_top(Sys S) { scan_top_body(S); }
+__global__ void kb_scan_top(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const Sys& S = T[M[blockIdx.x].sys];
+  if (!S.ctl->rebin_flag) return;
+  scan_top_body(S);
+}
 
-__global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t n,
-                            const uint32_t* __restrict__ tsum, uint32_t* __restrict__ out) {
-  const uint32_t base = blockIdx.x * SCAN_TILE + threadIdx.x * (SCAN_TILE / 256);
+__device__ __forceinline__ void scan_down_body(const Sys& S, const Blk blk) {
+  const uint32_t* __restrict__ in = S.count;
+  const uint32_t n = (uint32_t)S.ncell;
+  uint32_t* __restrict__ out = S.cell_start;
+  const uint32_t base = blk.b * SCAN_TILE + threadIdx.x * (SCAN_TILE / 256);
   uint32_t loc[SCAN_TILE / 256];
   uint32_t s = 0;
 #pragma unroll
@@ -497,27 +564,54 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t n,
     s += loc[k];
   }
   uint32_t total;
-  uint32_t run = tsum[blockIdx.x] + block_exclusive_scan_256(s, total);
-  if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0u;
+  uint32_t run = S.blk_off[blk.b] + block_exclusive_scan_256(s, total);
+  if (blk.b == 0 && threadIdx.x == 0) out[0] = 0u;
 #pragma unroll
   for (int k = 0; k < SCAN_TILE / 256; ++k) {
     run += loc[k];
     if (base + k < n) out[base + k + 1] = run;
   }
 }
+__global__ void k_scan_down(Sys S) { scan_down_body(S, Blk{blockIdx.x, gridDim.x}); }
+__global__ void kb_scan_down(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.ctl->rebin_flag) return;
+  scan_down_body(S, Blk{m.b, m.nb});
+}
 
-__global__ void k_rebin_scatter(Sys S) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+// Batched rebuilds clear the cell counters in a kernel (a single system uses memsets).
+__global__ void kb_rebin_clear(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.ctl->rebin_flag) return;
+  const uint32_t c = m.b * blockDim.x + threadIdx.x;
+  if (c < (uint32_t)S.ncell) {
+    S.count[c] = 0u;
+    S.fill[c] = 0u;
+  }
+}
+
+__device__ __forceinline__ void rebin_scatter_body(const Sys& S, const Blk blk) {
+  const uint32_t i = blk.b * blockDim.x + threadIdx.x;
   if (i >= S.n) return;
   const uint32_t k = S.key[i];
   const uint32_t pos = atomicAdd(&S.fill[k], 1u);
   S.tmp[S.cell_start[k] + pos] = i;
 }
 
+__global__ void k_rebin_scatter(Sys S) { rebin_scatter_body(S, Blk{blockIdx.x, gridDim.x}); }
+__global__ void kb_rebin_scatter(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
+  rebin_scatter_body(S, Blk{m.b, m.nb});
+}
+
 // Sorts each cell's members by old slot: the order inside a cell then does
 // not depend on the order in which the scatter's atomics completed.
-__global__ void k_rebin_cellsort(Sys S) {
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void rebin_cellsort_body(const Sys& S, const Blk blk) {
+  const uint32_t c = blk.b * blockDim.x + threadIdx.x;
   if (c >= (uint32_t)S.ncell) return;
   const uint32_t s0 = S.cell_start[c], s1 = S.cell_start[c + 1];
   for (uint32_t a = s0 + 1; a < s1; ++a) {
@@ -531,16 +625,24 @@ __global__ void k_rebin_cellsort(Sys S) {
   }
 }
 
+__global__ void k_rebin_cellsort(Sys S) { rebin_cellsort_body(S, Blk{blockIdx.x, gridDim.x}); }
+__global__ void kb_rebin_cellsort(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
+  rebin_cellsort_body(S, Blk{m.b, m.nb});
+}
+
 // New slot s takes old slot tmp[s]: copies every per-particle array into the
 // other set and writes the fixed-point position with a fresh displacement
 // reference.
-__global__ void k_rebin_permute(Sys S) {
+__device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk) {
   Ctl* ctl = S.ctl;
   const int set = ctl->set;
   const SoA A = set ? S.s1 : S.s0;
   const SoA B = set ? S.s0 : S.s1;
   uint4* P = ctl->phase ? S.P1 : S.P0;
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t s = blk.b * blockDim.x + threadIdx.x;
   if (s >= S.n) return;
   const uint32_t o = S.tmp[s];
   const double x = A.x[o], y = A.y[o], z = A.z[o];
@@ -565,16 +667,32 @@ __global__ void k_rebin_permute(Sys S) {
   P[s] = make_uint4(X, Y, Z, coarse_ref(X, Y, Z, S.wshift));
 }
 
-__global__ void k_rebin_remap(Sys S) {
+__global__ void k_rebin_permute(Sys S) { rebin_permute_body(S, Blk{blockIdx.x, gridDim.x}); }
+__global__ void kb_rebin_permute(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
+  rebin_permute_body(S, Blk{m.b, m.nb});
+}
+
+__device__ __forceinline__ void rebin_remap_body(const Sys& S, const Blk blk) {
   Ctl* ctl = S.ctl;
   const SoA B = ctl->set ? S.s0 : S.s1;  // the set just written
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t s = blk.b * blockDim.x + threadIdx.x;
   if (s >= S.n) return;
   const uint32_t nb = B.nadj[s];
   for (uint32_t b = 0; b < nb; ++b) {
     const uint32_t e = B.adj[(size_t)s * S.cap + b];
     B.adj[(size_t)s * S.cap + b] = S.new_of_old[e & SLOT_MASK] | (e & ~SLOT_MASK);
   }
+}
+
+__global__ void k_rebin_remap(Sys S) { rebin_remap_body(S, Blk{blockIdx.x, gridDim.x}); }
+__global__ void kb_rebin_remap(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
+  rebin_remap_body(S, Blk{m.b, m.nb});
 }
 
 // ---------------------------------------------------------------------------
@@ -598,8 +716,7 @@ struct RowInfo {
 constexpr int TILE_ROWS_MAX = 18;  // (TY + 2) x 3 for TY <= 4
 
 template <bool NL16>
-__global__ void __launch_bounds__(256) k_build_nlist(Sys S) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, unsigned char* smem) {
   const int CAP = S.tile_cap;
   uint4* sX = reinterpret_cast<uint4*>(smem);
   RowInfo* ri = reinterpret_cast<RowInfo*>(smem + 16 * (size_t)CAP);
@@ -609,7 +726,7 @@ __global__ void __launch_bounds__(256) k_build_nlist(Sys S) {
   Ctl* ctl = S.ctl;
   const uint4* __restrict__ P = ctl->phase ? S.P1 : S.P0;
   const int nx = S.nc[0], ny = S.nc[1], nz = S.nc[2];
-  const int ty = blockIdx.x % S.tiles_y, cz = blockIdx.x / S.tiles_y;
+  const int ty = blk.b % S.tiles_y, cz = blk.b / S.tiles_y;
   const int cy0 = ty * S.tile_y;
   const int TYb = min(S.tile_y, ny - cy0);
   const int RY = TYb + 2, R = 3 * RY;
@@ -726,12 +843,27 @@ __global__ void __launch_bounds__(256) k_build_nlist(Sys S) {
       if (overflow) set_status(ctl, PRX_ECAPACITY);
     }
   }
-  if (last_block(&ctl->done_rebin)) {
+  if (last_block(&ctl->done_rebin, blk.nb)) {
     ctl->done_rebin = 0u;
     ctl->set ^= 1;
     ctl->rebin_flag = 0;
     ctl->rebins += 1ull;
   }
+}
+
+template <bool NL16>
+__global__ void __launch_bounds__(256) k_build_nlist(Sys S) {
+  extern __shared__ __align__(16) unsigned char smem_b[];
+  build_nlist_body<NL16>(S, Blk{blockIdx.x, gridDim.x}, smem_b);
+}
+__global__ void __launch_bounds__(256)
+    kb_build_nlist(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  extern __shared__ __align__(16) unsigned char smem_b[];
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.ctl->rebin_flag) return;
+  if (S.nl16) build_nlist_body<true>(S, Blk{m.b, m.nb}, smem_b);
+  else build_nlist_body<false>(S, Blk{m.b, m.nb}, smem_b);
 }
 
 inline unsigned blocks_for(uint64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -795,13 +927,13 @@ void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, c
   else k_rebin_keys<<<gp, 256, 0, st>>>(S);
   H(mode == 2 ? "count_keys" : "rebin_keys", 1);
   H("scan_tiles", 0);
-  k_scan_tiles<<<tiles, 256, 0, st>>>(S.count, S.ncell, S.blk_off);
+  k_scan_tiles<<<tiles, 256, 0, st>>>(S);
   H("scan_tiles", 1);
   H("scan_top", 0);
-  k_scan_top<<<1, 256, 0, st>>>(S.blk_off, tiles);
+  k_scan_top<<<1, 256, 0, st>>>(S);
   H("scan_top", 1);
   H("scan_down", 0);
-  k_scan_down<<<tiles, 256, 0, st>>>(S.count, S.ncell, S.blk_off, S.cell_start);
+  k_scan_down<<<tiles, 256, 0, st>>>(S);
   H("scan_down", 1);
   H("rebin_scatter", 0);
   k_rebin_scatter<<<gp, 256, 0, st>>>(S);
@@ -821,6 +953,31 @@ void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, c
   if (S.nl16) k_build_nlist<true><<<gt, S.tile_threads, sm, st>>>(S);
   else k_build_nlist<false><<<gt, S.tile_threads, sm, st>>>(S);
   H("build_nlist", 1);
+}
+
+void launch_batch_step(const BatchLaunch& L, cudaStream_t st, cudaGraphConditionalHandle h,
+                       int use_cond) {
+  kb_step_nl<<<L.n_part, 256, 0, st>>>(L.T, L.part, h, use_cond);
+}
+
+// The rebuild pipeline over every member; members whose flag is clear
+// return at once from each kernel.
+void launch_batch_rebuild(const BatchLaunch& L, cudaStream_t st) {
+  kb_rebin_clear<<<L.n_cell, 256, 0, st>>>(L.T, L.cell);
+  kb_rebin_keys<<<L.n_part, 256, 0, st>>>(L.T, L.part);
+  kb_scan_tiles<<<L.n_tile, 256, 0, st>>>(L.T, L.tile);
+  kb_scan_top<<<L.n_one, 256, 0, st>>>(L.T, L.one);
+  kb_scan_down<<<L.n_tile, 256, 0, st>>>(L.T, L.tile);
+  kb_rebin_scatter<<<L.n_part, 256, 0, st>>>(L.T, L.part);
+  kb_rebin_cellsort<<<L.n_cell, 256, 0, st>>>(L.T, L.cell);
+  kb_rebin_permute<<<L.n_part, 256, 0, st>>>(L.T, L.part);
+  kb_rebin_remap<<<L.n_part, 256, 0, st>>>(L.T, L.part);
+  kb_build_nlist<<<L.n_build, L.build_threads, L.build_smem, st>>>(L.T, L.build);
+}
+
+int configure_batch_build_kernel(size_t smem_bytes) {
+  return cudaFuncSetAttribute(kb_build_nlist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes) == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace prx

@@ -92,6 +92,13 @@ struct RxParams {
   uint8_t maxval[PRX_MAX_TYPES];
 };
 
+// Control block shared by the members of a batch.
+struct BatchCtl {
+  int any_rebuild;          // some member needs a rebuild after this step
+  unsigned int done_step;   // members whose step finished (last-member detection)
+  int pad0, pad1;
+};
+
 struct Sys {
   uint32_t n, cap;
   int nc[3];
@@ -137,6 +144,25 @@ struct Sys {
   double *fout, *eout;
   double* red;              // per-block partial sums (observables)
   Ctl* ctl;
+  // reaction scheme (has_rx = 0: none)
+  RxParams R;
+  int has_rx;
+  // batch membership: in_batch = 1 inside a batched launch; batch = the
+  // batch's control block
+  int in_batch;
+  BatchCtl* batch;
+  unsigned int n_members;   // members of the batch (last-member detection)
+};
+
+// Part of a grid that belongs to one system: local block index and block
+// count (the whole grid for a single system).
+struct Blk {
+  uint32_t b, nb;
+};
+
+// One entry of a batched launch's block map: system, local block, block count.
+struct BlkMap {
+  uint32_t sys, b, nb, pad;
 };
 
 // ---------------------------------------------------------------------------
@@ -268,12 +294,26 @@ __device__ __forceinline__ double min_image(double d, double L, double half) {
   return d;
 }
 
+// Block maps of a batched launch, one per kernel family (device arrays).
+struct BatchLaunch {
+  const Sys* T;             // member table
+  const BlkMap *part, *cell, *tile, *one, *build;
+  unsigned n_part, n_cell, n_tile, n_one, n_build;
+  int build_threads;
+  size_t build_smem;
+};
+
 // ---- host-side launchers (defined in the kernel translation units) ----------
+void launch_batch_step(const BatchLaunch& L, cudaStream_t st, cudaGraphConditionalHandle h,
+                       int use_cond);
+void launch_batch_rebuild(const BatchLaunch& L, cudaStream_t st);
+void launch_batch_rx(const BatchLaunch& L, cudaStream_t st);
+int configure_batch_build_kernel(size_t smem_bytes);
 void launch_step(const Sys& S, cudaStream_t st, int fp64, int forces_only,
                  cudaGraphConditionalHandle h, int use_cond);
 void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, const char*, int),
                   void* hook_ctx);
-void launch_rx(const Sys& S, const RxParams& R, cudaStream_t st, long long step_arg,
+void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
                void (*hook)(void*, const char*, int), void* hook_ctx);
 void launch_observables(const Sys& S, cudaStream_t st, int nblocks);
 int rebin_kernel_count();

@@ -42,7 +42,6 @@ struct prx_system {
   prx_system_desc d{};
   int has_rx = 0;
   prx_reaction_desc rxd{};
-  RxParams R{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t cap = nullptr;
@@ -285,7 +284,7 @@ int build_graph(prx_system* sys, int nsteps, bool with_rx, cudaGraphExec_t* out)
     bodies.push_back(np.conditional.phGraph_out[0]);
     CK(cudaStreamUpdateCaptureDependencies(sys->cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
   }
-  if (with_rx) launch_rx(sys->S, sys->R, sys->cap, -1, nullptr, nullptr);
+  if (with_rx) launch_rx(sys->S, sys->cap, -1, nullptr, nullptr);
   CK(cudaStreamEndCapture(sys->cap, &g));
   for (cudaGraph_t body : bodies) {
     CK(cudaStreamBeginCaptureToGraph(sys->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -326,7 +325,7 @@ int direct_step(prx_system* sys) {
   if (sys->ctl_host->rebin_flag) launch_rebin(sys->S, sys->stream, 0, prof_hook, sys);
   sys->host_step++;
   if (sys->has_rx && sys->host_step % sys->rxd.theta == 0) {
-    launch_rx(sys->S, sys->R, sys->stream, -1, prof_hook, sys);
+    launch_rx(sys->S, sys->stream, -1, prof_hook, sys);
     sys->other_launches += rx_kernel_count();
   }
   CK(cudaGetLastError());
@@ -668,6 +667,7 @@ int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx) {
   if (!sys) return PRX_EINVAL;
   if (!rx) {
     sys->has_rx = 0;
+    sys->S.has_rx = 0;
     destroy_graphs(sys);
     return PRX_OK;
   }
@@ -675,7 +675,7 @@ int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx) {
   if (rc) return rc;
   CK(cudaStreamSynchronize(sys->stream));
   sys->rxd = *rx;
-  RxParams& R = sys->R;
+  RxParams& R = sys->S.R;
   R.mask_A = rx->type_mask_A;
   R.mask_T = rx->type_mask_T;
   R.a_lo = rx->a_lo;
@@ -690,6 +690,7 @@ int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx) {
   R.style = (uint32_t)rx->bond_style;
   for (int t = 0; t < PRX_MAX_TYPES; ++t) R.maxval[t] = rx->max_valence[t];
   sys->has_rx = 1;
+  sys->S.has_rx = 1;
   destroy_graphs(sys);
   const double need = std::max(wca_rc(sys->d), rx->r_react);
   if (need > sys->grid_rcut) {
@@ -746,7 +747,7 @@ int prx_react_once(prx_system* sys, uint64_t step, prx_rx_trace* trace) {
   if (!sys) return PRX_EINVAL;
   if (!sys->has_rx) return fail(sys, PRX_EINVAL, "no reaction scheme set");
   if (sys->S.n) {
-    launch_rx(sys->S, sys->R, sys->stream, (long long)step, sys->profiling ? prof_hook : nullptr, sys);
+    launch_rx(sys->S, sys->stream, (long long)step, sys->profiling ? prof_hook : nullptr, sys);
     sys->other_launches += rx_kernel_count();
     CK(cudaGetLastError());
   }

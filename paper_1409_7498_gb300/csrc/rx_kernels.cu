@@ -33,12 +33,12 @@ __device__ __forceinline__ unsigned long long key64(uint4 w) {
   return ((unsigned long long)w.x << 32) | w.y;
 }
 
-__device__ __forceinline__ bool last_block_rx(unsigned int* counter) {
+__device__ __forceinline__ bool last_block_rx(unsigned int* counter, uint32_t nb) {
   __shared__ bool is_last;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    is_last = (atomicAdd(counter, 1u) == nb - 1);
   }
   __syncthreads();
   return is_last && threadIdx.x == 0;
@@ -71,10 +71,12 @@ __device__ __forceinline__ uint32_t nl_get_rx(const Sys& S, int k, uint32_t i) {
 
 // Work list of the eligible A's (their order does not matter: each A's
 // result goes to its own slot), and win[] cleared for every slot.
-__global__ void __launch_bounds__(RX_THREADS) k_rx_compact(Sys S, RxParams R) {
+__device__ __forceinline__ void rx_compact_body(const Sys& S, const Blk blk) {
+  const RxParams& R = S.R;
+
   Ctl* ctl = S.ctl;
   const SoA B = ctl->set ? S.s1 : S.s0;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t i = blk.b * blockDim.x + threadIdx.x;
   bool el = false;
   if (i < S.n) {
     S.win[i] = NONE;
@@ -100,18 +102,31 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_compact(Sys S, RxParams R) {
   if (el) S.tmp[bbase + wcnt[wid] + __popc(bal & ((1u << lane) - 1u))] = i;
 }
 
+__global__ void __launch_bounds__(RX_THREADS) k_rx_compact(Sys S) {
+  rx_compact_body(S, Blk{blockIdx.x, gridDim.x});
+}
+__global__ void __launch_bounds__(RX_THREADS)
+    kb_rx_compact(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.has_rx) return;  // this member has no reaction scheme
+  rx_compact_body(S, Blk{m.b, m.nb});
+}
+
 // Steps 1-5 for one eligible A: its Verlet list holds every particle within
 // the force cutoff, hence every candidate within r_react <= r_c.  Grid-stride
 // over the work list of eligible A's.
 template <bool NL16>
-__global__ void __launch_bounds__(RX_THREADS) k_rx_find(Sys S, RxParams R, long long step_arg) {
+__device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long long step_arg) {
+  const RxParams& R = S.R;
+
   Ctl* ctl = S.ctl;
   const unsigned long long step = step_arg >= 0 ? (unsigned long long)step_arg : ctl->step;
   const SoA B = ctl->set ? S.s1 : S.s0;
   const uint4* P = ctl->phase ? S.P1 : S.P0;
   const uint32_t nact = ctl->n_active;
   long long ncand = 0, nret = 0;
-  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nact; w += gridDim.x * blockDim.x) {
+  for (uint32_t w = blk.b * blockDim.x + threadIdx.x; w < nact; w += blk.nb * blockDim.x) {
     const uint32_t i = S.tmp[w];
     uint32_t best = NONE;
     {
@@ -167,14 +182,27 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_find(Sys S, RxParams R, long 
   }
 }
 
+template <bool NL16>
+__global__ void __launch_bounds__(RX_THREADS) k_rx_find(Sys S, long long step_arg) {
+  rx_find_body<NL16>(S, Blk{blockIdx.x, gridDim.x}, step_arg);
+}
+__global__ void __launch_bounds__(RX_THREADS)
+    kb_rx_find(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.has_rx) return;  // this member has no reaction scheme
+  if (S.nl16) rx_find_body<true>(S, Blk{m.b, m.nb}, -1LL);
+  else rx_find_body<false>(S, Blk{m.b, m.nb}, -1LL);
+}
+
 // Steps 6-7 for one A winner: every other A that picked the same T lies
 // within r_react of T, hence in T's Verlet list.
 template <bool NL16>
-__global__ void __launch_bounds__(RX_THREADS) k_rx_select_T(Sys S, long long step_arg) {
+__device__ __forceinline__ void rx_select_T_body(const Sys& S, const Blk blk, long long step_arg) {
   Ctl* ctl = S.ctl;
   const unsigned long long step = step_arg >= 0 ? (unsigned long long)step_arg : ctl->step;
   const SoA B = ctl->set ? S.s1 : S.s0;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t i = blk.b * blockDim.x + threadIdx.x;
   uint32_t fin = NONE;
   bool winner = false;
   if (i < S.n) {
@@ -202,14 +230,27 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_select_T(Sys S, long long ste
   const int nfin = __syncthreads_count(fin != NONE);
   const int nwin = __syncthreads_count(winner);
   if (threadIdx.x == 0) {
-    S.blk_count[blockIdx.x] = (uint32_t)nfin;
+    S.blk_count[blk.b] = (uint32_t)nfin;
     if (nwin) atomicAdd((unsigned long long*)&ctl->trace[2], (unsigned long long)nwin);
   }
 }
 
+template <bool NL16>
+__global__ void __launch_bounds__(RX_THREADS) k_rx_select_T(Sys S, long long step_arg) {
+  rx_select_T_body<NL16>(S, Blk{blockIdx.x, gridDim.x}, step_arg);
+}
+__global__ void __launch_bounds__(RX_THREADS)
+    kb_rx_select_T(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.has_rx) return;  // this member has no reaction scheme
+  if (S.nl16) rx_select_T_body<true>(S, Blk{m.b, m.nb}, -1LL);
+  else rx_select_T_body<false>(S, Blk{m.b, m.nb}, -1LL);
+}
+
 // One block: exclusive scan of the per-block counts, bond-list base, and a
 // cleared history record for this reaction step.
-__global__ void k_rx_scan(Sys S, uint32_t nblk) {
+__device__ __forceinline__ void rx_scan_body(const Sys& S, const uint32_t nblk) {
   Ctl* ctl = S.ctl;
   __shared__ uint32_t warp_tot[32];
   __shared__ uint32_t carry_s;
@@ -259,11 +300,20 @@ __global__ void k_rx_scan(Sys S, uint32_t nblk) {
   for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x) cnt[k] = 0;
 }
 
-__global__ void __launch_bounds__(RX_THREADS) k_rx_apply(Sys S, RxParams R, long long step_arg) {
+__global__ void k_rx_scan(Sys S, uint32_t nblk) { rx_scan_body(S, nblk); }
+__global__ void kb_rx_scan(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const Sys& S = T[M[blockIdx.x].sys];
+  if (!S.has_rx) return;
+  rx_scan_body(S, S.n ? (S.n + RX_THREADS - 1) / RX_THREADS : 1u);
+}
+
+__device__ __forceinline__ void rx_apply_body(const Sys& S, const Blk blk, long long step_arg) {
+  const RxParams& R = S.R;
+
   Ctl* ctl = S.ctl;
   const unsigned long long step = step_arg >= 0 ? (unsigned long long)step_arg : ctl->step;
   const SoA B = ctl->set ? S.s1 : S.s0;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t i = blk.b * blockDim.x + threadIdx.x;
   const uint32_t T = i < S.n ? S.fin[i] : NONE;
   const bool has = T != NONE;
   // rank of this pair among the block's pairs (ballot + warp prefix)
@@ -276,7 +326,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_apply(Sys S, RxParams R, long
   for (int w = 0; w < wid; ++w) before += wcount[w];
   const uint32_t rank = before + __popc(bal & ((1u << lane) - 1u));
   if (!has) return;
-  const unsigned long long pos = ctl->rx_base + S.blk_off[blockIdx.x] + rank;
+  const unsigned long long pos = ctl->rx_base + S.blk_off[blk.b] + rank;
   const uint32_t ta = B.type[i], tt = B.type[T];
   const uint32_t capA = R.maxval[ta] < S.cap ? R.maxval[ta] : S.cap;
   const uint32_t capT = R.maxval[tt] < S.cap ? R.maxval[tt] : S.cap;
@@ -301,15 +351,27 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_apply(Sys S, RxParams R, long
   S.bonds[pos] = rec;
 }
 
+__global__ void __launch_bounds__(RX_THREADS) k_rx_apply(Sys S, long long step_arg) {
+  rx_apply_body(S, Blk{blockIdx.x, gridDim.x}, step_arg);
+}
+__global__ void __launch_bounds__(RX_THREADS)
+    kb_rx_apply(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.has_rx) return;  // this member has no reaction scheme
+  rx_apply_body(S, Blk{m.b, m.nb}, -1LL);
+}
+
 // Populations per (type, state) into history record hist_count % hist_cap
 // (integer atomics: the counts do not depend on their order).
-__global__ void __launch_bounds__(RX_THREADS) k_obs_hist(Sys S, long long step_arg, int record) {
+__device__ __forceinline__ void obs_hist_body(const Sys& S, const Blk blk, long long step_arg,
+                                              int record) {
   Ctl* ctl = S.ctl;
   const SoA B = ctl->set ? S.s1 : S.s0;
   __shared__ int32_t h[PRX_MAX_TYPES * PRX_MAX_STATES];
   for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x) h[k] = 0;
   __syncthreads();
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t i = blk.b * blockDim.x + threadIdx.x;
   if (i < S.n) {
     const uint32_t t = B.type[i];
     const int s = B.state[i];
@@ -320,7 +382,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_obs_hist(Sys S, long long step_a
   HistRec* rec = &S.hist[slot];
   for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x)
     if (h[k]) atomicAdd(&rec->counts[0][0] + k, h[k]);
-  if (last_block_rx(&ctl->done_obs)) {
+  if (last_block_rx(&ctl->done_obs, blk.nb)) {
     ctl->done_obs = 0u;
     rec->step = step_arg >= 0 ? step_arg : (long long)ctl->step;
     rec->bonds = (long long)ctl->nbonds;
@@ -329,6 +391,17 @@ __global__ void __launch_bounds__(RX_THREADS) k_obs_hist(Sys S, long long step_a
       ctl->reactions += 1ull;
     }
   }
+}
+
+__global__ void __launch_bounds__(RX_THREADS) k_obs_hist(Sys S, long long step_arg, int record) {
+  obs_hist_body(S, Blk{blockIdx.x, gridDim.x}, step_arg, record);
+}
+__global__ void __launch_bounds__(RX_THREADS)
+    kb_obs_hist(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.has_rx) return;  // this member has no reaction scheme
+  obs_hist_body(S, Blk{m.b, m.nb}, -1LL, 1);
 }
 
 // Per-block FP64 partial sums of m v^2 / 2 and m v (fixed-order tree).
@@ -358,13 +431,21 @@ __global__ void __launch_bounds__(RX_THREADS) k_obs_sums(Sys S, double mass) {
   if (threadIdx.x < 4) S.red[4 * (size_t)blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
 }
 
+// Batched reaction steps clear each member's counters in a kernel.
+__global__ void kb_rx_begin(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const Sys& S = T[M[blockIdx.x].sys];
+  if (!S.has_rx || threadIdx.x != 0) return;
+  for (int q = 0; q < 4; ++q) S.ctl->trace[q] = 0;
+  S.ctl->n_active = 0u;
+}
+
 inline unsigned blocks_rx(uint32_t n) { return n ? (n + RX_THREADS - 1) / RX_THREADS : 1u; }
 
 }  // namespace
 
 int rx_kernel_count() { return 6; }
 
-void launch_rx(const Sys& S, const RxParams& R, cudaStream_t st, long long step_arg,
+void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
                void (*hook)(void*, const char*, int), void* ctx) {
   const unsigned g = blocks_rx(S.n);
   auto H = [&](const char* nm, int p) {
@@ -372,12 +453,12 @@ void launch_rx(const Sys& S, const RxParams& R, cudaStream_t st, long long step_
   };
   cudaMemsetAsync(&S.ctl->trace[0], 0, sizeof(long long) * 4 + sizeof(unsigned int), st);
   H("rx_compact", 0);
-  k_rx_compact<<<g, RX_THREADS, 0, st>>>(S, R);
+  k_rx_compact<<<g, RX_THREADS, 0, st>>>(S);
   H("rx_compact", 1);
   const unsigned gf = g < 1216u ? g : 1216u;
   H("rx_find", 0);
-  if (S.nl16) k_rx_find<true><<<gf, RX_THREADS, 0, st>>>(S, R, step_arg);
-  else k_rx_find<false><<<gf, RX_THREADS, 0, st>>>(S, R, step_arg);
+  if (S.nl16) k_rx_find<true><<<gf, RX_THREADS, 0, st>>>(S, step_arg);
+  else k_rx_find<false><<<gf, RX_THREADS, 0, st>>>(S, step_arg);
   H("rx_find", 1);
   H("rx_select_T", 0);
   if (S.nl16) k_rx_select_T<true><<<g, RX_THREADS, 0, st>>>(S, step_arg);
@@ -387,7 +468,7 @@ void launch_rx(const Sys& S, const RxParams& R, cudaStream_t st, long long step_
   k_rx_scan<<<1, 1024, 0, st>>>(S, g);
   H("rx_scan", 1);
   H("rx_apply", 0);
-  k_rx_apply<<<g, RX_THREADS, 0, st>>>(S, R, step_arg);
+  k_rx_apply<<<g, RX_THREADS, 0, st>>>(S, step_arg);
   H("rx_apply", 1);
   H("obs_hist", 0);
   k_obs_hist<<<g, RX_THREADS, 0, st>>>(S, step_arg, 1);
@@ -400,6 +481,16 @@ void launch_observables(const Sys& S, cudaStream_t st, int nblocks) {
   cudaMemsetAsync(&S.hist[S.hist_cap], 0, sizeof(HistRec), st);
   k_obs_hist<<<nblocks, RX_THREADS, 0, st>>>(S, -1, 0);
   k_obs_sums<<<nblocks, RX_THREADS, 0, st>>>(S, S.mass);
+}
+
+void launch_batch_rx(const BatchLaunch& L, cudaStream_t st) {
+  kb_rx_begin<<<L.n_one, 32, 0, st>>>(L.T, L.one);
+  kb_rx_compact<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
+  kb_rx_find<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
+  kb_rx_select_T<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
+  kb_rx_scan<<<L.n_one, 1024, 0, st>>>(L.T, L.one);
+  kb_rx_apply<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
+  kb_obs_hist<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
 }
 
 }  // namespace prx
