@@ -62,6 +62,7 @@ extern "C" {
 #define PRX_MAX_ADJ 8         /* largest adjacency capacity per particle */
 
 typedef struct prx_system prx_system; /* opaque, library-owned */
+typedef struct prx_batch prx_batch;   /* opaque, library-owned (see below) */
 
 /* System descriptor.  Units are reduced LJ units (Sec. II.C). */
 typedef struct {
@@ -256,6 +257,62 @@ int prx_react_noalloc(const prx_reaction_desc* rx, const double* box, double dt,
                       int8_t* d_state, uint32_t adj_cap, uint8_t* d_nadj, uint32_t* d_adj,
                       prx_bond* d_bonds_out, uint32_t bonds_cap, uint32_t* d_nbonds_out,
                       void* cuda_stream, prx_rx_trace* trace);
+
+/* ---- batched ensemble -------------------------------------------------------- */
+/* A batch advances many independent systems (replicas of different sizes,
+ * schemes, rates and seeds) together: every MD step is ONE kernel launch
+ * over all members, each block serving one part of one member; the
+ * neighbour-list rebuild and the reaction step are one launch per kernel
+ * too, in which members that need no rebuild (or have no reaction scheme)
+ * return at once.  The steps, rebuilds and reactions of a batch are replayed
+ * from CUDA graphs.  Every member computes exactly what it computes alone
+ * (prx_run): the same kernels on the same data, bit for bit.
+ *
+ * The paper runs one system at a time; batching is this library's addition
+ * for ensembles of replicas (the 32-seed kinetics averages of Sec. IV) and
+ * for serving many jobs on one GPU. */
+typedef struct {
+  uint32_t members;         /* systems in the batch */
+  uint32_t active;          /* members with at least one particle */
+  uint64_t particles;       /* sum of the members' particle counts */
+  uint64_t steps;           /* steps run by the batch */
+  uint64_t rebuilds;        /* steps after which some member rebuilt its lists */
+  uint64_t reactions;       /* reaction steps run */
+  uint64_t kernel_launches; /* kernels launched by the batch */
+  uint64_t graph_launches;  /* CUDA graph replays */
+} prx_batch_stats;
+
+/* Creates an empty batch whose work is queued on cuda_stream (NULL: a
+ * library-owned stream). */
+int prx_batch_create(void* cuda_stream, prx_batch** out);
+
+/* Waits for the batch, returns every member to standalone use (on its own
+ * stream, state kept) and frees the batch.  NULL is a no-op. */
+void prx_batch_destroy(prx_batch* b);
+
+/* Adds a system.  PRX_EINVAL when the system is in a batch already, uses
+ * PRX_FORCE_FP64 (batches run FP32 forces only), is being profiled, or has
+ * a reaction scheme whose Theta differs from that of the batch's reacting
+ * members or whose step is at another point of the Theta cycle.  The
+ * system's own stream is synchronised first.  While it is a member,
+ * prx_run, prx_react_once, prx_set_reaction, prx_compute_forces and
+ * prx_profile_begin on it return PRX_EINVAL; read-back calls and prx_save
+ * work and wait for the batch's stream. */
+int prx_batch_add(prx_batch* b, prx_system* sys);
+
+/* Waits for the batch and removes a member (PRX_EINVAL if it is not one). */
+int prx_batch_remove(prx_batch* b, prx_system* sys);
+
+/* Queues nsteps steps of every member (reactions every Theta steps as in
+ * prx_run) on the batch's stream and returns without waiting. */
+int prx_batch_run(prx_batch* b, uint64_t nsteps);
+
+/* Waits for the batch; returns the first non-zero member status (its index
+ * in *failed when failed != NULL, else -1 there). */
+int prx_batch_sync(prx_batch* b, int32_t* failed);
+
+int prx_batch_stats_get(prx_batch* b, prx_batch_stats* out);
+const char* prx_batch_last_error(const prx_batch* b);
 
 /* ---- errors ---------------------------------------------------------------- */
 const char* prx_last_error(const prx_system* sys);

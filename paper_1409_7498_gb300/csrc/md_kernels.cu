@@ -164,6 +164,7 @@ __device__ __forceinline__ void step_epilogue(const Sys& S, int ph, unsigned lon
       if (atomicAdd(&S.batch->done_step, 1u) == S.n_members - 1) {
         S.batch->done_step = 0u;
         const int flag = atomicExch(&S.batch->any_rebuild, 0);
+        if (flag) S.batch->rebuilds += 1ull;
         if (use_cond) cudaGraphSetConditional(cond, flag ? 1u : 0u);
       }
     }
@@ -469,12 +470,6 @@ __device__ __forceinline__ void count_keys_body(const Sys& S, const Blk blk) {
 }
 
 __global__ void k_count_keys(Sys S) { count_keys_body(S, Blk{blockIdx.x, gridDim.x}); }
-__global__ void kb_count_keys(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
-  const BlkMap m = M[blockIdx.x];
-  const Sys& S = T[m.sys];
-  if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
-  count_keys_body(S, Blk{m.b, m.nb});
-}
 
 // Exclusive scan of count[0..ncell) into cell_start[0..ncell], three passes.
 __device__ __forceinline__ void scan_tiles_body(const Sys& S, const Blk blk) {
@@ -974,6 +969,8 @@ void launch_batch_rebuild(const BatchLaunch& L, cudaStream_t st) {
   kb_rebin_remap<<<L.n_part, 256, 0, st>>>(L.T, L.part);
   kb_build_nlist<<<L.n_build, L.build_threads, L.build_smem, st>>>(L.T, L.build);
 }
+
+int batch_rebuild_kernel_count() { return 10; }
 
 int configure_batch_build_kernel(size_t smem_bytes) {
   return cudaFuncSetAttribute(kb_build_nlist, cudaFuncAttributeMaxDynamicSharedMemorySize,

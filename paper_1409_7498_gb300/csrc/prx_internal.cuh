@@ -96,7 +96,7 @@ struct RxParams {
 struct BatchCtl {
   int any_rebuild;          // some member needs a rebuild after this step
   unsigned int done_step;   // members whose step finished (last-member detection)
-  int pad0, pad1;
+  unsigned long long rebuilds;  // steps after which the rebuild pipeline ran
 };
 
 struct Sys {
@@ -309,6 +309,8 @@ void launch_batch_step(const BatchLaunch& L, cudaStream_t st, cudaGraphCondition
 void launch_batch_rebuild(const BatchLaunch& L, cudaStream_t st);
 void launch_batch_rx(const BatchLaunch& L, cudaStream_t st);
 int configure_batch_build_kernel(size_t smem_bytes);
+int batch_rebuild_kernel_count();
+int batch_rx_kernel_count();
 void launch_step(const Sys& S, cudaStream_t st, int fp64, int forces_only,
                  cudaGraphConditionalHandle h, int use_cond);
 void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, const char*, int),

@@ -60,6 +60,33 @@ struct prx_system {
   bool profiling = false;
   std::vector<ProfEvent> prof;
   std::string err;
+  prx_batch* batch = nullptr;      // batch this system belongs to, if any
+  cudaStream_t solo_stream = nullptr;  // the system's own stream while in a batch
+};
+
+// A batch: systems advanced together, one launch per kernel for all members.
+struct prx_batch {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap = nullptr;
+  std::vector<prx_system*> members;
+  uint64_t theta = 0;  // reaction interval shared by the reacting members (0: none)
+  uint64_t phase = 0;  // steps run mod theta
+  uint64_t steps = 0, kernel_steps = 0, graph_launches = 0, rx_runs = 0;
+  uint64_t rebuilds_seen = 0;  // device rebuild counter at the last table reset
+  // device tables (valid while `valid`)
+  BatchCtl* bctl = nullptr;
+  BatchCtl* bctl_host = nullptr;
+  Sys* T = nullptr;
+  size_t T_cap = 0;
+  BlkMap* maps = nullptr;
+  size_t maps_cap = 0;
+  BatchLaunch L{};
+  uint32_t n_active = 0;
+  bool any_rx = false;
+  cudaGraphExec_t g_step = nullptr, g_chunk = nullptr, g_react = nullptr;
+  bool valid = false;
+  std::string err;
 };
 
 namespace {
@@ -261,39 +288,61 @@ int full_rebin(prx_system* sys, int mode) {
   return PRX_OK;
 }
 
-int build_graph(prx_system* sys, int nsteps, bool with_rx, cudaGraphExec_t* out) {
+#define CE(call)                       \
+  do {                                 \
+    cudaError_t e_ = (call);           \
+    if (e_ != cudaSuccess) return e_;  \
+  } while (0)
+
+// Captures `nsteps` x (step, IF(rebuild)) followed optionally by the
+// reaction kernels into one executable graph.  `step(h)` launches the step
+// kernel(s) that set the conditional handle h; `rebuild()` and `rx()` the
+// rebuild and reaction sequences; all on the capture stream.
+template <class StepF, class RebuildF, class RxF>
+cudaError_t capture_graph(cudaStream_t cap, int nsteps, bool with_rx, StepF step, RebuildF rebuild,
+                          RxF rx, cudaGraphExec_t* out) {
   cudaGraph_t g;
-  CK(cudaGraphCreate(&g, 0));
+  CE(cudaGraphCreate(&g, 0));
   std::vector<cudaGraph_t> bodies;
-  CK(cudaStreamBeginCaptureToGraph(sys->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  CE(cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   for (int s = 0; s < nsteps; ++s) {
     cudaGraphConditionalHandle h;
-    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-    launch_step(sys->S, sys->cap, sys->d.force_precision == PRX_FORCE_FP64, 0, h, 1);
+    CE(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    step(h);
     cudaStreamCaptureStatus cs;
     cudaGraph_t gcap;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
-    CK(cudaStreamGetCaptureInfo(sys->cap, &cs, nullptr, &gcap, &deps, nullptr, &ndeps));
+    CE(cudaStreamGetCaptureInfo(cap, &cs, nullptr, &gcap, &deps, nullptr, &ndeps));
     cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
     np.conditional.handle = h;
     np.conditional.type = cudaGraphCondTypeIf;
     np.conditional.size = 1;
     cudaGraphNode_t cn;
-    CK(cudaGraphAddNode(&cn, gcap, deps, nullptr, ndeps, &np));
+    CE(cudaGraphAddNode(&cn, gcap, deps, nullptr, ndeps, &np));
     bodies.push_back(np.conditional.phGraph_out[0]);
-    CK(cudaStreamUpdateCaptureDependencies(sys->cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CE(cudaStreamUpdateCaptureDependencies(cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
   }
-  if (with_rx) launch_rx(sys->S, sys->cap, -1, nullptr, nullptr);
-  CK(cudaStreamEndCapture(sys->cap, &g));
+  if (with_rx) rx();
+  CE(cudaStreamEndCapture(cap, &g));
   for (cudaGraph_t body : bodies) {
-    CK(cudaStreamBeginCaptureToGraph(sys->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    launch_rebin(sys->S, sys->cap, 0, nullptr, nullptr);
+    CE(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    rebuild();
     cudaGraph_t tmp;
-    CK(cudaStreamEndCapture(sys->cap, &tmp));
+    CE(cudaStreamEndCapture(cap, &tmp));
   }
-  CK(cudaGraphInstantiate(out, g, 0));
-  CK(cudaGraphDestroy(g));
+  CE(cudaGraphInstantiate(out, g, 0));
+  CE(cudaGraphDestroy(g));
+  return cudaSuccess;
+}
+
+int build_graph(prx_system* sys, int nsteps, bool with_rx, cudaGraphExec_t* out) {
+  const bool fp64 = sys->d.force_precision == PRX_FORCE_FP64;
+  CK(capture_graph(
+      sys->cap, nsteps, with_rx,
+      [&](cudaGraphConditionalHandle h) { launch_step(sys->S, sys->cap, fp64, 0, h, 1); },
+      [&] { launch_rebin(sys->S, sys->cap, 0, nullptr, nullptr); },
+      [&] { launch_rx(sys->S, sys->cap, -1, nullptr, nullptr); }, out));
   return PRX_OK;
 }
 
@@ -598,6 +647,120 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
   return PRX_OK;
 }
 
+int bfail(prx_batch* b, int code, const std::string& msg) {
+  b->err = msg;
+  return code;
+}
+
+#define CKB(call)                                                                      \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return bfail(b, PRX_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+  } while (0)
+
+void batch_destroy_graphs(prx_batch* b) {
+  if (b->g_step) cudaGraphExecDestroy(b->g_step);
+  if (b->g_chunk) cudaGraphExecDestroy(b->g_chunk);
+  if (b->g_react) cudaGraphExecDestroy(b->g_react);
+  b->g_step = b->g_chunk = b->g_react = nullptr;
+}
+
+// Member table, block maps and graphs of a batch after its membership
+// changed.  Each active member (n > 0) gets a copy of its Sys marked as a
+// batch member; every kernel family gets a block map listing, per block,
+// the member and the block's index within that member's own grid (the grid
+// the member would be launched with alone).
+int batch_prepare(prx_batch* b) {
+  if (b->valid) return PRX_OK;
+  CKB(cudaStreamSynchronize(b->stream));
+  batch_destroy_graphs(b);
+  CKB(cudaMemcpy(b->bctl_host, b->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost));
+  b->rebuilds_seen += b->bctl_host->rebuilds;
+  CKB(cudaMemset(b->bctl, 0, sizeof(BatchCtl)));
+  std::vector<Sys> table;
+  b->any_rx = false;
+  for (prx_system* m : b->members) {
+    if (!m->S.n) continue;
+    table.push_back(m->S);
+    b->any_rx = b->any_rx || m->has_rx;
+  }
+  b->n_active = (uint32_t)table.size();
+  if (!b->n_active) {
+    b->valid = true;
+    return PRX_OK;
+  }
+  std::vector<BlkMap> part, cell, tile, one, build;
+  auto add = [](std::vector<BlkMap>& v, uint32_t sys, uint64_t nb) {
+    if (nb == 0) nb = 1;
+    for (uint64_t q = 0; q < nb; ++q) v.push_back(BlkMap{sys, (uint32_t)q, (uint32_t)nb, 0u});
+  };
+  int build_threads = 32;
+  size_t build_smem = 0;
+  for (uint32_t q = 0; q < b->n_active; ++q) {
+    Sys& S = table[q];
+    S.in_batch = 1;
+    S.batch = b->bctl;
+    S.n_members = b->n_active;
+    add(part, q, (S.n + 255) / 256);
+    add(cell, q, ((uint64_t)S.ncell + 255) / 256);
+    add(tile, q, ((uint64_t)S.ncell + SCAN_TILE - 1) / SCAN_TILE);
+    add(one, q, 1);
+    add(build, q, (uint64_t)S.tiles_y * S.nc[2]);
+    build_threads = std::max(build_threads, S.tile_threads);
+    build_smem = std::max(build_smem, build_tile_smem(S));
+  }
+  const size_t nmaps = part.size() + cell.size() + tile.size() + one.size() + build.size();
+  if (b->n_active > b->T_cap) {
+    if (b->T) cudaFree(b->T);
+    b->T = nullptr;
+    b->T_cap = 0;
+    CKB(cudaMalloc(&b->T, sizeof(Sys) * b->n_active));
+    b->T_cap = b->n_active;
+  }
+  if (nmaps > b->maps_cap) {
+    if (b->maps) cudaFree(b->maps);
+    b->maps = nullptr;
+    b->maps_cap = 0;
+    CKB(cudaMalloc(&b->maps, sizeof(BlkMap) * nmaps));
+    b->maps_cap = nmaps;
+  }
+  std::vector<BlkMap> all;
+  all.reserve(nmaps);
+  BatchLaunch& L = b->L;
+  L.T = b->T;
+  auto place = [&](std::vector<BlkMap>& v, const BlkMap** ptr, unsigned* cnt) {
+    *ptr = b->maps + all.size();
+    *cnt = (unsigned)v.size();
+    all.insert(all.end(), v.begin(), v.end());
+  };
+  place(part, &L.part, &L.n_part);
+  place(cell, &L.cell, &L.n_cell);
+  place(tile, &L.tile, &L.n_tile);
+  place(one, &L.one, &L.n_one);
+  place(build, &L.build, &L.n_build);
+  L.build_threads = build_threads;
+  L.build_smem = build_smem;
+  CKB(cudaMemcpy(b->T, table.data(), sizeof(Sys) * table.size(), cudaMemcpyHostToDevice));
+  CKB(cudaMemcpy(b->maps, all.data(), sizeof(BlkMap) * all.size(), cudaMemcpyHostToDevice));
+  if (configure_batch_build_kernel(build_smem))
+    return bfail(b, PRX_ECUDA, "list-build shared memory of " + std::to_string(build_smem) + " bytes refused");
+  const int chunk = b->any_rx ? (int)b->theta : kNoRxChunk;
+  auto step = [&](cudaGraphConditionalHandle h) { launch_batch_step(L, b->cap, h, 1); };
+  auto rebuild = [&] { launch_batch_rebuild(L, b->cap); };
+  auto rx = [&] { launch_batch_rx(L, b->cap); };
+  CKB(capture_graph(b->cap, 1, false, step, rebuild, rx, &b->g_step));
+  CKB(capture_graph(b->cap, chunk, b->any_rx, step, rebuild, rx, &b->g_chunk));
+  if (b->any_rx) CKB(capture_graph(b->cap, 0, true, step, rebuild, rx, &b->g_react));
+  b->valid = true;
+  return PRX_OK;
+}
+
+// Calls that would change a batch member on its own are refused.
+int refuse_member(prx_system* sys) {
+  return fail(sys, PRX_EINVAL, "not allowed while the system is a member of a batch");
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -649,6 +812,7 @@ int prx_create(const prx_system_desc* desc, const double* pos, const double* vel
 
 void prx_destroy(prx_system* sys) {
   if (!sys) return;
+  if (sys->batch) prx_batch_remove(sys->batch, sys);
   if (sys->stream) cudaStreamSynchronize(sys->stream);
   destroy_graphs(sys);
   for (auto& e : sys->prof) {
@@ -665,6 +829,7 @@ void prx_destroy(prx_system* sys) {
 
 int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx) {
   if (!sys) return PRX_EINVAL;
+  if (sys->batch) return refuse_member(sys);
   if (!rx) {
     sys->has_rx = 0;
     sys->S.has_rx = 0;
@@ -703,6 +868,7 @@ int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx) {
 
 int prx_run(prx_system* sys, uint64_t nsteps) {
   if (!sys) return PRX_EINVAL;
+  if (sys->batch) return refuse_member(sys);
   if (sys->S.n == 0) {
     sys->host_step += nsteps;
     return PRX_OK;
@@ -745,6 +911,7 @@ int prx_sync(prx_system* sys) {
 
 int prx_react_once(prx_system* sys, uint64_t step, prx_rx_trace* trace) {
   if (!sys) return PRX_EINVAL;
+  if (sys->batch) return refuse_member(sys);
   if (!sys->has_rx) return fail(sys, PRX_EINVAL, "no reaction scheme set");
   if (sys->S.n) {
     launch_rx(sys->S, sys->stream, (long long)step, sys->profiling ? prof_hook : nullptr, sys);
@@ -764,6 +931,7 @@ int prx_react_once(prx_system* sys, uint64_t step, prx_rx_trace* trace) {
 
 int prx_compute_forces(prx_system* sys, double* f_out, double* epot_out) {
   if (!sys || (!f_out && sys->S.n)) return PRX_EINVAL;
+  if (sys->batch) return refuse_member(sys);
   const size_t n = sys->S.n;
   if (!n) {
     if (epot_out) *epot_out = 0.0;
@@ -795,7 +963,7 @@ int prx_compute_forces(prx_system* sys, double* f_out, double* epot_out) {
 int prx_get_step(prx_system* sys, uint64_t* step) {
   if (!sys || !step) return PRX_EINVAL;
   int rc = sync_status(sys);
-  *step = sys->ctl_host->step;
+  *step = sys->S.n ? sys->ctl_host->step : sys->host_step;  // an empty system launches nothing
   return rc;
 }
 
@@ -937,6 +1105,7 @@ int prx_get_stats(prx_system* sys, prx_stats* out) {
 
 int prx_profile_begin(prx_system* sys) {
   if (!sys) return PRX_EINVAL;
+  if (sys->batch) return refuse_member(sys);
   CK(cudaStreamSynchronize(sys->stream));
   for (auto& e : sys->prof) {
     cudaEventDestroy(e.a);
@@ -1139,5 +1308,167 @@ int prx_load(const char* path, void* cuda_stream, prx_system** out) {
   *out = sys;
   return PRX_OK;
 }
+
+// ---- batched ensemble ---------------------------------------------------------
+
+int prx_batch_create(void* cuda_stream, prx_batch** out) {
+  if (!out) return PRX_EINVAL;
+  *out = nullptr;
+  prx_batch* b = new (std::nothrow) prx_batch();
+  if (!b) return PRX_ENOMEM;
+  bool ok = true;
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else {
+    ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess;
+    b->own_stream = ok;
+  }
+  ok = ok && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->bctl, sizeof(BatchCtl)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&b->bctl_host, sizeof(BatchCtl)) == cudaSuccess;
+  ok = ok && cudaMemset(b->bctl, 0, sizeof(BatchCtl)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    g_create_error = "batch creation failed (stream or device memory)";
+    prx_batch_destroy(b);
+    return PRX_ECUDA;
+  }
+  *out = b;
+  return PRX_OK;
+}
+
+void prx_batch_destroy(prx_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (prx_system* m : b->members) {
+    m->stream = m->solo_stream;
+    m->batch = nullptr;
+  }
+  batch_destroy_graphs(b);
+  if (b->T) cudaFree(b->T);
+  if (b->maps) cudaFree(b->maps);
+  if (b->bctl) cudaFree(b->bctl);
+  if (b->bctl_host) cudaFreeHost(b->bctl_host);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+int prx_batch_add(prx_batch* b, prx_system* sys) {
+  if (!b || !sys) return PRX_EINVAL;
+  if (sys->batch) return bfail(b, PRX_EINVAL, "system is already a member of a batch");
+  if (sys->d.force_precision != PRX_FORCE_FP32)
+    return bfail(b, PRX_EINVAL, "batches run PRX_FORCE_FP32 systems only");
+  if (sys->profiling) return bfail(b, PRX_EINVAL, "system is being profiled");
+  if (sys->has_rx) {
+    const uint64_t th = sys->rxd.theta;
+    if (b->theta && th != b->theta)
+      return bfail(b, PRX_EINVAL, "reaction interval differs from the batch's");
+    if (b->theta && sys->host_step % th != b->phase)
+      return bfail(b, PRX_EINVAL, "system is at another point of the reaction cycle");
+  }
+  if (cudaStreamSynchronize(sys->stream) != cudaSuccess)
+    return bfail(b, PRX_ECUDA, "synchronising the system's stream failed");
+  if (sys->has_rx && !b->theta) {
+    b->theta = sys->rxd.theta;
+    b->phase = sys->host_step % b->theta;
+  }
+  sys->solo_stream = sys->stream;
+  sys->stream = b->stream;
+  sys->batch = b;
+  b->members.push_back(sys);
+  b->valid = false;
+  return PRX_OK;
+}
+
+int prx_batch_remove(prx_batch* b, prx_system* sys) {
+  if (!b || !sys || sys->batch != b) return PRX_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return bfail(b, PRX_ECUDA, "synchronising the batch stream failed");
+  b->members.erase(std::find(b->members.begin(), b->members.end(), sys));
+  sys->stream = sys->solo_stream;
+  sys->batch = nullptr;
+  b->valid = false;
+  bool rx = false;
+  for (prx_system* m : b->members) rx = rx || m->has_rx;
+  if (!rx) b->theta = 0, b->phase = 0;
+  return PRX_OK;
+}
+
+int prx_batch_run(prx_batch* b, uint64_t nsteps) {
+  if (!b) return PRX_EINVAL;
+  int rc = batch_prepare(b);
+  if (rc) return rc;
+  const uint64_t total = nsteps;
+  if (b->n_active) {
+    const uint64_t theta = b->any_rx ? b->theta : (uint64_t)kNoRxChunk;
+    uint64_t ph = b->any_rx ? b->phase : 0;
+    while (nsteps > 0) {
+      cudaError_t e;
+      if (ph == 0 && nsteps >= theta) {
+        e = cudaGraphLaunch(b->g_chunk, b->stream);
+        nsteps -= theta;
+        if (b->any_rx) b->rx_runs++;
+      } else {
+        e = cudaGraphLaunch(b->g_step, b->stream);
+        nsteps--;
+        ph = (ph + 1) % theta;
+        if (b->any_rx && ph == 0 && e == cudaSuccess) {
+          e = cudaGraphLaunch(b->g_react, b->stream);
+          b->graph_launches++;
+          b->rx_runs++;
+        }
+      }
+      if (e != cudaSuccess) return bfail(b, PRX_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+      b->graph_launches++;
+    }
+  }
+  b->steps += total;
+  if (b->theta) b->phase = (b->phase + total) % b->theta;
+  if (b->n_active) b->kernel_steps += total;
+  for (prx_system* m : b->members) m->host_step += total;
+  return PRX_OK;
+}
+
+int prx_batch_sync(prx_batch* b, int32_t* failed) {
+  if (failed) *failed = -1;
+  if (!b) return PRX_EINVAL;
+  for (prx_system* m : b->members)
+    if (cudaMemcpyAsync(m->ctl_host, m->S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+      return bfail(b, PRX_ECUDA, "reading a member's control block failed");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, PRX_ECUDA, std::string("batch stream: ") + cudaGetErrorString(e));
+  for (size_t q = 0; q < b->members.size(); ++q) {
+    const int st = b->members[q]->ctl_host->status;
+    if (st) {
+      if (failed) *failed = (int32_t)q;
+      b->members[q]->err = std::string("device reported ") + prx_status_string(st);
+      return bfail(b, st, "member " + std::to_string(q) + ": device reported " + prx_status_string(st));
+    }
+  }
+  return PRX_OK;
+}
+
+int prx_batch_stats_get(prx_batch* b, prx_batch_stats* out) {
+  if (!b || !out) return PRX_EINVAL;
+  memset(out, 0, sizeof(*out));
+  cudaError_t e = cudaMemcpyAsync(b->bctl_host, b->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, PRX_ECUDA, std::string("batch stream: ") + cudaGetErrorString(e));
+  out->members = (uint32_t)b->members.size();
+  for (prx_system* m : b->members) {
+    out->particles += m->S.n;
+    if (m->S.n) out->active++;
+  }
+  out->steps = b->steps;
+  out->rebuilds = b->rebuilds_seen + b->bctl_host->rebuilds;
+  out->reactions = b->rx_runs;
+  out->kernel_launches = b->kernel_steps + out->rebuilds * (uint64_t)batch_rebuild_kernel_count() +
+                         b->rx_runs * (uint64_t)batch_rx_kernel_count();
+  out->graph_launches = b->graph_launches;
+  return PRX_OK;
+}
+
+const char* prx_batch_last_error(const prx_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
 
 }  // extern "C"

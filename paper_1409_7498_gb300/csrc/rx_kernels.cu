@@ -483,6 +483,8 @@ void launch_observables(const Sys& S, cudaStream_t st, int nblocks) {
   k_obs_sums<<<nblocks, RX_THREADS, 0, st>>>(S, S.mass);
 }
 
+int batch_rx_kernel_count() { return 7; }
+
 void launch_batch_rx(const BatchLaunch& L, cudaStream_t st) {
   kb_rx_begin<<<L.n_one, 32, 0, st>>>(L.T, L.one);
   kb_rx_compact<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);

@@ -75,6 +75,12 @@ class prx_stats(C.Structure):
                 ("cells", C.c_uint32 * 3), ("cell_edge", C.c_double * 3)]
 
 
+class prx_batch_stats(C.Structure):
+    _fields_ = [("members", C.c_uint32), ("active", C.c_uint32), ("particles", C.c_uint64),
+                ("steps", C.c_uint64), ("rebuilds", C.c_uint64), ("reactions", C.c_uint64),
+                ("kernel_launches", C.c_uint64), ("graph_launches", C.c_uint64)]
+
+
 class prx_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
 
@@ -116,6 +122,14 @@ def lib():
         "prx_react_noalloc": ([P(prx_reaction_desc), P(C.c_double), C.c_double, U64, U64,
                                C.c_uint32, VP, VP, VP, C.c_uint32, VP, VP, VP, C.c_uint32, VP,
                                VP, P(prx_rx_trace)], I),
+        "prx_batch_create": ([VP, P(VP)], I),
+        "prx_batch_destroy": ([VP], None),
+        "prx_batch_add": ([VP, VP], I),
+        "prx_batch_remove": ([VP, VP], I),
+        "prx_batch_run": ([VP, U64], I),
+        "prx_batch_sync": ([VP, P(C.c_int32)], I),
+        "prx_batch_stats_get": ([VP, P(prx_batch_stats)], I),
+        "prx_batch_last_error": ([VP], C.c_char_p),
         "prx_last_error": ([VP], C.c_char_p),
         "prx_status_string": ([I], C.c_char_p),
     }
@@ -318,6 +332,95 @@ def prx_react_noalloc(rx, box, dt, seed, step, n, d_pos, d_type, d_state, adj_ca
         raise PolyrxError(rc, lib().prx_status_string(rc).decode())
     return dict(candidates=t.candidates, retained=t.retained, a_winners=t.a_winners,
                 formed=t.formed)
+
+
+def _bcheck(rc: int, b=None):
+    if rc != PRX_OK:
+        msg = lib().prx_batch_last_error(b)
+        raise PolyrxError(rc, (msg or b"").decode() or lib().prx_status_string(rc).decode())
+
+
+def prx_batch_create(stream=None):
+    h = C.c_void_p()
+    _bcheck(lib().prx_batch_create(C.c_void_p(stream) if stream else None, C.byref(h)))
+    return h.value
+
+
+def prx_batch_destroy(b):
+    lib().prx_batch_destroy(b)
+
+
+def prx_batch_add(b, h):
+    _bcheck(lib().prx_batch_add(b, h), b)
+
+
+def prx_batch_remove(b, h):
+    _bcheck(lib().prx_batch_remove(b, h), b)
+
+
+def prx_batch_run(b, nsteps: int):
+    _bcheck(lib().prx_batch_run(b, int(nsteps)), b)
+
+
+def prx_batch_sync(b):
+    """Waits for the batch; raises PolyrxError (with .member set) on a member's status."""
+    failed = C.c_int32(-1)
+    rc = lib().prx_batch_sync(b, C.byref(failed))
+    if rc != PRX_OK:
+        msg = lib().prx_batch_last_error(b)
+        e = PolyrxError(rc, (msg or b"").decode() or lib().prx_status_string(rc).decode())
+        e.member = failed.value
+        raise e
+
+
+def prx_batch_stats_get(b) -> dict:
+    st = prx_batch_stats()
+    _bcheck(lib().prx_batch_stats_get(b, C.byref(st)), b)
+    return {k: getattr(st, k) for k, _ in prx_batch_stats._fields_}
+
+
+class Batch:
+    """Owning handle over one prx_batch.  Members are System objects; the
+    batch keeps them alive while they are members."""
+
+    def __init__(self, stream=None):
+        self.h = prx_batch_create(stream)
+        self.members = []
+
+    def add(self, system):
+        prx_batch_add(self.h, system.h)
+        self.members.append(system)
+
+    def remove(self, system):
+        prx_batch_remove(self.h, system.h)
+        self.members.remove(system)
+
+    def run(self, nsteps):
+        prx_batch_run(self.h, nsteps)
+
+    def sync(self):
+        prx_batch_sync(self.h)
+
+    def stats(self):
+        return prx_batch_stats_get(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            prx_batch_destroy(self.h)
+            self.h = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class System:

@@ -156,6 +156,31 @@ def chain_growth_scheme(k: float, theta: int = 10, r_react: float = 1.1,
                 max_valence=tuple(mv))
 
 
+CHAIN_PHI0 = 328 / 33_096  # initiator fraction of the chain-growth workload
+
+
+def ensemble_specs(replicas: int, n_lo: int, n_hi: int, k_lo: float, k_hi: float,
+                   seed: int) -> list:
+    """Replicas of the batched-ensemble workload: size and rate log-uniform,
+    step growth (f = 4) or chain growth with equal odds, one seed each."""
+    rng = np.random.default_rng(seed)
+    n = log_uniform_int(rng, n_lo, n_hi, replicas)
+    k = np.exp(rng.uniform(math.log(k_lo), math.log(k_hi), replicas))
+    kind = rng.integers(0, 2, replicas)
+    return [dict(kind="step" if kind[r] == 0 else "chain", n=int(n[r]), k=float(k[r]),
+                 seed=seed + 1 + r) for r in range(replicas)]
+
+
+def replica(spec: dict, theta: int = 10):
+    """(Inputs, scheme, adjacency capacity) of one ensemble replica."""
+    if spec["kind"] == "step":
+        return (step_growth_sites(spec["n"], 4, spec["seed"]),
+                step_growth_scheme(4, spec["k"], theta), 4)
+    n_init = max(1, int(round(CHAIN_PHI0 * spec["n"])))
+    return (chain_growth(spec["n"] - n_init, n_init, spec["seed"]),
+            chain_growth_scheme(spec["k"], theta), 2)
+
+
 # The five workloads, by size.  Physical parameters shared by all of them:
 # sigma = eps = m = 1, kT = 1, gamma = 1, dt = 0.005, FENE k = 30, R0 = 1.5,
 # r_react = 1.1, Theta = 10, rho = 0.85.

@@ -32,13 +32,15 @@ def test_exports_every_declared_symbol(P):
     missing = [n for n in names if not hasattr(L, n)]
     assert not missing, missing
     # the binding wraps every one of them under the same name
-    wrapped = [n for n in names if n not in ("prx_last_error", "prx_status_string")]
+    wrapped = [n for n in names
+               if n not in ("prx_last_error", "prx_status_string", "prx_batch_last_error")]
     assert all(hasattr(P, n) for n in wrapped), [n for n in wrapped if not hasattr(P, n)]
 
 
 def test_struct_layouts_match_header(P):
     structs = ["prx_system_desc", "prx_reaction_desc", "prx_bond", "prx_rx_trace",
-               "prx_observables", "prx_history_record", "prx_stats", "prx_kernel_time"]
+               "prx_observables", "prx_history_record", "prx_stats", "prx_kernel_time",
+               "prx_batch_stats"]
     src = "#include <stdio.h>\n#include \"polyrx.h\"\nint main(void){\n" + "".join(
         f'printf("%zu\\n", sizeof({s}));\n' for s in structs) + "return 0;}\n"
     with tempfile.TemporaryDirectory() as d:
@@ -49,7 +51,7 @@ def test_struct_layouts_match_header(P):
         sizes = [int(v) for v in subprocess.check_output([exe]).split()]
     py = [C.sizeof(P.prx_system_desc), C.sizeof(P.prx_reaction_desc), C.sizeof(P.prx_bond),
           C.sizeof(P.prx_rx_trace), C.sizeof(P.prx_observables), P.HISTORY_DTYPE.itemsize,
-          C.sizeof(P.prx_stats), C.sizeof(P.prx_kernel_time)]
+          C.sizeof(P.prx_stats), C.sizeof(P.prx_kernel_time), C.sizeof(P.prx_batch_stats)]
     assert sizes == py
     assert P.BOND_DTYPE.itemsize == C.sizeof(P.prx_bond)
 
@@ -70,8 +72,8 @@ def test_library_has_no_cpu_fallback_path():
     kernels = set()
     for f in os.listdir(csrc):
         if f.endswith(".cu"):
-            kernels |= set(re.findall(r"__global__[^;{]*?\b(k_\w+)\s*\(", open(os.path.join(csrc, f)).read()))
-    for k in ["k_step_nl", "k_build_nlist", "k_forces64", "k_integrate64", "k_rebin_keys", "k_rebin_permute", "k_rx_find", "k_rx_select_T",
+            kernels |= set(re.findall(r"__global__[^;{]*?\b(kb?_\w+)\s*\(", open(os.path.join(csrc, f)).read()))
+    for k in ["k_step_nl", "kb_step_nl", "kb_build_nlist", "kb_rx_find", "k_build_nlist", "k_forces64", "k_integrate64", "k_rebin_keys", "k_rebin_permute", "k_rx_find", "k_rx_select_T",
               "k_rx_apply", "k_obs_hist"]:
         assert k in kernels
     binding = open(os.path.join(ROOT, "paper_1409_7498_gb300", "polyrx.py")).read()
