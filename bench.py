@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     ap.add_argument("--direct", action="store_true",
                     help="launch kernels one by one instead of CUDA graphs (for ncu launch lists)")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the batched-ensemble measurement")
+    ap.add_argument("--ensemble-steps", type=int, default=20,
+                    help="timed reaction intervals of the ensemble measurement")
     return ap.parse_args()
 
 
@@ -142,6 +146,92 @@ def cpu_baseline(budget_s: float) -> dict:
     return {"value": inp.n * steps / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
             "sample": f"{steps} MD steps of the {inp.n}-bead step-growth workload "
                       f"(reaction every {THETA} steps), FP64, one thread, {el:.1f} s"}
+
+
+ENSEMBLE = synth.WORKLOADS["ensemble_256"]
+
+
+def ensemble(P, torch, steps: int, warmup: int = 3) -> dict:
+    """Batched ensemble (256 replicas, sizes log-uniform in 1,024-65,536
+    beads, step or chain growth, k log-uniform in [0.01, 1], own seeds)
+    advanced together by one prx_batch, against the same replicas run one at
+    a time through prx_run (each run to completion and synchronised before
+    the next starts).  Both legs time the same number of MD steps per replica
+    from the same state; wall clock around each leg.  A sample of replicas is
+    then re-run alone from the initial inputs for the same total number of
+    steps and compared bit for bit with the replicas that went through the
+    batch (same accuracy: identical results)."""
+    W = ENSEMBLE
+    specs = synth.ensemble_specs(W["replicas"], W["n_lo"], W["n_hi"], W["k_lo"], W["k_hi"],
+                                 synth.BASE_SEED)
+    reps = []
+    for sp in specs:
+        inp, sch, cap = synth.replica(sp)
+        desc = P.make_desc(inp.n, inp.L, adj_cap=cap, seed=sp["seed"])
+        g = P.System(desc, inp.x, inp.v, inp.type, inp.state)
+        g.set_reaction(P.make_reaction(**sch))
+        reps.append((sp, g))
+    beads = sum(sp["n"] for sp in specs)
+    nrep = len(reps)
+    md_steps = steps * THETA
+    stream = torch.cuda.Stream()
+    b = P.Batch(stream=stream.cuda_stream)
+    for _, g in reps:
+        b.add(g)
+    b.run(warmup * THETA)
+    b.sync()
+    st0 = b.stats()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    b.run(md_steps)
+    ev1.record(stream)
+    b.sync()
+    t_batch = time.perf_counter() - t0
+    ms_batch = ev0.elapsed_time(ev1)
+    st1 = b.stats()
+    b.close()
+    # the same replicas, one job at a time
+    for _, g in reps:  # untimed: builds each replica's graphs
+        g.run(THETA)
+        g.sync()
+    t0 = time.perf_counter()
+    for _, g in reps:
+        g.run(md_steps)
+        g.sync()
+    t_plain = time.perf_counter() - t0
+    total = (warmup + steps + 1 + steps) * THETA
+    # same accuracy: a sample re-run alone from the initial inputs
+    sample = sorted(range(nrep), key=lambda r: specs[r]["n"])[:: max(1, nrep // 4)][:4]
+    identical = True
+    for r in sample:
+        sp, g = reps[r]
+        inp, sch, cap = synth.replica(sp)
+        desc = P.make_desc(inp.n, inp.L, adj_cap=cap, seed=sp["seed"])
+        with P.System(desc, inp.x, inp.v, inp.type, inp.state) as a:
+            a.set_reaction(P.make_reaction(**sch))
+            a.run(total)
+            identical &= bool(np.array_equal(a.positions(), g.positions())
+                              and np.array_equal(a.states(), g.states())
+                              and np.array_equal(np.sort(a.bonds(), order=["step", "a", "t"]),
+                                                 np.sort(g.bonds(), order=["step", "a", "t"])))
+    for _, g in reps:
+        g.close()
+    rs_batch = nrep * md_steps / t_batch
+    rs_plain = nrep * md_steps / t_plain
+    return {"workload": "ensemble_256", "replicas": nrep, "beads_total": beads,
+            "md_steps_per_replica": md_steps, "unit": "replica-steps/s",
+            "batched": {"value": rs_batch, "particle_steps_per_s": beads * md_steps / t_batch,
+                        "device_ms": ms_batch, "wall_s": t_batch,
+                        "kernel_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
+                        "rebuild_steps": int(st1["rebuilds"] - st0["rebuilds"])},
+            "plain": {"value": rs_plain, "particle_steps_per_s": beads * md_steps / t_plain,
+                      "wall_s": t_plain, "how": "each replica through prx_run, synchronised "
+                                                "before the next starts"},
+            "speedup": rs_batch / rs_plain, "identical": identical,
+            "identical_sample": [specs[r]["n"] for r in sample],
+            "l2": "not flushed: the ensemble state (~1 GB) exceeds L2"}
 
 
 def run_reference(args, rank, world):
@@ -298,6 +388,10 @@ def main():
                                         "read-back, final states and bonds, destroy"}
         del ob
 
+    ens = None
+    if world == 1 and not args.no_ensemble:
+        ens = ensemble(P, torch, args.ensemble_steps)
+
     if world > 1:
         dist.barrier()
     if rank == 0:
@@ -323,7 +417,7 @@ def main():
                          "top_kernel": top["name"],
                          "kernel_ms": {r["name"]: round(r["total_ms"], 4) for r in prof},
                          "kernel_launches": {r["name"]: r["launches"] for r in prof}},
-            "e2e": e2e, "cpu_baseline": cpu,
+            "e2e": e2e, "cpu_baseline": cpu, "ensemble": ens,
         }
         print(json.dumps(line), flush=True)
     g.close()

@@ -11,6 +11,7 @@
 //   position comes from x' through integer operations on its binary64
 //   fields, so the FP64 pipe (about 70x slower than FP32 on this part) sees
 //   only the six DFMAs.
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "prx_internal.cuh"
@@ -891,15 +892,34 @@ size_t build_tile_smem(const Sys& S) {
          4 * (size_t)TILE_ROWS_MAX * (S.nc[0] + 1);
 }
 
-int configure_build_kernel(size_t smem_bytes) {
-  if (cudaFuncSetAttribute(k_build_nlist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_bytes) != cudaSuccess)
-    return -1;
-  if (cudaFuncSetAttribute(k_build_nlist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_bytes) != cudaSuccess)
-    return -1;
+// The dynamic shared-memory limit is an attribute of the kernel (per device),
+// shared by every system: it only ever grows, to the largest tile any system
+// on the device has asked for, so that systems of different sizes coexist.
+namespace {
+std::mutex g_smem_mu;
+size_t g_smem_set[2][64];  // [single, batched][device]
+int raise_smem_limit(int which, size_t bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  if (bytes <= g_smem_set[which][dev]) return 0;
+  bool ok;
+  if (which == 0) {
+    ok = cudaFuncSetAttribute(k_build_nlist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(k_build_nlist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes) == cudaSuccess;
+  } else {
+    ok = cudaFuncSetAttribute(kb_build_nlist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes) == cudaSuccess;
+  }
+  if (!ok) return -1;
+  g_smem_set[which][dev] = bytes;
   return 0;
 }
+}  // namespace
+
+int configure_build_kernel(size_t smem_bytes) { return raise_smem_limit(0, smem_bytes); }
 
 int rebin_kernel_count() { return 9; }
 
@@ -972,9 +992,6 @@ void launch_batch_rebuild(const BatchLaunch& L, cudaStream_t st) {
 
 int batch_rebuild_kernel_count() { return 10; }
 
-int configure_batch_build_kernel(size_t smem_bytes) {
-  return cudaFuncSetAttribute(kb_build_nlist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_bytes) == cudaSuccess ? 0 : -1;
-}
+int configure_batch_build_kernel(size_t smem_bytes) { return raise_smem_limit(1, smem_bytes); }
 
 }  // namespace prx

@@ -183,3 +183,20 @@ def test_batch_reports_the_failing_member(P):
     finally:
         for g in (good, bad, empty):
             g.close()
+
+
+def test_systems_of_different_sizes_coexist(P):
+    """A larger system created before a smaller one still runs alone: the
+    list-build kernel's shared-memory limit is shared by every system."""
+    big = make(P, dict(kind="step", n=60000, k=0.1, seed=41))
+    small = make(P, dict(kind="step", n=1100, k=0.1, seed=42))
+    try:
+        big.run(30)
+        small.run(30)
+        big.sync()
+        small.sync()
+        assert big.step() == 30 and small.step() == 30
+        assert big.stats()["rebins"] > 1
+    finally:
+        big.close()
+        small.close()
