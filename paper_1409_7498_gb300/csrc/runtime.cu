@@ -788,18 +788,31 @@ const char* prx_last_error(const prx_system* sys) { return sys ? sys->err.c_str(
 
 int prx_estimate_bytes(const prx_system_desc* desc, uint64_t* bytes) {
   if (!desc || !bytes) return PRX_EINVAL;
+  // mirrors the allocations of prx_create and of the cell grid / Verlet
+  // list set up for the WCA cutoff (a larger reaction cutoff grows the list)
   const uint64_t n = desc->n, cap = desc->adj_cap ? desc->adj_cap : 1;
   const double rc = std::pow(2.0, 1.0 / 6.0) * desc->wca_sigma;
-  const double skin = desc->skin < 0.0 ? kDefaultSkin : desc->skin;
+  double skin = desc->skin < 0.0 ? kDefaultSkin : desc->skin;
+  const double Lmin = std::min(desc->box[0], std::min(desc->box[1], desc->box[2]));
+  if (Lmin / (rc + skin) < 3.0) skin = std::max(0.02, Lmin / 3.0 - rc);
+  const double rv = rc + skin;
   uint64_t ncell = 1;
+  int nc[3];
   for (int k = 0; k < 3; ++k) {
-    int nc = (int)std::floor(desc->box[k] / (rc + skin));
-    nc = std::max(3, std::min(511, nc));
-    ncell *= (uint64_t)nc;
+    nc[k] = std::max(3, std::min(1023, (int)std::floor(desc->box[k] / rv)));
+    ncell *= (uint64_t)nc[k];
   }
+  const double V = desc->box[0] * desc->box[1] * desc->box[2];
+  const double mean_nb = (double)n / V * 4.0 / 3.0 * M_PI * rv * rv * rv;
+  const uint64_t list_cap = (uint64_t)std::max(32, std::min(255, (int)std::ceil(2.5 * mean_nb + 16.0)));
+  const double span = ((double)nc[0] * nc[1] + nc[0] + 1.0) * ((double)n / (double)ncell) * 1.3 + 64.0;
+  const uint64_t nl_bytes = (n < 32768 || span < 30000.0) ? 2 : 4;
   const uint64_t per_set = n * (6 * 8 + 4 + 3 + 4 * cap);
+  const uint64_t nblk = std::max<uint64_t>(n / RX_THREADS + 1, ncell / SCAN_TILE + 1) + 1;
+  const uint64_t allocs = 40;  // separate cudaMalloc calls, each rounded up
   *bytes = 2 * per_set + n * (2 * 16 + 6 * 4) + (n * cap / 2 + 1) * sizeof(prx_bond) +
-           ncell * 12 + (kHistCap + 1ull) * sizeof(prx_history_record) + 4 * 8 * (n / 256 + 2);
+           (kHistCap + 1ull) * sizeof(prx_history_record) + sizeof(Ctl) + 32 * (n / RX_THREADS + 2) +
+           32 * n + ncell * 12 + 8 * nblk + list_cap * n * nl_bytes + n + allocs * 4096;
   return PRX_OK;
 }
 

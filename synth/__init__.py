@@ -181,6 +181,22 @@ def replica(spec: dict, theta: int = 10):
             chain_growth_scheme(spec["k"], theta), 2)
 
 
+def serving_trace(arrivals: int, rate: float, n_lo: int, n_hi: int, steps_lo: int, steps_hi: int,
+                  k_lo: float, k_hi: float, seed: int) -> list:
+    """Jobs of the serving workload: Poisson arrivals (exponential gaps of
+    mean 1/rate seconds), sizes and step counts log-uniform, step or chain
+    growth with equal odds, rate k log-uniform, one seed each."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, arrivals))
+    n = log_uniform_int(rng, n_lo, n_hi, arrivals)
+    steps = log_uniform_int(rng, steps_lo, steps_hi, arrivals)
+    k = np.exp(rng.uniform(math.log(k_lo), math.log(k_hi), arrivals))
+    kind = rng.integers(0, 2, arrivals)
+    return [dict(kind="step" if kind[r] == 0 else "chain", n=int(n[r]), k=float(k[r]),
+                 seed=seed + 1 + r, arrival=float(t[r]), nsteps=int(steps[r]))
+            for r in range(arrivals)]
+
+
 # The five workloads, by size.  Physical parameters shared by all of them:
 # sigma = eps = m = 1, kT = 1, gamma = 1, dt = 0.005, FENE k = 30, R0 = 1.5,
 # r_react = 1.1, Theta = 10, rho = 0.85.
@@ -190,5 +206,5 @@ WORKLOADS = {
     "step_growth_1m": dict(n_total=1_048_576, f=4, k=0.1, steps=20_000),
     "ensemble_256": dict(replicas=256, n_lo=1024, n_hi=65_536, k_lo=0.01, k_hi=1.0, steps=20_000),
     "serving_stream": dict(rate=20.0, n_lo=2048, n_hi=262_144, steps_lo=5000, steps_hi=50_000,
-                           arrivals=512),
+                           arrivals=512, k_lo=0.01, k_hi=1.0),
 }
