@@ -54,6 +54,9 @@ def parse():
                     help="skip the batched-ensemble measurement")
     ap.add_argument("--ensemble-steps", type=int, default=20,
                     help="timed reaction intervals of the ensemble measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serving-arrivals", type=int, default=64)
+    ap.add_argument("--serving-step-scale", type=float, default=0.1)
     return ap.parse_args()
 
 
@@ -234,6 +237,72 @@ def ensemble(P, torch, steps: int, warmup: int = 3) -> dict:
             "l2": "not flushed: the ensemble state (~1 GB) exceeds L2"}
 
 
+SERVING = synth.WORKLOADS["serving_stream"]
+
+
+def serving(P, torch, arrivals: int, step_scale: float) -> dict:
+    """Serving stream: Poisson arrivals (20 jobs/s) of step- or chain-growth
+    jobs of 2,048-262,144 beads (log-uniform), replayed in real time through
+    the continuous-batching server (admission by device memory, one shared
+    batch), then the same trace one job at a time (FIFO, each job created,
+    run alone and read back before the next).  Latency = arrival to result
+    read-back.  The step counts are the workload's (5,000-50,000,
+    log-uniform) times `step_scale`, and the arrival count is bounded, so
+    that both legs finish in seconds.  Two jobs are re-run alone afterwards
+    and compared bit for bit with their served results."""
+    from paper_1409_7498_gb300.serve import Job, PolyrxBackend, Server, serve_serial, serve_trace
+    W = SERVING
+    lo, hi = max(10, int(W["steps_lo"] * step_scale)), max(10, int(W["steps_hi"] * step_scale))
+    specs = synth.serving_trace(arrivals, W["rate"], W["n_lo"], W["n_hi"], lo, hi, W["k_lo"],
+                                W["k_hi"], synth.BASE_SEED + 5)
+
+    def jobs():
+        out = []
+        for i, sp in enumerate(specs):
+            inp, sch, cap = synth.replica(sp)
+            sysd = dict(desc=P.make_desc(inp.n, inp.L, adj_cap=cap, seed=sp["seed"]), pos=inp.x,
+                        vel=inp.v, type=inp.type, state=inp.state,
+                        reaction=P.make_reaction(**sch))
+            out.append(Job(job_id=i, nsteps=sp["nsteps"], arrival=sp["arrival"], system=sysd,
+                           n=sp["n"]))
+        return out
+
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(0.5 * free, 64 << 30))
+    be = PolyrxBackend(P)
+    srv = Server(be, budget, round_steps=100, theta=THETA)
+    jb = jobs()
+    res_b = serve_trace(srv, jb)
+    be.shutdown()
+    res_b.update(rounds=srv.rounds, max_resident_jobs=srv.max_members,
+                 peak_admitted_bytes=srv.peak_in_use, budget_bytes=budget)
+    be2 = PolyrxBackend(P)
+    res_s = serve_serial(be2, jobs())
+    be2.shutdown()
+    identical = True
+    sample = sorted(range(len(jb)), key=lambda i: jb[i].n * jb[i].nsteps)[:2]
+    for i in sample:
+        j = jb[i]
+        sd = j.system
+        with P.System(sd["desc"], sd["pos"], sd["vel"], sd["type"], sd["state"]) as g:
+            g.set_reaction(sd["reaction"])
+            g.run(j.nsteps)
+            identical &= bool(np.array_equal(g.states(), j.result["states"]) and np.array_equal(
+                np.sort(g.bonds(), order=["step", "a", "t"]),
+                np.sort(j.result["bonds"], order=["step", "a", "t"])))
+    beads = [sp["n"] for sp in specs]
+    offered = W["rate"] * float(np.mean(beads)) * float(np.mean([sp["nsteps"] for sp in specs]))
+    return {"workload": "serving_stream", "arrivals": arrivals, "rate_per_s": W["rate"],
+            "beads": [W["n_lo"], W["n_hi"]], "steps": [lo, hi],
+            "scaled": f"steps x{step_scale} and {arrivals} of {W['arrivals']} arrivals, "
+                      "so that both legs run in seconds",
+            "offered_particle_steps_per_s": offered,
+            "batched": res_b, "serial": res_s,
+            "p99_speedup": res_s["p99_latency_s"] / res_b["p99_latency_s"],
+            "throughput_ratio": res_b["replica_steps_per_s"] / res_s["replica_steps_per_s"],
+            "identical": identical}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle, timed on this host's cores; each bench
     step is one MD step of the same 1M-bead workload (the reaction every
@@ -391,6 +460,9 @@ def main():
     ens = None
     if world == 1 and not args.no_ensemble:
         ens = ensemble(P, torch, args.ensemble_steps)
+    srv = None
+    if world == 1 and not args.no_serving:
+        srv = serving(P, torch, args.serving_arrivals, args.serving_step_scale)
 
     if world > 1:
         dist.barrier()
@@ -417,7 +489,7 @@ def main():
                          "top_kernel": top["name"],
                          "kernel_ms": {r["name"]: round(r["total_ms"], 4) for r in prof},
                          "kernel_launches": {r["name"]: r["launches"] for r in prof}},
-            "e2e": e2e, "cpu_baseline": cpu, "ensemble": ens,
+            "e2e": e2e, "cpu_baseline": cpu, "ensemble": ens, "serving": srv,
         }
         print(json.dumps(line), flush=True)
     g.close()
