@@ -106,20 +106,6 @@ __device__ __forceinline__ bool bond64(const Sys& S, uint32_t style, double dx, 
   return true;
 }
 
-// Last of the nb blocks that run a system's part of a grid: true in thread 0
-// of the block that finished last.
-__device__ __forceinline__ bool last_block(unsigned int* counter, uint32_t nb) {
-  __shared__ bool is_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned int prev = atomicAdd(counter, 1u);
-    is_last = (prev == nb - 1);
-  }
-  __syncthreads();
-  return is_last && threadIdx.x == 0;
-}
-
 // Last warp of a grid to finish, without a block barrier: each warp counts
 // itself out of its block in shared memory, and the last warp of a block
 // counts the block out of the grid.  `warps_left` is set to the block's warp
@@ -273,17 +259,6 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
     uint32_t arow[4];  // first four adjacency entries prefetched; more are rare
 #pragma unroll
     for (int b = 0; b < 4; ++b) arow[b] = b < (int)S.cap ? __ldg(B.adj + (size_t)i * S.cap + b) : 0u;
-    double xi = 0.0, yi = 0.0, zi = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;
-    uint32_t pid = 0u;
-    if (!FORCES_ONLY) {
-      xi = B.x[i];
-      yi = B.y[i];
-      zi = B.z[i];
-      vx = B.vx[i];
-      vy = B.vy[i];
-      vz = B.vz[i];
-      pid = __ldg(B.id + i);
-    }
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
     // software pipeline over the list, four entries per stage: the next
     // stage's list entries load while this stage's four gathers complete
@@ -317,6 +292,9 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
       S.fout[3 * (size_t)i + 2] = (double)fz;
       S.eout[i] = (double)e;
     } else {
+      const double xi = B.x[i], yi = B.y[i], zi = B.z[i];
+      const double vx = B.vx[i], vy = B.vy[i], vz = B.vz[i];
+      const uint32_t pid = __ldg(B.id + i);
       integrate32(S, ctl, B, Pn, i, pid, pi.w, step, fx, fy, fz, xi, yi, zi, vx, vy, vz);
     }
   }
@@ -324,7 +302,7 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
 }
 
 template <bool NL16, bool FORCES_ONLY>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 5)
     k_step_nl(Sys S, cudaGraphConditionalHandle cond, int use_cond) {
   step_nl_body<NL16, FORCES_ONLY>(S, Blk{blockIdx.x, gridDim.x}, cond, use_cond);
 }
@@ -429,33 +407,54 @@ __global__ void __launch_bounds__(STEP_THREADS)
 // per-particle array into the other SoA set with fresh fixed-point positions,
 // adjacency remap, then the Verlet lists.
 // ---------------------------------------------------------------------------
+// v >= L: v - L; then v < 0: v + L.  The tests compare binary64 bit
+// patterns on the integer pipe (for non-negative doubles the bit order is the
+// numeric order; -0.0 counts as 0), so the FP64 pipe only sees the rare
+// particle that left the box.
 __device__ __forceinline__ double wrap_into_box(double v, double L) {
-  if (v >= L) v = __dsub_rn(v, L);
-  if (v < 0.0) v = __dadd_rn(v, L);
+  if (__double_as_longlong(v) >= __double_as_longlong(L)) v = __dsub_rn(v, L);
+  const long long b = __double_as_longlong(v);
+  if (b < 0 && (b << 1) != 0) v = __dadd_rn(v, L);
   return v;
 }
 
+// Cell of every slot from the fixed-point position the last step wrote.
 __device__ __forceinline__ void rebin_keys_body(const Sys& S, const Blk blk) {
   Ctl* ctl = S.ctl;
-  const SoA B = ctl->set ? S.s1 : S.s0;
+  const uint4* __restrict__ P = ctl->phase ? S.P1 : S.P0;
   const uint32_t i = blk.b * blockDim.x + threadIdx.x;
   if (i >= S.n) return;
-  double* xs[3] = {B.x, B.y, B.z};
-  int c[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const double v0 = xs[d][i];
-    const double v = wrap_into_box(v0, S.L[d]);
-    if (v != v0) xs[d][i] = v;
-    const uint32_t X = periodic_fx(v, S.Lfx[d], S.M64[d]);
-    c[d] = (int)__umulhi(X, (uint32_t)S.nc[d]);
-  }
-  const uint32_t k = (uint32_t)((c[2] * S.nc[1] + c[1]) * S.nc[0] + c[0]);
+  const uint4 q = P[i];
+  const uint32_t cx = __umulhi(q.x, (uint32_t)S.nc[0]);
+  const uint32_t cy = __umulhi(q.y, (uint32_t)S.nc[1]);
+  const uint32_t cz = __umulhi(q.z, (uint32_t)S.nc[2]);
+  const uint32_t k = (cz * (uint32_t)S.nc[1] + cy) * (uint32_t)S.nc[0] + cx;
   S.key[i] = k;
   atomicAdd(&S.count[k], 1u);
 }
 
 __global__ void k_rebin_keys(Sys S) { rebin_keys_body(S, Blk{blockIdx.x, gridDim.x}); }
+
+// First binning of a system (no step has written fixed-point positions yet):
+// cells from the FP64 positions, which are wrapped into the box in place.
+__global__ void k_rebin_keys_x(Sys S) {
+  Ctl* ctl = S.ctl;
+  const SoA B = ctl->set ? S.s1 : S.s0;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.n) return;
+  double* xs[3] = {B.x, B.y, B.z};
+  uint32_t c[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double v0 = xs[d][i];
+    const double v = wrap_into_box(v0, S.L[d]);
+    if (v != v0) xs[d][i] = v;
+    c[d] = __umulhi(periodic_fx(v, S.Lfx[d], S.M64[d]), (uint32_t)S.nc[d]);
+  }
+  const uint32_t k = (c[2] * (uint32_t)S.nc[1] + c[1]) * (uint32_t)S.nc[0] + c[0];
+  S.key[i] = k;
+  atomicAdd(&S.count[k], 1u);
+}
 __global__ void kb_rebin_keys(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
@@ -632,7 +631,7 @@ __global__ void kb_rebin_cellsort(const Sys* __restrict__ T, const BlkMap* __res
 // New slot s takes old slot tmp[s]: copies every per-particle array into the
 // other set and writes the fixed-point position with a fresh displacement
 // reference.
-__device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk) {
+__device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk, bool wrap) {
   Ctl* ctl = S.ctl;
   const int set = ctl->set;
   const SoA A = set ? S.s1 : S.s0;
@@ -641,7 +640,15 @@ __device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk) 
   const uint32_t s = blk.b * blockDim.x + threadIdx.x;
   if (s >= S.n) return;
   const uint32_t o = S.tmp[s];
-  const double x = A.x[o], y = A.y[o], z = A.z[o];
+  // positions re-enter the box here (a checkpoint restore keeps them as
+  // saved, so that the continued run wraps them at the same step as the
+  // original run)
+  double x = A.x[o], y = A.y[o], z = A.z[o];
+  if (wrap) {
+    x = wrap_into_box(x, S.L[0]);
+    y = wrap_into_box(y, S.L[1]);
+    z = wrap_into_box(z, S.L[2]);
+  }
   B.x[s] = x;
   B.y[s] = y;
   B.z[s] = z;
@@ -663,12 +670,14 @@ __device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk) 
   P[s] = make_uint4(X, Y, Z, coarse_ref(X, Y, Z, S.wshift));
 }
 
-__global__ void k_rebin_permute(Sys S) { rebin_permute_body(S, Blk{blockIdx.x, gridDim.x}); }
+__global__ void k_rebin_permute(Sys S, int wrap) {
+  rebin_permute_body(S, Blk{blockIdx.x, gridDim.x}, wrap != 0);
+}
 __global__ void kb_rebin_permute(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
   if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
-  rebin_permute_body(S, Blk{m.b, m.nb});
+  rebin_permute_body(S, Blk{m.b, m.nb}, true);
 }
 
 __device__ __forceinline__ void rebin_remap_body(const Sys& S, const Blk blk) {
@@ -700,6 +709,18 @@ __global__ void kb_rebin_remap(const Sys* __restrict__ T, const BlkMap* __restri
 // particle's 3 x 3 x 3 cell neighbourhood is 9 contiguous ranges.  A pair
 // enters the list when its fixed-point distance is below r_c + skin.
 // ---------------------------------------------------------------------------
+// Stores that happen only when `pred` holds, as one predicated instruction.
+__device__ __forceinline__ void st_global_pred_u16(void* p, uint16_t v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.global.u16 [%0], %1;\n\t}"
+      ::"l"(p), "h"(v), "r"((int)pred) : "memory");
+}
+__device__ __forceinline__ void st_global_pred_u32(void* p, uint32_t v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.global.u32 [%0], %1;\n\t}"
+      ::"l"(p), "r"(v), "r"((int)pred) : "memory");
+}
+
 struct RowInfo {
   int base;        // first staged index of the row
   int padL;        // particles of the left image cell (cell nx-1)
@@ -718,6 +739,8 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
   RowInfo* ri = reinterpret_cast<RowInfo*>(smem + 16 * (size_t)CAP);
   uint32_t* sCS = reinterpret_cast<uint32_t*>(ri + TILE_ROWS_MAX);
   __shared__ int sTOT;
+  __shared__ unsigned int warps_left;
+  if (threadIdx.x == 0) warps_left = blockDim.x >> 5;
 
   Ctl* ctl = S.ctl;
   const uint4* __restrict__ P = ctl->phase ? S.P1 : S.P0;
@@ -785,8 +808,16 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
       const int hi = r.base + (cx + 2 > nx ? r.tot : r.padL + (int)cs[cx + 2] - r.row_lo);
       win[w] = (uint32_t)lo | ((uint32_t)hi << 16);
     }
+    // Appends are branch-free: every candidate computes its entry, and a
+    // predicated store writes it only on a hit, so the warp does not
+    // diverge on the (frequent) hits.  `wp` walks the slot's column.
     int cnt = 0;
     bool overflow = false;
+    const int cap = S.list_cap;
+    const int n = (int)S.n, half = n / 2;
+    unsigned char* wp = (unsigned char*)S.nl + (size_t)i * (NL16 ? 2 : 4);
+    const size_t stride = (size_t)n * (NL16 ? 2 : 4);
+    const float sx = S.scale[0], sy = S.scale[1], sz = S.scale[2], rv2 = S.rv2_build;
     for (int c0 = 0; c0 < TOT; c0 += CAP) {
       const int cn = min(CAP, TOT - c0);
       __syncthreads();
@@ -811,25 +842,23 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
           const int hi = min((int)(win[w] >> 16), c0 + cn) - c0;
           for (int k = lo; k < hi; ++k) {
             const uint4 q = sX[k];
-            const float dx = __int2float_rn(pdiff(q.x, pi.x)) * S.scale[0];
-            const float dy = __int2float_rn(pdiff(q.y, pi.y)) * S.scale[1];
-            const float dz = __int2float_rn(pdiff(q.z, pi.z)) * S.scale[2];
-            if (fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < S.rv2_build && q.w != i) {
-              if (cnt < S.list_cap) {
-                int r = (int)q.w - (int)i;
-                if (r > (int)(S.n / 2)) r -= (int)S.n;
-                else if (r < -(int)(S.n / 2)) r += (int)S.n;
-                if constexpr (NL16) {
-                  if (r > 32767 || r < -32767) overflow = true;
-                  ((int16_t*)S.nl)[(size_t)cnt * S.n + i] = (int16_t)r;
-                } else {
-                  ((int32_t*)S.nl)[(size_t)cnt * S.n + i] = r;
-                }
-                ++cnt;
-              } else {
-                overflow = true;
-              }
+            const float dx = __int2float_rn(pdiff(q.x, pi.x)) * sx;
+            const float dy = __int2float_rn(pdiff(q.y, pi.y)) * sy;
+            const float dz = __int2float_rn(pdiff(q.z, pi.z)) * sz;
+            const bool hit = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < rv2 && q.w != i;
+            int r = (int)q.w - (int)i;
+            r = r > half ? r - n : r;
+            r = r < -half ? r + n : r;
+            const bool put = hit && cnt < cap;
+            if constexpr (NL16) {
+              overflow |= hit && (cnt >= cap || r > 32767 || r < -32767);
+              st_global_pred_u16(wp, (uint16_t)(int16_t)r, put);
+            } else {
+              overflow |= hit && cnt >= cap;
+              st_global_pred_u32(wp, (uint32_t)r, put);
             }
+            wp += put ? stride : 0;
+            cnt += put ? 1 : 0;
           }
         }
       }
@@ -839,7 +868,9 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
       if (overflow) set_status(ctl, PRX_ECAPACITY);
     }
   }
-  if (last_block(&ctl->done_rebin, blk.nb)) {
+  // the last warp of the system's tiles flips the SoA set and clears the
+  // flag (a warp count, not a block barrier: warps that finish early leave)
+  if (last_warp(&ctl->done_rebin, &warps_left, blk.nb)) {
     ctl->done_rebin = 0u;
     ctl->set ^= 1;
     ctl->rebin_flag = 0;
@@ -923,7 +954,8 @@ int configure_build_kernel(size_t smem_bytes) { return raise_smem_limit(0, smem_
 
 int rebin_kernel_count() { return 9; }
 
-// Whole rebuild: keys (mode 0/1 from positions, 2 given), scan, scatter,
+// Whole rebuild: keys (mode 0: from the fixed-point positions of the last
+// step; 1: from the FP64 positions; 2: given), scan, scatter,
 // per-cell sort, permutation, adjacency remap, Verlet lists.  `hook`
 // (optional) is called before (0) and after (1) each launch with the
 // kernel's name, for event timing.
@@ -939,6 +971,7 @@ void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, c
   cudaMemsetAsync(S.fill, 0, sizeof(uint32_t) * S.ncell, st);
   H(mode == 2 ? "count_keys" : "rebin_keys", 0);
   if (mode == 2) k_count_keys<<<gp, 256, 0, st>>>(S);
+  else if (mode == 1) k_rebin_keys_x<<<gp, 256, 0, st>>>(S);
   else k_rebin_keys<<<gp, 256, 0, st>>>(S);
   H(mode == 2 ? "count_keys" : "rebin_keys", 1);
   H("scan_tiles", 0);
@@ -957,7 +990,7 @@ void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, c
   k_rebin_cellsort<<<gc, 256, 0, st>>>(S);
   H("rebin_cellsort", 1);
   H("rebin_permute", 0);
-  k_rebin_permute<<<gp, 256, 0, st>>>(S);
+  k_rebin_permute<<<gp, 256, 0, st>>>(S, mode != 2);
   H("rebin_permute", 1);
   H("rebin_remap", 0);
   k_rebin_remap<<<gp, 256, 0, st>>>(S);
