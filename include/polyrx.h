@@ -258,6 +258,26 @@ int prx_react_noalloc(const prx_reaction_desc* rx, const double* box, double dt,
                       prx_bond* d_bonds_out, uint32_t bonds_cap, uint32_t* d_nbonds_out,
                       void* cuda_stream, prx_rx_trace* trace);
 
+/* ---- autotuner ---------------------------------------------------------------- */
+/* Times the MD step (with the reaction every Theta steps when rx != NULL) of
+ * the system described by desc and the host arrays (as for prx_create) for
+ * each of the n_skins candidate skins, and writes the fastest to *best_skin.
+ * Each candidate is a temporary system built from the same inputs on a
+ * library stream, so the call needs the device memory of one extra system; it
+ * runs steps / 4 + 1 warm-up steps, then times `steps` steps with CUDA
+ * events.  ms_per_step (n_skins entries, may be NULL) receives each
+ * candidate's time, -1 for a candidate that could not run (e.g. a box too
+ * small for that list radius).  The skin sets the Verlet-list radius
+ * r_c + skin, the cell edge and how often the lists are rebuilt; it does not
+ * change the model: runs that differ only in the skin differ only in the
+ * order of floating-point sums.  The choice depends on timing, so a run that
+ * must be reproducible records the chosen skin in its descriptor.
+ * PRX_EINVAL when no candidate could run. */
+int prx_autotune_skin(const prx_system_desc* desc, const double* pos, const double* vel,
+                      const uint8_t* type, const int8_t* state, const prx_reaction_desc* rx,
+                      uint32_t steps, const double* skins, uint32_t n_skins, double* best_skin,
+                      double* ms_per_step);
+
 /* ---- batched ensemble -------------------------------------------------------- */
 /* A batch advances many independent systems (replicas of different sizes,
  * schemes, rates and seeds) together: every MD step is ONE kernel launch

@@ -21,15 +21,17 @@ namespace prx {
 namespace {
 
 // WCA pair term in FP32; d = x_j - x_i.  Adds -g d to f and V/2 to e.
+// Reciprocals and quotients use the hardware approximation (relative error
+// about 2^-22), well inside the FP32 force tolerance.
 __device__ __forceinline__ void wca32(const Sys& S, float dx, float dy, float dz, float r2,
                                       float& fx, float& fy, float& fz, float& e) {
-  const float r2i = __fdiv_rn(1.0f, r2);
+  const float r2i = __fdividef(1.0f, r2);
   const float sr2 = S.sig2f * r2i;
   const float sr6 = sr2 * sr2 * sr2;
   float g = S.eps24f * sr6 * (2.0f * sr6 - 1.0f) * r2i;
   if (S.fcapf > 0.0f) {
     const float r = sqrtf(r2);
-    if (g * r > S.fcapf) g = S.fcapf / r;
+    if (g * r > S.fcapf) g = __fdividef(S.fcapf, r);
   }
   fx -= g * dx;
   fy -= g * dy;
@@ -44,17 +46,17 @@ __device__ __forceinline__ bool bond32(const Sys& S, uint32_t style, float dx, f
   float g;
   if (style == 0u) {
     if (!(r2 < S.fr02f)) return false;
-    const float q = 1.0f - r2 / S.fr02f;
-    g = -S.fkf / q;
+    const float q = 1.0f - r2 * S.fr02if;
+    g = -__fdividef(S.fkf, q);
     e += 0.5f * (-0.5f * S.fkf * S.fr02f * logf(q));
   } else {
     const float r = sqrtf(r2);
     if (!(r > S.rcf && r < 2.0f * S.rcf)) return true;
     const float sd = 2.0f * S.rcf - r;
-    const float ss2 = S.sig2f / (sd * sd);
+    const float ss2 = __fdividef(S.sig2f, sd * sd);
     const float ss6 = ss2 * ss2 * ss2;
-    const float dVdr = S.eps24f * (2.0f * ss6 * ss6 - ss6) / sd;
-    g = -dVdr / r;
+    const float dVdr = __fdividef(S.eps24f * (2.0f * ss6 * ss6 - ss6), sd);
+    g = -__fdividef(dVdr, r);
     e += 0.5f * S.eps4f * (ss6 * ss6 - ss6 + 0.25f);
   }
   fx -= g * dx;
@@ -709,6 +711,14 @@ __global__ void kb_rebin_remap(const Sys* __restrict__ T, const BlkMap* __restri
 // particle's 3 x 3 x 3 cell neighbourhood is 9 contiguous ranges.  A pair
 // enters the list when its fixed-point distance is below r_c + skin.
 // ---------------------------------------------------------------------------
+// 16-byte copy global -> shared that does not wait for the data (cp.async,
+// L2 only); cp_async_wait_all() waits for every copy the thread issued.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Stores that happen only when `pred` holds, as one predicated instruction.
 __device__ __forceinline__ void st_global_pred_u16(void* p, uint16_t v, bool pred) {
   asm volatile(
@@ -821,18 +831,23 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
     for (int c0 = 0; c0 < TOT; c0 += CAP) {
       const int cn = min(CAP, TOT - c0);
       __syncthreads();
-      for (int sr = warp; sr < R; sr += nwarps) {
-        const RowInfo r = ri[sr];
-        const int k0 = max(r.base, c0), k1 = min(r.base + r.tot, c0 + cn);
-        for (int ent = k0 + lane; ent < k1; ent += 32) {
-          const int kr = ent - r.base;
-          int slot;
-          if (kr < r.padL) slot = r.left_start + kr;
-          else if (kr < r.padL + r.rowcount) slot = r.row_lo + (kr - r.padL);
-          else slot = r.row_lo + (kr - r.padL - r.rowcount);
-          const uint4 q = P[slot];
-          sX[ent - c0] = make_uint4(q.x, q.y, q.z, (uint32_t)slot);
+      // every copy of a thread in flight at once (cp.async), then the slot
+      // goes into .w once the copies have landed
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int sr = warp; sr < R; sr += nwarps) {
+          const RowInfo r = ri[sr];
+          const int k0 = max(r.base, c0), k1 = min(r.base + r.tot, c0 + cn);
+          for (int ent = k0 + lane; ent < k1; ent += 32) {
+            const int kr = ent - r.base;
+            int slot;
+            if (kr < r.padL) slot = r.left_start + kr;
+            else if (kr < r.padL + r.rowcount) slot = r.row_lo + (kr - r.padL);
+            else slot = r.row_lo + (kr - r.padL - r.rowcount);
+            if (pass == 0) cp_async16(&sX[ent - c0], P + slot);
+            else sX[ent - c0].w = (uint32_t)slot;
+          }
         }
+        if (pass == 0) cp_async_wait_all();
       }
       __syncthreads();
       if (act) {

@@ -121,7 +121,7 @@ struct Sys {
   // list-build tiling (cells of edge >= r_c + skin)
   int tile_y, tiles_y, tile_threads, tile_cap;
   // physics (FP32 and FP64 copies)
-  float rc2f, sig2f, eps24f, eps4f, fcapf, fkf, fr02f, rcf, sigf;
+  float rc2f, sig2f, eps24f, eps4f, fcapf, fkf, fr02f, fr02if, rcf, sigf;
   double rc2, sig2, eps24, eps4, fcap, fk, fr02, rc, sig;
   double dt, a_fric, b_kick;  // v' = a v + b F ; x' = x + dt v'
   double gm;                  // gamma m (FP64 mode writes the friction force out)

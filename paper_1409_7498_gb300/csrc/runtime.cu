@@ -216,9 +216,10 @@ int setup_grid(prx_system* sys, double rc) {
   const double rho = (double)S.n / V;
   const double mean_nb = rho * 4.0 / 3.0 * M_PI * rv * rv * rv;
   S.list_cap = std::max(32, std::min(255, (int)std::ceil(2.5 * mean_nb + 16.0)));
-  const double per_cell = (double)S.n / (double)ncell;
-  const double span = ((double)S.nc[0] * S.nc[1] + S.nc[0] + 1.0) * per_cell * 1.3 + 64.0;
-  S.nl16 = (S.n < 32768 || span < 30000.0) ? 1 : 0;
+  // 16-bit relative entries only when every offset (mod n) fits: with
+  // periodic wraps in y and z a neighbour can lie up to two cell layers away
+  // in slot order, so larger systems take 32-bit entries (measured: no cost)
+  S.nl16 = S.n < 32768 ? 1 : 0;
   {
     void* nl = nullptr;
     if ((rc2 = dalloc(sys, sys->grid_allocs, (uint8_t**)&nl,
@@ -231,6 +232,7 @@ int setup_grid(prx_system* sys, double rc) {
     // list-build tiling: the largest tile of 1..4 cell rows whose particles
     // fit 256 threads; staging buffer sized for all neighbour rows at once
     const double per_row = (double)S.n / ((double)S.nc[1] * S.nc[2]);
+    const double per_cell = (double)S.n / (double)ncell;
     int ty = 1;
     for (int c = 2; c <= 4; ++c)
       if (c * per_row + 3.0 * std::sqrt(c * per_row) + 16.0 <= 256.0) ty = c;
@@ -481,6 +483,7 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
   S.fkf = (float)desc->fene_k;
   S.fr02 = desc->fene_r0 * desc->fene_r0;
   S.fr02f = (float)S.fr02;
+  S.fr02if = (float)(1.0 / S.fr02);
   S.dt = desc->dt;
   S.mass = desc->mass;
   S.b_kick = desc->dt / desc->mass;
@@ -805,8 +808,7 @@ int prx_estimate_bytes(const prx_system_desc* desc, uint64_t* bytes) {
   const double V = desc->box[0] * desc->box[1] * desc->box[2];
   const double mean_nb = (double)n / V * 4.0 / 3.0 * M_PI * rv * rv * rv;
   const uint64_t list_cap = (uint64_t)std::max(32, std::min(255, (int)std::ceil(2.5 * mean_nb + 16.0)));
-  const double span = ((double)nc[0] * nc[1] + nc[0] + 1.0) * ((double)n / (double)ncell) * 1.3 + 64.0;
-  const uint64_t nl_bytes = (n < 32768 || span < 30000.0) ? 2 : 4;
+  const uint64_t nl_bytes = n < 32768 ? 2 : 4;  // as setup_grid
   const uint64_t per_set = n * (6 * 8 + 4 + 3 + 4 * cap);
   const uint64_t nblk = std::max<uint64_t>(n / RX_THREADS + 1, ncell / SCAN_TILE + 1) + 1;
   const uint64_t allocs = 40;  // separate cudaMalloc calls, each rounded up
@@ -1319,6 +1321,48 @@ int prx_load(const char* path, void* cuda_stream, prx_system** out) {
     }
   }
   *out = sys;
+  return PRX_OK;
+}
+
+// ---- autotuner -------------------------------------------------------------------
+
+int prx_autotune_skin(const prx_system_desc* desc, const double* pos, const double* vel,
+                      const uint8_t* type, const int8_t* state, const prx_reaction_desc* rx,
+                      uint32_t steps, const double* skins, uint32_t n_skins, double* best_skin,
+                      double* ms_per_step) {
+  if (!desc || !skins || !n_skins || !best_skin || steps == 0) return PRX_EINVAL;
+  double best = -1.0, best_ms = 0.0;
+  for (uint32_t c = 0; c < n_skins; ++c) {
+    if (ms_per_step) ms_per_step[c] = -1.0;
+    prx_system_desc d = *desc;
+    d.skin = skins[c];
+    prx_system* sys = nullptr;
+    if (prx_create(&d, pos, vel, type, state, nullptr, 0, nullptr, &sys) != PRX_OK) continue;
+    bool ok = !rx || prx_set_reaction(sys, rx) == PRX_OK;
+    cudaEvent_t a = nullptr, b = nullptr;
+    float ms = 0.f;
+    ok = ok && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+    ok = ok && prx_run(sys, steps / 4 + 1) == PRX_OK && prx_sync(sys) == PRX_OK;
+    ok = ok && cudaEventRecord(a, sys->stream) == cudaSuccess;
+    ok = ok && prx_run(sys, steps) == PRX_OK;
+    ok = ok && cudaEventRecord(b, sys->stream) == cudaSuccess;
+    ok = ok && prx_sync(sys) == PRX_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    prx_destroy(sys);
+    if (!ok) continue;
+    const double per = ms / steps;
+    if (ms_per_step) ms_per_step[c] = per;
+    if (best < 0.0 || per < best_ms) {
+      best = skins[c];
+      best_ms = per;
+    }
+  }
+  if (best < 0.0) {
+    g_create_error = "no candidate skin could be run";
+    return PRX_EINVAL;
+  }
+  *best_skin = best;
   return PRX_OK;
 }
 

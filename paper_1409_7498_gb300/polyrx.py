@@ -122,6 +122,9 @@ def lib():
         "prx_react_noalloc": ([P(prx_reaction_desc), P(C.c_double), C.c_double, U64, U64,
                                C.c_uint32, VP, VP, VP, C.c_uint32, VP, VP, VP, C.c_uint32, VP,
                                VP, P(prx_rx_trace)], I),
+        "prx_autotune_skin": ([P(prx_system_desc), VP, VP, VP, VP, P(prx_reaction_desc),
+                               C.c_uint32, P(C.c_double), C.c_uint32, P(C.c_double),
+                               P(C.c_double)], I),
         "prx_batch_create": ([VP, P(VP)], I),
         "prx_batch_destroy": ([VP], None),
         "prx_batch_add": ([VP, VP], I),
@@ -332,6 +335,24 @@ def prx_react_noalloc(rx, box, dt, seed, step, n, d_pos, d_type, d_state, adj_ca
         raise PolyrxError(rc, lib().prx_status_string(rc).decode())
     return dict(candidates=t.candidates, retained=t.retained, a_winners=t.a_winners,
                 formed=t.formed)
+
+
+def prx_autotune_skin(desc: prx_system_desc, pos, vel, type_, state, rx=None, steps: int = 100,
+                      skins=(0.25, 0.3, 0.35, 0.4, 0.45, 0.5)):
+    """Fastest skin among the candidates; returns (best, {skin: ms per step})."""
+    n = desc.n
+    pos = np.ascontiguousarray(pos, np.float64).reshape(n, 3)
+    vel = None if vel is None else np.ascontiguousarray(vel, np.float64).reshape(n, 3)
+    type_ = np.ascontiguousarray(type_, np.uint8)
+    state = np.ascontiguousarray(state, np.int8)
+    sk = (C.c_double * len(skins))(*map(float, skins))
+    ms = (C.c_double * len(skins))()
+    best = C.c_double()
+    rc = lib().prx_autotune_skin(C.byref(desc), _ptr(pos), _ptr(vel), _ptr(type_), _ptr(state),
+                                 C.byref(rx) if rx is not None else None, int(steps), sk,
+                                 len(skins), C.byref(best), ms)
+    _check(rc, None)
+    return best.value, {float(skins[q]): ms[q] for q in range(len(skins))}
 
 
 def _bcheck(rc: int, b=None):
