@@ -25,6 +25,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 OK, EINVAL, ENOMEM, ECAPACITY, EOVERSTRETCH, ENONFINITE = 0, -1, -2, -3, -4, -5
 BOND_FENE, BOND_MIRROR_LJ = 0, 1
+SELECT_RANDOM, SELECT_NEAREST = 0, 1
 TAG_THERMO, TAG_ACCEPT, TAG_SEL_A, TAG_SEL_T = 1, 2, 3, 4
 
 
@@ -56,7 +57,7 @@ class _RX(C.Structure):
         ("mask_A", C.c_uint32), ("mask_T", C.c_uint32), ("a_lo", C.c_int32), ("a_hi", C.c_int32),
         ("t_lo", C.c_int32), ("t_hi", C.c_int32), ("dA", C.c_int32), ("dT", C.c_int32),
         ("k", C.c_double), ("theta", C.c_int64), ("r_react", C.c_double),
-        ("bond_style", C.c_int32), ("max_valence", C.c_uint8 * 8),
+        ("bond_style", C.c_int32), ("selection", C.c_int32), ("max_valence", C.c_uint8 * 8),
     ]
 
 
@@ -152,11 +153,12 @@ class Reaction:
     r_react: float = 1.1
     bond_style: int = BOND_FENE
     max_valence: tuple = (8,) * 8
+    selection: int = 0  # SELECT_RANDOM (Table I) or SELECT_NEAREST (LAMMPS rule, Sec. IV.A)
 
     def _c(self) -> _RX:
         mv = list(self.max_valence) + [0] * (8 - len(self.max_valence))
         return _RX(self.mask_A, self.mask_T, self.a_lo, self.a_hi, self.t_lo, self.t_hi, self.dA,
-                   self.dT, self.k, self.theta, self.r_react, self.bond_style,
+                   self.dT, self.k, self.theta, self.r_react, self.bond_style, self.selection,
                    (C.c_uint8 * 8)(*mv[:8]))
 
 

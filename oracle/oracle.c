@@ -369,6 +369,7 @@ int orc_check_reaction(const orc_rx_params* rx) {
   if (rx->a_lo > rx->a_hi || rx->t_lo > rx->t_hi) return ORC_EINVAL;
   if (rx->theta < 1 || !(rx->k >= 0.0) || !(rx->r_react > 0.0)) return ORC_EINVAL;
   if (rx->bond_style != ORC_BOND_FENE && rx->bond_style != ORC_BOND_MIRROR_LJ) return ORC_EINVAL;
+  if (rx->selection != ORC_SELECT_RANDOM && rx->selection != ORC_SELECT_NEAREST) return ORC_EINVAL;
   if ((rx->mask_A | rx->mask_T) >> 8) return ORC_EINVAL;
   /* A particle may not be eligible as A and as T at once: for a type in
    * both masks the two state windows must be disjoint. */
@@ -436,11 +437,136 @@ static void find_visit(int64_t i, int64_t j, void* vctx) {
   c->nlist++;
 }
 
+/* Step 9 for the final pairs, in ascending id of A: both adjacency rows,
+ * the bond list, and the state shifts delta_A and delta_T (Eq. 2). */
+static int add_bonds(orc_system* s, const orc_rx_params* rx, const pair_t* list, int64_t nfin,
+                     int64_t step) {
+  int status = ORC_OK;
+  for (int64_t q = 0; q < nfin; ++q) {
+    uint32_t a = list[q].a, t = list[q].t;
+    int capA = s->cap < rx->max_valence[s->type[a] & 7] ? s->cap : rx->max_valence[s->type[a] & 7];
+    int capT = s->cap < rx->max_valence[s->type[t] & 7] ? s->cap : rx->max_valence[s->type[t] & 7];
+    if (s->nadj[a] >= capA || s->nadj[t] >= capT || s->nb >= s->nb_cap) {
+      status = ORC_ECAPACITY;
+      continue;
+    }
+    s->adj[(int64_t)s->cap * a + s->nadj[a]] = t;
+    s->adj_style[(int64_t)s->cap * a + s->nadj[a]] = (uint8_t)rx->bond_style;
+    s->nadj[a]++;
+    s->adj[(int64_t)s->cap * t + s->nadj[t]] = a;
+    s->adj_style[(int64_t)s->cap * t + s->nadj[t]] = (uint8_t)rx->bond_style;
+    s->nadj[t]++;
+    s->bond_a[s->nb] = a;
+    s->bond_t[s->nb] = t;
+    s->bond_step[s->nb] = step;
+    s->bond_style[s->nb] = (uint8_t)rx->bond_style;
+    s->nb++;
+    s->state[a] = (int8_t)(s->state[a] + rx->dA);
+    s->state[t] = (int8_t)(s->state[t] + rx->dT);
+  }
+  return status;
+}
+
+/* Nearest-partner search of the LAMMPS rule: for particle i (an A when
+ * want_T, else a T), the eligible partner j of the other kind within the
+ * reaction cutoff, not bonded to i, of smallest r^2 (ties to the smaller
+ * id). */
+typedef struct {
+  const orc_system* s;
+  const orc_md_params* md;
+  const orc_rx_params* rx;
+  double rr2;
+  int want_T;
+  int64_t best;
+  double best_r2;
+  int64_t in_range;
+} nearest_ctx;
+
+static void nearest_visit(int64_t i, int64_t j, void* vctx) {
+  nearest_ctx* c = (nearest_ctx*)vctx;
+  if (c->want_T ? !eligible_T(c->s, c->rx, j) : !eligible_A(c->s, c->rx, j)) return;
+  if (bonded(c->s, i, j)) return;
+  double d[3];
+  separation(c->s->x, i, j, c->md->L, d);
+  const double r2 = dist2_fixed(d);
+  if (!(r2 < c->rr2)) return;
+  c->in_range++;
+  if (c->best < 0 || r2 < c->best_r2 || (r2 == c->best_r2 && j < c->best)) {
+    c->best = j;
+    c->best_r2 = r2;
+  }
+}
+
+/* The LAMMPS fix bond/create selection (Sec. IV.A): every eligible A records
+ * its nearest eligible T and every eligible T its nearest eligible A; a pair
+ * whose two particles picked each other is a candidate, and it reacts when
+ * u < k dt Theta, the draw keyed by the pair's ids with the smaller first
+ * (the probability is evaluated on the particle of lowest identifier). */
+static int react_nearest(orc_system* s, const orc_md_params* md, const orc_rx_params* rx,
+                         int use_cells, int64_t step, orc_rx_trace* trace) {
+  const double p = rx->k * md->dt * (double)rx->theta;
+  const double rr2 = rx->r_react * rx->r_react;
+  int64_t* near = (int64_t*)malloc(sizeof(int64_t) * (size_t)(s->n ? s->n : 1));
+  pair_t* list = (pair_t*)malloc(sizeof(pair_t) * (size_t)(s->n ? s->n : 1));
+  if (!near || !list) {
+    free(near);
+    free(list);
+    return ORC_ENOMEM;
+  }
+  cells_t cl;
+  int have = 0;
+  if (use_cells) {
+    have = cells_build(s, md->L, rx->r_react, &cl);
+    if (have < 0) {
+      free(near);
+      free(list);
+      return ORC_ENOMEM;
+    }
+  }
+  int64_t in_range = 0;
+  for (int64_t i = 0; i < s->n; ++i) {
+    near[i] = -1;
+    const int isA = eligible_A(s, rx, i), isT = eligible_T(s, rx, i);
+    if (!isA && !isT) continue;
+    nearest_ctx c = {s, md, rx, rr2, isA, -1, 0.0, 0};
+    for_each_neighbor(s, have ? &cl : NULL, md->L, i, nearest_visit, &c);
+    near[i] = c.best;
+    if (isA) in_range += c.in_range; /* every (A, T) pair in range, counted once */
+  }
+  if (have) cells_free(&cl);
+  int64_t mutual = 0, accepted = 0;
+  for (int64_t a = 0; a < s->n; ++a) {
+    if (!eligible_A(s, rx, a) || near[a] < 0) continue;
+    const int64_t t = near[a];
+    if (near[t] != a) continue;
+    mutual++;
+    const uint32_t lo = (uint32_t)(a < t ? a : t), hi = (uint32_t)(a < t ? t : a);
+    uint32_t w[4];
+    draw(md->seed, step, lo, hi, ORC_TAG_NEAREST, w);
+    if (!(orc_u53(w[0], w[1]) < p)) continue; /* Eq. 4 */
+    list[accepted].a = (uint32_t)a;
+    list[accepted].t = (uint32_t)t;
+    list[accepted].key = 0;
+    accepted++;
+  }
+  free(near);
+  const int status = add_bonds(s, rx, list, accepted, step);
+  if (trace) {
+    trace->candidates = in_range;
+    trace->retained = mutual;
+    trace->a_winners = accepted;
+    trace->formed = accepted;
+  }
+  free(list);
+  return status;
+}
+
 int orc_react(orc_system* s, const orc_md_params* md, const orc_rx_params* rx, int use_cells,
               int64_t step, orc_rx_trace* trace) {
   if (!s || !md) return ORC_EINVAL;
   int rc = orc_check_reaction(rx);
   if (rc) return rc;
+  if (rx->selection == ORC_SELECT_NEAREST) return react_nearest(s, md, rx, use_cells, step, trace);
   find_ctx c;
   memset(&c, 0, sizeof(c));
   c.s = s;
@@ -517,29 +643,7 @@ int orc_react(orc_system* s, const orc_md_params* md, const orc_rx_params* rx, i
   qsort(c.list, (size_t)nfin, sizeof(pair_t), cmp_by_a);
 
   /* Step 9: add the bonds and shift the states by delta_A and delta_T. */
-  int status = ORC_OK;
-  for (int64_t q = 0; q < nfin; ++q) {
-    uint32_t a = c.list[q].a, t = c.list[q].t;
-    int capA = s->cap < rx->max_valence[s->type[a] & 7] ? s->cap : rx->max_valence[s->type[a] & 7];
-    int capT = s->cap < rx->max_valence[s->type[t] & 7] ? s->cap : rx->max_valence[s->type[t] & 7];
-    if (s->nadj[a] >= capA || s->nadj[t] >= capT || s->nb >= s->nb_cap) {
-      status = ORC_ECAPACITY;
-      continue;
-    }
-    s->adj[(int64_t)s->cap * a + s->nadj[a]] = t;
-    s->adj_style[(int64_t)s->cap * a + s->nadj[a]] = (uint8_t)rx->bond_style;
-    s->nadj[a]++;
-    s->adj[(int64_t)s->cap * t + s->nadj[t]] = a;
-    s->adj_style[(int64_t)s->cap * t + s->nadj[t]] = (uint8_t)rx->bond_style;
-    s->nadj[t]++;
-    s->bond_a[s->nb] = a;
-    s->bond_t[s->nb] = t;
-    s->bond_step[s->nb] = step;
-    s->bond_style[s->nb] = (uint8_t)rx->bond_style;
-    s->nb++;
-    s->state[a] = (int8_t)(s->state[a] + rx->dA);
-    s->state[t] = (int8_t)(s->state[t] + rx->dT);
-  }
+  const int status = add_bonds(s, rx, c.list, nfin, step);
   if (trace) {
     trace->candidates = c.candidates;
     trace->retained = c.nlist;

@@ -32,6 +32,13 @@
 #define ORC_TAG_ACCEPT 2u
 #define ORC_TAG_SEL_A 3u
 #define ORC_TAG_SEL_T 4u
+#define ORC_TAG_NEAREST 5u
+
+/* Partner selection: the paper's algorithm (one T per A and one A per T,
+ * each chosen at random; Table I), or the nearest-partner rule of the LAMMPS
+ * fix bond/create that the paper compares it with (Sec. IV.A). */
+#define ORC_SELECT_RANDOM 0
+#define ORC_SELECT_NEAREST 1
 
 typedef struct {
   double L[3];        /* box edges */
@@ -56,6 +63,7 @@ typedef struct {
   int64_t theta;      /* reaction interval Theta in MD steps */
   double r_react;     /* reaction cutoff */
   int32_t bond_style; /* style of the created bonds */
+  int32_t selection;  /* ORC_SELECT_RANDOM (Table I) or ORC_SELECT_NEAREST (Sec. IV.A) */
   uint8_t max_valence[8]; /* per type: bonds a particle may hold */
 } orc_rx_params;
 

@@ -129,7 +129,7 @@ def log_uniform_int(rng: np.random.Generator, lo: int, hi: int, size=None):
 # and the CUDA library turn one of these into their own parameter struct.
 # ---------------------------------------------------------------------------
 def step_growth_scheme(f: int, k: float, theta: int = 10, r_react: float = 1.1,
-                       bond_style: int = 0) -> dict:
+                       bond_style: int = 0, selection: int = 0) -> dict:
     """Step growth, Sec. II.B, with difunctional single-bead targets:
     A crosslinkers start at state f and react while in states 1..f
     (delta_A = -1); B targets react while in states 0..1 (delta_T = +1), so a
@@ -139,11 +139,11 @@ def step_growth_scheme(f: int, k: float, theta: int = 10, r_react: float = 1.1,
     mv[TYPE_A] = f
     return dict(mask_A=1 << TYPE_A, mask_T=1 << TYPE_B, a_lo=1, a_hi=f, t_lo=0, t_hi=1, dA=-1,
                 dT=+1, k=k, theta=theta, r_react=r_react, bond_style=bond_style,
-                max_valence=tuple(mv))
+                max_valence=tuple(mv), selection=selection)
 
 
 def chain_growth_scheme(k: float, theta: int = 10, r_react: float = 1.1,
-                        bond_style: int = 0) -> dict:
+                        bond_style: int = 0, selection: int = 0) -> dict:
     """Chain growth, Sec. II.A: states M = 0, P = 1, P* = 2.  The active end
     P* (an initiator of type A or a monomer of type B) binds a monomer M of
     type B; the old end becomes P (delta_A = -1) and the monomer becomes the
@@ -153,7 +153,7 @@ def chain_growth_scheme(k: float, theta: int = 10, r_react: float = 1.1,
     mv[TYPE_A] = 1
     return dict(mask_A=(1 << TYPE_A) | (1 << TYPE_B), mask_T=1 << TYPE_B, a_lo=2, a_hi=2, t_lo=0,
                 t_hi=0, dA=-1, dT=+2, k=k, theta=theta, r_react=r_react, bond_style=bond_style,
-                max_valence=tuple(mv))
+                max_valence=tuple(mv), selection=selection)
 
 
 CHAIN_PHI0 = 328 / 33_096  # initiator fraction of the chain-growth workload

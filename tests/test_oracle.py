@@ -380,6 +380,68 @@ def test_brute_force_enumeration_tiny():
             assert s.state[a] == before[a] - 1 and s.state[t] == before[t] + 1
 
 
+# ---- the LAMMPS nearest-partner rule (Sec. IV.A) -----------------------------
+def nearest_rx(k=200.0, theta=1, f=4):
+    return rx_of(synth.step_growth_scheme(f=f, k=k, theta=theta, selection=orc.SELECT_NEAREST))
+
+
+def test_nearest_rule_hand_built():
+    """A0 - T1 at 0.9 and A3 - T2 at 0.8 are mutual nearest pairs; A0 - T2 at
+    1.0 is in range but neither picks the other: two bonds, always (p = 1),
+    where the random rule would sometimes pair A0 with T2."""
+    A, B = synth.TYPE_A, synth.TYPE_B
+    x = [[1, 1, 1], [1.9, 1, 1], [1, 2.0, 1], [1, 2.8, 1]]
+    s = make(x, [A, B, B, A], [4, 0, 0, 4])
+    tr = orc.react(s, md_for(10.0), nearest_rx(), step=7)
+    assert tr == dict(candidates=3, retained=2, a_winners=2, formed=2)
+    assert sorted(map(tuple, s.bonds()[:, 1:3].tolist())) == [(0, 1), (3, 2)]
+    # without T1, A0's nearest is T2, whose nearest is A3: A0 stays unbonded
+    s = make([x[0], [5.0, 5.0, 5.0], x[2], x[3]], [A, B, B, A], [4, 0, 0, 4])
+    tr = orc.react(s, md_for(10.0), nearest_rx(), step=7)
+    assert tr["retained"] == 1 and s.bonds()[:, 1:3].tolist() == [[3, 2]]
+
+
+def test_nearest_rule_brute_force():
+    """Independent enumeration on random dense configurations: with p = 1 the
+    bonds are exactly the mutual nearest (A, T) pairs; with p < 1 a subset, of
+    which each pair's draw, keyed by (step, smaller id, larger id, tag 5),
+    is below p."""
+    rng = np.random.default_rng(11)
+    for trial in range(120):
+        n, L = 30, 4.0
+        x = rng.random((n, 3)) * L
+        types = rng.integers(0, 2, n)
+        states = np.where(types == synth.TYPE_A, rng.integers(0, 5, n), rng.integers(0, 3, n))
+        isA = (types == synth.TYPE_A) & (states >= 1) & (states <= 4)
+        isT = (types == synth.TYPE_B) & (states <= 1)
+        d2 = np.full((n, n), np.inf)
+        for i in range(n):
+            for j in range(n):
+                if (isA[i] and isT[j]) or (isT[i] and isA[j]):
+                    d = x[j] - x[i]
+                    d = np.where(d > L / 2, d - L, np.where(d < -L / 2, d + L, d))
+                    r2 = float(d @ d)
+                    if r2 < 1.21:
+                        d2[i, j] = r2
+        near = [int(np.argmin(d2[i])) if np.isfinite(d2[i]).any() else -1 for i in range(n)]
+        mutual = {(a, near[a]) for a in range(n) if isA[a] and near[a] >= 0 and near[near[a]] == a}
+        k = 200.0 if trial % 2 == 0 else 60.0  # p = 1 or 0.3
+        s = make(x, types, states, L=L)
+        md = md_for(L, seed=1000 + trial)
+        tr = orc.react(s, md, nearest_rx(k=k), step=3)
+        formed = {(int(r[1]), int(r[2])) for r in s.bonds()}
+        assert tr["retained"] == len(mutual)
+        if k == 200.0:
+            assert formed == mutual
+        else:
+            assert formed <= mutual
+            p = k * 0.005
+            for a, t in mutual:
+                lo, hi = min(a, t), max(a, t)
+                w = orc.philox4x32_10([3, lo, hi, 5], [1000 + trial, 0])
+                assert ((a, t) in formed) == (orc.u53(w[0], w[1]) < p)
+
+
 def check_invariants(s, scheme, f, new_steps):
     n = s.n
     b = s.bonds()
