@@ -55,6 +55,9 @@ extern "C" {
 /* ---- constants ------------------------------------------------------- */
 #define PRX_BOND_FENE 0       /* Kremer-Grest FENE, Sec. II.C */
 #define PRX_BOND_MIRROR_LJ 1  /* mirror Lennard-Jones, Eq. 17 */
+#define PRX_SELECT_RANDOM 0   /* Table I: one T per A, one A per T, each at random */
+#define PRX_SELECT_NEAREST 1  /* LAMMPS fix bond/create (Sec. IV.A): mutual nearest
+                                 A-T pairs, then the acceptance test */
 #define PRX_FORCE_FP32 0      /* pair and bond forces in FP32, integration in FP64 */
 #define PRX_FORCE_FP64 1      /* everything in FP64 */
 #define PRX_MAX_TYPES 8
@@ -100,6 +103,7 @@ typedef struct {
   double r_react;         /* reaction cutoff (strict: r^2 < r_react^2, FP64) */
   uint32_t theta;         /* reaction interval Theta >= 1 */
   int32_t bond_style;     /* style of the created bonds */
+  int32_t selection;      /* PRX_SELECT_RANDOM or PRX_SELECT_NEAREST */
   uint8_t max_valence[PRX_MAX_TYPES]; /* per type: bonds a particle may hold */
 } prx_reaction_desc;
 
@@ -112,7 +116,8 @@ typedef struct {
   uint32_t reserved;
 } prx_bond;
 
-/* Counts of Table I for one reaction step. */
+/* Counts of Table I for one reaction step.  With PRX_SELECT_NEAREST:
+ * retained = mutual nearest pairs, a_winners = those accepted. */
 typedef struct {
   int64_t candidates;     /* step 1: eligible pairs within the cutoff */
   int64_t retained;       /* step 2: accepted by u < k dt Theta */

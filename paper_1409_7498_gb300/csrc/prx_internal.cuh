@@ -37,7 +37,8 @@ constexpr int RX_THREADS = 256;
 constexpr int SCAN_TILE = 2048;  // elements per scan tile (256 threads x 8)
 
 // Counter tags of the keyed Philox draws (fourth counter word, low byte).
-constexpr uint32_t TAG_THERMO = 1u, TAG_ACCEPT = 2u, TAG_SEL_A = 3u, TAG_SEL_T = 4u;
+constexpr uint32_t TAG_THERMO = 1u, TAG_ACCEPT = 2u, TAG_SEL_A = 3u, TAG_SEL_T = 4u,
+                   TAG_NEAREST = 5u;
 
 struct SoA {
   double *x, *y, *z, *vx, *vy, *vz;
@@ -89,6 +90,7 @@ struct RxParams {
   double rr2;       // r_react^2 (exact test)
   float rr2_pre;    // (r_react + margin)^2 (FP32 prefilter, always conservative)
   uint32_t style;
+  int32_t rule;     // PRX_SELECT_RANDOM or PRX_SELECT_NEAREST
   uint8_t maxval[PRX_MAX_TYPES];
 };
 
@@ -319,7 +321,7 @@ void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
                void (*hook)(void*, const char*, int), void* hook_ctx);
 void launch_observables(const Sys& S, cudaStream_t st, int nblocks);
 int rebin_kernel_count();
-int rx_kernel_count();
+int rx_kernel_count(int rule);
 int step_kernel_count(int fp64);
 size_t build_tile_smem(const Sys& S);
 int configure_build_kernel(size_t smem_bytes);

@@ -144,6 +144,8 @@ int validate_rx(prx_system* sys, const prx_reaction_desc* r) {
     return fail(sys, PRX_EINVAL, "theta >= 1, k >= 0, r_react > 0 required");
   if (r->bond_style != PRX_BOND_FENE && r->bond_style != PRX_BOND_MIRROR_LJ)
     return fail(sys, PRX_EINVAL, "unknown bond style");
+  if (r->selection != PRX_SELECT_RANDOM && r->selection != PRX_SELECT_NEAREST)
+    return fail(sys, PRX_EINVAL, "unknown selection rule");
   if ((r->type_mask_A | r->type_mask_T) >> PRX_MAX_TYPES) return fail(sys, PRX_EINVAL, "type mask beyond 8 types");
   if ((r->type_mask_A & r->type_mask_T) && !(r->a_hi < r->t_lo || r->t_hi < r->a_lo))
     return fail(sys, PRX_EINVAL, "A and T state windows overlap for a type in both masks");
@@ -377,7 +379,7 @@ int direct_step(prx_system* sys) {
   sys->host_step++;
   if (sys->has_rx && sys->host_step % sys->rxd.theta == 0) {
     launch_rx(sys->S, sys->stream, -1, prof_hook, sys);
-    sys->other_launches += rx_kernel_count();
+    sys->other_launches += rx_kernel_count(sys->S.R.rule);
   }
   CK(cudaGetLastError());
   return PRX_OK;
@@ -868,6 +870,7 @@ int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx) {
   R.rr2 = rx->r_react * rx->r_react;
   R.rr2_pre = (float)((rx->r_react + 1e-3) * (rx->r_react + 1e-3));
   R.style = (uint32_t)rx->bond_style;
+  R.rule = rx->selection;
   for (int t = 0; t < PRX_MAX_TYPES; ++t) R.maxval[t] = rx->max_valence[t];
   sys->has_rx = 1;
   sys->S.has_rx = 1;
@@ -930,7 +933,7 @@ int prx_react_once(prx_system* sys, uint64_t step, prx_rx_trace* trace) {
   if (!sys->has_rx) return fail(sys, PRX_EINVAL, "no reaction scheme set");
   if (sys->S.n) {
     launch_rx(sys->S, sys->stream, (long long)step, sys->profiling ? prof_hook : nullptr, sys);
-    sys->other_launches += rx_kernel_count();
+    sys->other_launches += rx_kernel_count(sys->S.R.rule);
     CK(cudaGetLastError());
   }
   int rc = sync_status(sys);
@@ -1110,7 +1113,7 @@ int prx_get_stats(prx_system* sys, prx_stats* out) {
   // sequence of kernels and increments the device counter once
   out->kernel_launches = sys->step_launches * (uint64_t)step_kernel_count(sys->d.force_precision) +
                          sys->ctl_host->rebins * (uint64_t)rebin_kernel_count() +
-                         sys->graph_rx_launches * (uint64_t)rx_kernel_count() + sys->other_launches;
+                         sys->graph_rx_launches * (uint64_t)rx_kernel_count(sys->S.R.rule) + sys->other_launches;
   for (int k = 0; k < 3; ++k) {
     out->cells[k] = (uint32_t)sys->S.nc[k];
     out->cell_edge[k] = sys->d.box[k] / sys->S.nc[k];

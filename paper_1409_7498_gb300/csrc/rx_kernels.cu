@@ -113,6 +113,48 @@ __global__ void __launch_bounds__(RX_THREADS)
   rx_compact_body(S, Blk{m.b, m.nb});
 }
 
+// LAMMPS rule (Sec. IV.A): the eligible partner of the other kind (a T when
+// want_T, else an A) within r_react of slot i, not bonded to it, of smallest
+// exact r^2 (ties to the smaller id); `in_range` counts the pairs in range.
+template <bool NL16>
+__device__ __forceinline__ uint32_t nearest_partner(const Sys& S, const SoA& B, const uint4* P,
+                                                    uint32_t i, bool want_T, long long& in_range) {
+  const RxParams& R = S.R;
+  const uint4 pi = P[i];
+  const double xi = B.x[i], yi = B.y[i], zi = B.z[i];
+  const uint32_t nb = B.nadj[i];
+  uint32_t best = NONE, bestid = 0u;
+  double best_r2 = 0.0;
+  const int cnt = S.nn[i];
+  for (int k = 0; k < cnt; ++k) {
+    const uint32_t j = nl_get_rx<NL16>(S, k, i);
+    const bool ok = want_T ? in_window(R.mask_T, R.t_lo, R.t_hi, B.type[j], B.state[j])
+                           : in_window(R.mask_A, R.a_lo, R.a_hi, B.type[j], B.state[j]);
+    if (!ok) continue;
+    const uint4 pj = P[j];
+    const float ex = __int2float_rn(pdiff(pj.x, pi.x)) * S.scale[0];
+    const float ey = __int2float_rn(pdiff(pj.y, pi.y)) * S.scale[1];
+    const float ez = __int2float_rn(pdiff(pj.z, pi.z)) * S.scale[2];
+    if (!(fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < R.rr2_pre)) continue;
+    const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
+    const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
+    const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
+    const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
+    if (!(r2 < R.rr2)) continue;
+    bool bonded = false;
+    for (uint32_t b = 0; b < nb; ++b) bonded |= (B.adj[(size_t)i * S.cap + b] & SLOT_MASK) == j;
+    if (bonded) continue;
+    ++in_range;
+    const uint32_t idj = B.id[j];
+    if (best == NONE || r2 < best_r2 || (r2 == best_r2 && idj < bestid)) {
+      best = j;
+      best_r2 = r2;
+      bestid = idj;
+    }
+  }
+  return best;
+}
+
 // Steps 1-5 for one eligible A: its Verlet list holds every particle within
 // the force cutoff, hence every candidate within r_react <= r_c.  Grid-stride
 // over the work list of eligible A's.
@@ -129,7 +171,9 @@ __device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long l
   for (uint32_t w = blk.b * blockDim.x + threadIdx.x; w < nact; w += blk.nb * blockDim.x) {
     const uint32_t i = S.tmp[w];
     uint32_t best = NONE;
-    {
+    if (R.rule == PRX_SELECT_NEAREST) {
+      best = nearest_partner<NL16>(S, B, P, i, true, ncand);
+    } else {
       const uint4 pi = P[i];
       const double xi = B.x[i], yi = B.y[i], zi = B.z[i];
       const uint32_t idi = B.id[i];
@@ -203,9 +247,21 @@ __device__ __forceinline__ void rx_select_T_body(const Sys& S, const Blk blk, lo
   const unsigned long long step = step_arg >= 0 ? (unsigned long long)step_arg : ctl->step;
   const SoA B = ctl->set ? S.s1 : S.s0;
   const uint32_t i = blk.b * blockDim.x + threadIdx.x;
+  const RxParams& R = S.R;
   uint32_t fin = NONE;
   bool winner = false;
-  if (i < S.n) {
+  if (i < S.n && R.rule == PRX_SELECT_NEAREST) {
+    // LAMMPS rule: an A and the T it picked react when the T picked it too
+    // and u < k dt Theta, drawn with the pair's smaller id first
+    const uint32_t T = in_window(R.mask_A, R.a_lo, R.a_hi, B.type[i], B.state[i]) ? S.win[i] : NONE;
+    if (T != NONE && S.win[T] == i) {
+      winner = true;
+      const uint32_t ida = B.id[i], idt = B.id[T];
+      const uint4 w = keyed_draw(S.seed, step, min(ida, idt), max(ida, idt), TAG_NEAREST);
+      if (u53(w.x, w.y) < R.p) fin = T;
+    }
+    S.fin[i] = fin;
+  } else if (i < S.n) {
     const uint32_t T = S.win[i];
     if (T != NONE) {
       winner = true;
@@ -231,8 +287,41 @@ __device__ __forceinline__ void rx_select_T_body(const Sys& S, const Blk blk, lo
   const int nwin = __syncthreads_count(winner);
   if (threadIdx.x == 0) {
     S.blk_count[blk.b] = (uint32_t)nfin;
-    if (nwin) atomicAdd((unsigned long long*)&ctl->trace[2], (unsigned long long)nwin);
+    if (R.rule == PRX_SELECT_NEAREST) {  // mutual pairs, accepted pairs
+      if (nwin) atomicAdd((unsigned long long*)&ctl->trace[1], (unsigned long long)nwin);
+      if (nfin) atomicAdd((unsigned long long*)&ctl->trace[2], (unsigned long long)nfin);
+    } else if (nwin) {
+      atomicAdd((unsigned long long*)&ctl->trace[2], (unsigned long long)nwin);
+    }
   }
+}
+
+// LAMMPS rule: every eligible T picks its nearest eligible A (win[] of T
+// slots; win[] of A slots holds the A's nearest T).
+template <bool NL16>
+__device__ __forceinline__ void rx_find_T_body(const Sys& S, const Blk blk) {
+  const RxParams& R = S.R;
+  if (R.rule != PRX_SELECT_NEAREST) return;
+  Ctl* ctl = S.ctl;
+  const SoA B = ctl->set ? S.s1 : S.s0;
+  const uint4* P = ctl->phase ? S.P1 : S.P0;
+  const uint32_t i = blk.b * blockDim.x + threadIdx.x;
+  if (i >= S.n || !in_window(R.mask_T, R.t_lo, R.t_hi, B.type[i], B.state[i])) return;
+  long long unused = 0;
+  S.win[i] = nearest_partner<NL16>(S, B, P, i, false, unused);
+}
+
+template <bool NL16>
+__global__ void __launch_bounds__(RX_THREADS) k_rx_find_T(Sys S) {
+  rx_find_T_body<NL16>(S, Blk{blockIdx.x, gridDim.x});
+}
+__global__ void __launch_bounds__(RX_THREADS)
+    kb_rx_find_T(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+  const BlkMap m = M[blockIdx.x];
+  const Sys& S = T[m.sys];
+  if (!S.has_rx) return;  // this member has no reaction scheme
+  if (S.nl16) rx_find_T_body<true>(S, Blk{m.b, m.nb});
+  else rx_find_T_body<false>(S, Blk{m.b, m.nb});
 }
 
 template <bool NL16>
@@ -443,7 +532,7 @@ inline unsigned blocks_rx(uint32_t n) { return n ? (n + RX_THREADS - 1) / RX_THR
 
 }  // namespace
 
-int rx_kernel_count() { return 6; }
+int rx_kernel_count(int rule) { return rule == PRX_SELECT_NEAREST ? 7 : 6; }
 
 void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
                void (*hook)(void*, const char*, int), void* ctx) {
@@ -460,6 +549,12 @@ void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
   if (S.nl16) k_rx_find<true><<<gf, RX_THREADS, 0, st>>>(S, step_arg);
   else k_rx_find<false><<<gf, RX_THREADS, 0, st>>>(S, step_arg);
   H("rx_find", 1);
+  if (S.R.rule == PRX_SELECT_NEAREST) {
+    H("rx_find_T", 0);
+    if (S.nl16) k_rx_find_T<true><<<g, RX_THREADS, 0, st>>>(S);
+    else k_rx_find_T<false><<<g, RX_THREADS, 0, st>>>(S);
+    H("rx_find_T", 1);
+  }
   H("rx_select_T", 0);
   if (S.nl16) k_rx_select_T<true><<<g, RX_THREADS, 0, st>>>(S, step_arg);
   else k_rx_select_T<false><<<g, RX_THREADS, 0, st>>>(S, step_arg);
@@ -483,12 +578,13 @@ void launch_observables(const Sys& S, cudaStream_t st, int nblocks) {
   k_obs_sums<<<nblocks, RX_THREADS, 0, st>>>(S, S.mass);
 }
 
-int batch_rx_kernel_count() { return 7; }
+int batch_rx_kernel_count() { return 8; }
 
 void launch_batch_rx(const BatchLaunch& L, cudaStream_t st) {
   kb_rx_begin<<<L.n_one, 32, 0, st>>>(L.T, L.one);
   kb_rx_compact<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
   kb_rx_find<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
+  kb_rx_find_T<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
   kb_rx_select_T<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
   kb_rx_scan<<<L.n_one, 1024, 0, st>>>(L.T, L.one);
   kb_rx_apply<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);

@@ -18,6 +18,7 @@ PRX_OK = 0
 PRX_EINVAL, PRX_ENOMEM, PRX_ECAPACITY, PRX_EOVERSTRETCH = -1, -2, -3, -4
 PRX_ENONFINITE, PRX_ETIMEOUT, PRX_ECUDA, PRX_EIO = -5, -6, -7, -8
 PRX_BOND_FENE, PRX_BOND_MIRROR_LJ = 0, 1
+PRX_SELECT_RANDOM, PRX_SELECT_NEAREST = 0, 1
 PRX_FORCE_FP32, PRX_FORCE_FP64 = 0, 1
 PRX_MAX_TYPES, PRX_MAX_STATES, PRX_MAX_ADJ = 8, 16, 8
 
@@ -41,7 +42,7 @@ class prx_reaction_desc(C.Structure):
     _fields_ = [("type_mask_A", C.c_uint32), ("type_mask_T", C.c_uint32), ("a_lo", C.c_int32),
                 ("a_hi", C.c_int32), ("t_lo", C.c_int32), ("t_hi", C.c_int32), ("dA", C.c_int32),
                 ("dT", C.c_int32), ("k", C.c_double), ("r_react", C.c_double),
-                ("theta", C.c_uint32), ("bond_style", C.c_int32),
+                ("theta", C.c_uint32), ("bond_style", C.c_int32), ("selection", C.c_int32),
                 ("max_valence", C.c_uint8 * PRX_MAX_TYPES)]
 
 
@@ -165,10 +166,11 @@ def make_desc(n, box, *, adj_cap=4, dt=0.005, kT=1.0, gamma=1.0, mass=1.0, wca_e
 
 
 def make_reaction(mask_A, mask_T, a_lo, a_hi, t_lo, t_hi, dA, dT, k, theta=10, r_react=1.1,
-                  bond_style=PRX_BOND_FENE, max_valence=(8,) * 8) -> prx_reaction_desc:
+                  bond_style=PRX_BOND_FENE, max_valence=(8,) * 8,
+                  selection=PRX_SELECT_RANDOM) -> prx_reaction_desc:
     mv = list(max_valence) + [0] * (8 - len(max_valence))
     return prx_reaction_desc(mask_A, mask_T, a_lo, a_hi, t_lo, t_hi, dA, dT, float(k),
-                             float(r_react), int(theta), int(bond_style),
+                             float(r_react), int(theta), int(bond_style), int(selection),
                              (C.c_uint8 * 8)(*mv[:8]))
 
 

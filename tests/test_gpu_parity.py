@@ -61,19 +61,24 @@ def gpu_from_oracle_state(P, inp, o, cap, seed, fp64=False, **kw):
 # ---------------------------------------------------------------------------
 # Reaction step: bit-exact
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("kind,n,k,pre", [
-    ("step_cfg1", 1250, 0.1, 0),
-    ("step_cfg1", 1250, 20.0, 3),
-    ("step4", 1257, 200.0, 2),       # p = 1: every candidate retained
-    ("step6", 4099, 5.0, 2),
-    ("chain", 3001, 1.0, 4),
-    ("chain", 33096, 0.1, 2),
-    ("step4", 33096, 2.0, 3),
+@pytest.mark.parametrize("kind,n,k,pre,sel", [
+    ("step_cfg1", 1250, 0.1, 0, 0),
+    ("step_cfg1", 1250, 20.0, 3, 0),
+    ("step4", 1257, 200.0, 2, 0),       # p = 1: every candidate retained
+    ("step6", 4099, 5.0, 2, 0),
+    ("chain", 3001, 1.0, 4, 0),
+    ("chain", 33096, 0.1, 2, 0),
+    ("step4", 33096, 2.0, 3, 0),
+    # the LAMMPS nearest-partner rule (Sec. IV.A)
+    ("step_cfg1", 1250, 20.0, 3, 1),
+    ("step4", 1257, 200.0, 2, 1),
+    ("chain", 3001, 1.0, 4, 1),
+    ("step4", 33096, 2.0, 3, 1),
 ])
-def test_react_once_bit_exact(P, kind, n, k, pre):
+def test_react_once_bit_exact(P, kind, n, k, pre, sel):
     seed = 7 + n
     inp, scheme, cap, o, md = seeded_state(kind, n, seed, pre_reactions=pre)
-    sch = dict(scheme, k=k)
+    sch = dict(scheme, k=k, selection=sel)
     g = gpu_from_oracle_state(P, inp, o, cap, seed)
     g.set_reaction(gpu_reaction(P, sch))
     for step in (10, 20, 30):
