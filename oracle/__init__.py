@@ -52,6 +52,10 @@ class _MD(C.Structure):
     ]
 
 
+class _CLASS(C.Structure):
+    _fields_ = [("type_mask", C.c_uint32), ("s_lo", C.c_int32), ("s_hi", C.c_int32)]
+
+
 class _RX(C.Structure):
     _fields_ = [
         ("mask_A", C.c_uint32), ("mask_T", C.c_uint32), ("a_lo", C.c_int32), ("a_hi", C.c_int32),
@@ -101,6 +105,9 @@ def lib():
         _lib.orc_react.argtypes = [P(_SYS), P(_MD), P(_RX), C.c_int, C.c_int64, P(_TRACE)]
         _lib.orc_observables.argtypes = [P(_SYS), P(_MD), P(_OBS)]
         _lib.orc_run.argtypes = [P(_SYS), P(_MD), P(_RX), C.c_int64, C.c_int, P(_OBS), C.c_int64]
+        _lib.orc_pair_histogram.argtypes = [P(_SYS), P(_MD), P(_CLASS), P(_CLASS), C.c_double,
+                                            C.c_int32, P(C.c_int64), P(C.c_int64),
+                                            P(C.c_int64)]
     return _lib
 
 
@@ -310,3 +317,16 @@ def run(sys: System, md: MDParams, rx: Reaction | None, nsteps: int, use_cells: 
     sys._sync_back(cs)
     _check(rc, "run")
     return [_obs_dict(obs[i]) for i in range(nrx)]
+
+
+def pair_histogram(sys: System, md: MDParams, a: tuple, b: tuple, r_max: float, nbins: int):
+    """Pair-distance histogram between class a and class b, each given as
+    (type_mask, state_lo, state_hi); returns (counts, n_a, n_b)."""
+    cs = sys._c()
+    counts = (C.c_int64 * nbins)()
+    na, nb = C.c_int64(), C.c_int64()
+    rc = lib().orc_pair_histogram(C.byref(cs), C.byref(md._c()), C.byref(_CLASS(*a)),
+                                  C.byref(_CLASS(*b)), float(r_max), int(nbins), counts,
+                                  C.byref(na), C.byref(nb))
+    _check(rc, "pair_histogram")
+    return np.array(list(counts), dtype=np.int64), na.value, nb.value

@@ -698,3 +698,44 @@ int orc_run(orc_system* s, const orc_md_params* md, const orc_rx_params* rx, int
   }
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------
+ * Pair-distance histogram between two particle classes (the data behind
+ * g_AB(r) and <N_AB>, Secs. V-VI), all pairs.
+ * ---------------------------------------------------------------------- */
+static int in_class(const orc_system* s, const orc_class* c, int64_t i) {
+  return ((c->type_mask >> (s->type[i] & 31)) & 1u) && s->state[i] >= c->s_lo && s->state[i] <= c->s_hi;
+}
+
+int orc_pair_histogram(const orc_system* s, const orc_md_params* md, const orc_class* a,
+                       const orc_class* b, double r_max, int32_t nbins, int64_t* counts,
+                       int64_t* n_a, int64_t* n_b) {
+  if (!s || !md || !a || !b || !counts || nbins < 1 || !(r_max > 0.0)) return ORC_EINVAL;
+  double* e2 = (double*)malloc(sizeof(double) * (size_t)(nbins + 1));
+  if (!e2) return ORC_ENOMEM;
+  for (int32_t k = 0; k <= nbins; ++k) {
+    const double e = r_max * (double)k / (double)nbins;
+    e2[k] = e * e;
+  }
+  for (int32_t k = 0; k < nbins; ++k) counts[k] = 0;
+  int64_t na = 0, nb = 0;
+  for (int64_t i = 0; i < s->n; ++i) {
+    nb += in_class(s, b, i);
+    if (!in_class(s, a, i)) continue;
+    na++;
+    for (int64_t j = 0; j < s->n; ++j) {
+      if (j == i || !in_class(s, b, j)) continue;
+      double d[3];
+      separation(s->x, i, j, md->L, d);
+      const double r2 = dist2_fixed(d);
+      if (!(r2 < e2[nbins])) continue;
+      int32_t k = 0;
+      while (k + 1 < nbins && e2[k + 1] <= r2) ++k;
+      counts[k]++;
+    }
+  }
+  if (n_a) *n_a = na;
+  if (n_b) *n_b = nb;
+  free(e2);
+  return ORC_OK;
+}

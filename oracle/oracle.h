@@ -113,6 +113,22 @@ int orc_check_reaction(const orc_rx_params* rx);
 int orc_react(orc_system* s, const orc_md_params* md, const orc_rx_params* rx,
               int use_cells, int64_t step, orc_rx_trace* trace);
 int orc_observables(const orc_system* s, const orc_md_params* md, orc_obs* o);
+
+/* A particle class: type in the mask and state in [s_lo, s_hi]. */
+typedef struct {
+  uint32_t type_mask;
+  int32_t s_lo, s_hi;
+} orc_class;
+
+/* Pair-distance histogram between two classes, the raw data of the radial
+ * distribution g_AB(r) whose integral up to the reaction cutoff gives the
+ * mean number of available partners <N_AB> (Secs. V, VI):
+ *   counts[k] = #{(i, j): i in a, j in b, j != i, e_k^2 <= r_ij^2 < e_(k+1)^2}
+ * with e_k = r_max k / nbins, r_ij^2 = fma(dz, dz, fma(dy, dy, dx dx)) under
+ * the minimum image.  *n_a, *n_b receive the class sizes. */
+int orc_pair_histogram(const orc_system* s, const orc_md_params* md, const orc_class* a,
+                       const orc_class* b, double r_max, int32_t nbins, int64_t* counts,
+                       int64_t* n_a, int64_t* n_b);
 int orc_run(orc_system* s, const orc_md_params* md, const orc_rx_params* rx,
             int64_t nsteps, int use_cells, orc_obs* obs_per_reaction, int64_t obs_cap);
 

@@ -563,3 +563,33 @@ def test_chain_fraction_limits():
     assert req.chain_fraction(0.0, 0.1, 3.25, 0.01) == pytest.approx(0.01)
     assert req.chain_fraction(1e6, 0.1, 3.25, 0.01) == pytest.approx(1.0)
     assert req.chain_fraction(0.0, 0.1, 3.25, 0.01, approximate=True) == 0.0
+
+
+# ---- pair-distance histogram (g(r) -> <N>, Secs. V-VI) ----------------------
+def test_pair_histogram_lattice_shells():
+    """Simple cubic lattice: 6, 12 and 8 neighbours at a, a sqrt2, a sqrt3."""
+    m, a = 6, 1.0
+    g = np.stack(np.meshgrid(*[np.arange(m)] * 3, indexing="ij"), -1).reshape(-1, 3) * a + 0.5
+    s = orc.System(g, np.zeros_like(g), np.zeros(len(g), np.uint8), np.zeros(len(g), np.int8),
+                   cap=1)
+    c, na, nb = orc.pair_histogram(s, md_for(m * a), (1, 0, 0), (1, 0, 0), 2.0, 20)
+    assert na == nb == m ** 3
+    expect = np.zeros(20, np.int64)
+    expect[10], expect[14], expect[17] = 6 * na, 12 * na, 8 * na  # bins of 0.1
+    assert np.array_equal(c, expect)
+
+
+def test_pair_histogram_ideal_gas_and_symmetry():
+    """Uniform random points: counts per shell = N_a rho_b V_shell within 5
+    sigma; counting (a, b) and (b, a) gives the same histogram."""
+    rng = np.random.default_rng(5)
+    n, L = 3000, 12.0
+    x = rng.random((n, 3)) * L
+    t = rng.integers(0, 2, n).astype(np.uint8)
+    s = orc.System(x, np.zeros_like(x), t, np.zeros(n, np.int8), cap=1)
+    ca, na, nb = orc.pair_histogram(s, md_for(L), (1, 0, 0), (2, 0, 0), 1.5, 15)
+    cb, nb2, na2 = orc.pair_histogram(s, md_for(L), (2, 0, 0), (1, 0, 0), 1.5, 15)
+    assert np.array_equal(ca, cb) and na == na2 and nb == nb2
+    edges = np.linspace(0, 1.5, 16)
+    expect = na * nb / L ** 3 * 4.0 / 3.0 * np.pi * np.diff(edges ** 3)
+    assert np.all(np.abs(ca - expect) < 5 * np.sqrt(expect) + 1)
