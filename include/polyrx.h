@@ -215,6 +215,27 @@ int prx_get_observables(prx_system* sys, prx_observables* out);
 int prx_get_history(prx_system* sys, prx_history_record* out, uint64_t cap, uint64_t* n_out);
 int prx_get_stats(prx_system* sys, prx_stats* out);
 
+/* ---- analysis ----------------------------------------------------------------- */
+/* A particle class: type bit set in type_mask, state in [s_lo, s_hi]. */
+typedef struct {
+  uint32_t type_mask;
+  int32_t s_lo, s_hi;
+} prx_class;
+
+/* Pair-distance histogram between class a and class b at the current
+ * positions: counts[k] (host, nbins entries) receives the number of ordered
+ * pairs (i in a, j in b, j != i) with e_k^2 <= r_ij^2 < e_(k+1)^2, where
+ * e_k = r_max k / nbins and r_ij^2 is the exact FP64 minimum-image distance
+ * of the reaction test.  These are the data of the radial distribution
+ * g_ab(r) whose integral up to the reaction cutoff is the mean number of
+ * available partners <N_ab> (Secs. V-VI); *n_a, *n_b (may be NULL) receive
+ * the class sizes.  The pairs come from the Verlet lists, which hold every
+ * pair closer than the larger of the WCA and reaction cutoffs: r_max above
+ * it, or nbins outside 1..2048, is PRX_EINVAL.  Read-only: allowed for a batch
+ * member (it waits for the batch's stream).  Synchronises. */
+int prx_pair_histogram(prx_system* sys, const prx_class* a, const prx_class* b, double r_max,
+                       uint32_t nbins, uint64_t* counts, uint64_t* n_a, uint64_t* n_b);
+
 /* ---- checkpoint ------------------------------------------------------------ */
 /* Writes positions, velocities, types, states, bonds, step, descriptor and
  * reaction scheme.  Every random draw is keyed by (seed, step, ids), so a

@@ -94,6 +94,12 @@ struct RxParams {
   uint8_t maxval[PRX_MAX_TYPES];
 };
 
+// A particle class of the pair histogram: type in the mask, state in [lo, hi].
+struct PairClass {
+  uint32_t mask;
+  int32_t lo, hi;
+};
+
 // Control block shared by the members of a batch.
 struct BatchCtl {
   int any_rebuild;          // some member needs a rebuild after this step
@@ -320,6 +326,9 @@ void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, c
 void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
                void (*hook)(void*, const char*, int), void* hook_ctx);
 void launch_observables(const Sys& S, cudaStream_t st, int nblocks);
+void launch_pair_hist(const Sys& S, cudaStream_t st, const PairClass& a, const PairClass& b,
+                      const double* e2, int nbins, unsigned long long* counts,
+                      unsigned long long* nab);
 int rebin_kernel_count();
 int rx_kernel_count(int rule);
 int step_kernel_count(int fp64);

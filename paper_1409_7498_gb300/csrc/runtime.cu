@@ -1327,6 +1327,48 @@ int prx_load(const char* path, void* cuda_stream, prx_system** out) {
   return PRX_OK;
 }
 
+// ---- analysis ---------------------------------------------------------------------
+
+int prx_pair_histogram(prx_system* sys, const prx_class* a, const prx_class* b, double r_max,
+                       uint32_t nbins, uint64_t* counts, uint64_t* n_a, uint64_t* n_b) {
+  if (!sys || !a || !b || !counts || nbins < 1 || nbins > 2048) return PRX_EINVAL;
+  if (!(r_max > 0.0) || r_max > sys->grid_rcut)
+    return fail(sys, PRX_EINVAL, "r_max beyond the cutoff the Verlet lists guarantee");
+  std::vector<double> e2(nbins + 1);
+  for (uint32_t k = 0; k <= nbins; ++k) {
+    const double e = r_max * (double)k / (double)nbins;
+    e2[k] = e * e;
+  }
+  double* d_e2 = nullptr;
+  unsigned long long* d_c = nullptr;
+  CK(cudaMalloc(&d_e2, sizeof(double) * (nbins + 1)));
+  if (cudaMalloc(&d_c, sizeof(unsigned long long) * (nbins + 2)) != cudaSuccess) {
+    cudaFree(d_e2);
+    return fail(sys, PRX_ENOMEM, "histogram buffers");
+  }
+  std::vector<unsigned long long> h(nbins + 2, 0ull);
+  cudaError_t e = cudaMemcpyAsync(d_e2, e2.data(), sizeof(double) * (nbins + 1), cudaMemcpyHostToDevice,
+                                  sys->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_c, 0, sizeof(unsigned long long) * (nbins + 2), sys->stream);
+  if (e == cudaSuccess && sys->S.n) {
+    launch_pair_hist(sys->S, sys->stream, PairClass{a->type_mask, a->s_lo, a->s_hi},
+                     PairClass{b->type_mask, b->s_lo, b->s_hi}, d_e2, (int)nbins, d_c, d_c + nbins);
+    sys->other_launches++;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.data(), d_c, sizeof(unsigned long long) * (nbins + 2), cudaMemcpyDeviceToHost,
+                        sys->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sys->stream);
+  cudaFree(d_e2);
+  cudaFree(d_c);
+  if (e != cudaSuccess) return fail(sys, PRX_ECUDA, std::string("pair histogram: ") + cudaGetErrorString(e));
+  for (uint32_t k = 0; k < nbins; ++k) counts[k] = h[k];
+  if (n_a) *n_a = h[nbins];
+  if (n_b) *n_b = h[nbins + 1];
+  return sync_status(sys);
+}
+
 // ---- autotuner -------------------------------------------------------------------
 
 int prx_autotune_skin(const prx_system_desc* desc, const double* pos, const double* vel,

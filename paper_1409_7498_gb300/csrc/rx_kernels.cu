@@ -528,6 +528,59 @@ __global__ void kb_rx_begin(const Sys* __restrict__ T, const BlkMap* __restrict_
   S.ctl->n_active = 0u;
 }
 
+// Pair-distance histogram between two particle classes (the data of
+// g_AB(r), Secs. V-VI): one thread per slot of class a runs over its Verlet
+// list; pairs are binned by the exact FP64 r^2 (minimum image, the reaction
+// test's fma order) against the squared bin edges e2[0..nbins].  Counts are
+// integers, so the result does not depend on the order of the atomics.
+template <bool NL16>
+__global__ void __launch_bounds__(RX_THREADS)
+    k_pair_hist(Sys S, PairClass a, PairClass b, const double* __restrict__ e2, int nbins,
+                unsigned long long* counts, unsigned long long* nab) {
+  extern __shared__ __align__(16) unsigned char smem_h[];
+  double* se2 = reinterpret_cast<double*>(smem_h);
+  unsigned int* sc = reinterpret_cast<unsigned int*>(se2 + nbins + 1);
+  for (int k = threadIdx.x; k <= nbins; k += blockDim.x) se2[k] = e2[k];
+  for (int k = threadIdx.x; k < nbins; k += blockDim.x) sc[k] = 0u;
+  __syncthreads();
+  Ctl* ctl = S.ctl;
+  const SoA B = ctl->set ? S.s1 : S.s0;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool ia = false, ib = false;
+  if (i < S.n) {
+    ia = in_window(a.mask, a.lo, a.hi, B.type[i], B.state[i]);
+    ib = in_window(b.mask, b.lo, b.hi, B.type[i], B.state[i]);
+  }
+  if (ia) {
+    const double xi = B.x[i], yi = B.y[i], zi = B.z[i];
+    const double rmax2 = se2[nbins];
+    const int cnt = S.nn[i];
+    for (int k = 0; k < cnt; ++k) {
+      const uint32_t j = nl_get_rx<NL16>(S, k, i);
+      if (!in_window(b.mask, b.lo, b.hi, B.type[j], B.state[j])) continue;
+      const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
+      const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
+      const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
+      const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
+      if (!(r2 < rmax2)) continue;
+      int lo = 0, hi = nbins - 1;  // largest bin whose lower edge is <= r
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (se2[mid] <= r2) lo = mid;
+        else hi = mid - 1;
+      }
+      atomicAdd(&sc[lo], 1u);
+    }
+  }
+  const int na = __syncthreads_count(ia), nb = __syncthreads_count(ib);
+  for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+    if (sc[k]) atomicAdd(&counts[k], (unsigned long long)sc[k]);
+  if (threadIdx.x == 0) {
+    if (na) atomicAdd(&nab[0], (unsigned long long)na);
+    if (nb) atomicAdd(&nab[1], (unsigned long long)nb);
+  }
+}
+
 inline unsigned blocks_rx(uint32_t n) { return n ? (n + RX_THREADS - 1) / RX_THREADS : 1u; }
 
 }  // namespace
@@ -568,6 +621,15 @@ void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
   H("obs_hist", 0);
   k_obs_hist<<<g, RX_THREADS, 0, st>>>(S, step_arg, 1);
   H("obs_hist", 1);
+}
+
+void launch_pair_hist(const Sys& S, cudaStream_t st, const PairClass& a, const PairClass& b,
+                      const double* e2, int nbins, unsigned long long* counts,
+                      unsigned long long* nab) {
+  const unsigned g = blocks_rx(S.n);
+  const size_t sm = 8 * (size_t)(nbins + 1) + 4 * (size_t)nbins;
+  if (S.nl16) k_pair_hist<true><<<g, RX_THREADS, sm, st>>>(S, a, b, e2, nbins, counts, nab);
+  else k_pair_hist<false><<<g, RX_THREADS, sm, st>>>(S, a, b, e2, nbins, counts, nab);
 }
 
 // On-demand observables: the spare history slot (index hist_cap) receives the

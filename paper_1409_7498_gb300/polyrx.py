@@ -82,6 +82,10 @@ class prx_batch_stats(C.Structure):
                 ("kernel_launches", C.c_uint64), ("graph_launches", C.c_uint64)]
 
 
+class prx_class(C.Structure):
+    _fields_ = [("type_mask", C.c_uint32), ("s_lo", C.c_int32), ("s_hi", C.c_int32)]
+
+
 class prx_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
 
@@ -123,6 +127,8 @@ def lib():
         "prx_react_noalloc": ([P(prx_reaction_desc), P(C.c_double), C.c_double, U64, U64,
                                C.c_uint32, VP, VP, VP, C.c_uint32, VP, VP, VP, C.c_uint32, VP,
                                VP, P(prx_rx_trace)], I),
+        "prx_pair_histogram": ([VP, P(prx_class), P(prx_class), C.c_double, C.c_uint32, VP,
+                                P(U64), P(U64)], I),
         "prx_autotune_skin": ([P(prx_system_desc), VP, VP, VP, VP, P(prx_reaction_desc),
                                C.c_uint32, P(C.c_double), C.c_uint32, P(C.c_double),
                                P(C.c_double)], I),
@@ -339,6 +345,17 @@ def prx_react_noalloc(rx, box, dt, seed, step, n, d_pos, d_type, d_state, adj_ca
                 formed=t.formed)
 
 
+def prx_pair_histogram(h, a, b, r_max: float, nbins: int):
+    """Pair-distance histogram between classes a and b, each (type_mask,
+    state_lo, state_hi); returns (counts, n_a, n_b)."""
+    counts = np.zeros(int(nbins), np.uint64)
+    na, nb = C.c_uint64(), C.c_uint64()
+    _check(lib().prx_pair_histogram(h, C.byref(prx_class(*a)), C.byref(prx_class(*b)),
+                                    float(r_max), int(nbins), _ptr(counts), C.byref(na),
+                                    C.byref(nb)), h)
+    return counts.astype(np.int64), na.value, nb.value
+
+
 def prx_autotune_skin(desc: prx_system_desc, pos, vel, type_, state, rx=None, steps: int = 100,
                       skins=(0.25, 0.3, 0.35, 0.4, 0.45, 0.5)):
     """Fastest skin among the candidates; returns (best, {skin: ms per step})."""
@@ -529,3 +546,6 @@ class System:
 
     def save(self, path):
         prx_save(self.h, path)
+
+    def pair_histogram(self, a, b, r_max, nbins):
+        return prx_pair_histogram(self.h, a, b, r_max, nbins)
