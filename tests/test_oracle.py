@@ -593,3 +593,29 @@ def test_pair_histogram_ideal_gas_and_symmetry():
     edges = np.linspace(0, 1.5, 16)
     expect = na * nb / L ** 3 * 4.0 / 3.0 * np.pi * np.diff(edges ** 3)
     assert np.all(np.abs(ca - expect) < 5 * np.sqrt(expect) + 1)
+
+
+# ---- thermoneutral bonding (mirror LJ, Eq. 17 and Sec. II) ------------------
+@pytest.mark.parametrize("style", [orc.BOND_FENE, orc.BOND_MIRROR_LJ])
+def test_bond_creation_energy_jump(style):
+    """A reaction step changes no position or velocity, so the energy changes
+    by the new bonds' potential alone: zero for mirror-LJ bonds formed at
+    r <= r_react <= sigma_c (thermoneutral), and the sum of the FENE energies
+    -k R0^2 / 2 ln(1 - (r/R0)^2) of the new bonds otherwise."""
+    inp = synth.step_growth(1600, 400, 4, 9, jitter=0.5)
+    s = orc.System(inp.x, inp.v, inp.type, inp.state, cap=4)
+    md = md_for(inp.L, seed=9)
+    _, e0 = orc.forces(s, md, use_cells=True)
+    rx = rx_of(synth.step_growth_scheme(4, k=200.0, theta=1, bond_style=style))
+    orc.react(s, md, rx, step=1)
+    _, e1 = orc.forces(s, md, use_cells=True)
+    b = s.bonds()
+    assert len(b) > 50
+    if style == orc.BOND_MIRROR_LJ:
+        assert e1 == e0
+    else:
+        d = s.x[b[:, 2]] - s.x[b[:, 1]]
+        d -= inp.L * np.round(d / inp.L)
+        r2 = (d ** 2).sum(1)
+        jump = (-0.5 * 30.0 * 1.5 ** 2 * np.log(1.0 - r2 / 1.5 ** 2)).sum()
+        assert abs((e1 - e0) - jump) < 1e-9 * jump and jump > 10.0 * len(b)
