@@ -619,3 +619,39 @@ def test_bond_creation_energy_jump(style):
         r2 = (d ** 2).sum(1)
         jump = (-0.5 * 30.0 * 1.5 ** 2 * np.log(1.0 - r2 / 1.5 ** 2)).sum()
         assert abs((e1 - e0) - jump) < 1e-9 * jump and jump > 10.0 * len(b)
+
+
+# ---- step growth against the rate equation (Sec. II.B, Eq. step-kin) --------
+def test_low_functionality_step_growth_follows_the_rate_equation():
+    """f = 1 crosslinkers among difunctional targets in the short-time regime
+    (k <N> t <= 1, t <= 3): the fraction of crosslinkers that have not
+    reacted decays as exp(-k <N_XE> t), <N_XE> the mean number of available
+    targets within r_react per unreacted crosslinker, measured on the same
+    runs (Table I candidates).  Four seeds; within 3 standard errors (or
+    0.02)."""
+    k, theta, nsteps = 0.1, 10, 600
+    rx = rx_of(synth.step_growth_scheme(f=1, k=k, theta=theta))
+    fr, cand, elig = [], 0, 0
+    for seed in range(4):
+        inp = synth.step_growth(1000, 250, 1, 300 + seed)
+        s = orc.System(inp.x, inp.v, inp.type, inp.state, cap=2)
+        md = md_for(inp.L, seed=300 + seed)
+        curve = []
+        for q in range(nsteps // theta):
+            for _ in range(theta):
+                orc.step(s, md)
+            n_el = int(((s.type == synth.TYPE_A) & (s.state == 1)).sum())
+            tr = orc.react(s, md, rx, step=s.step, use_cells=True)
+            cand += tr["candidates"]
+            elig += n_el
+            curve.append(((s.type == synth.TYPE_A) & (s.state == 1)).sum() / 250.0)
+        fr.append(curve)
+    fr = np.array(fr)
+    n_mean = cand / elig
+    t = 0.005 * theta * np.arange(1, nsteps // theta + 1)
+    theory = np.exp(-k * n_mean * t)
+    assert k * n_mean * t[-1] <= 1.1
+    for q in (19, 39, 59):  # t = 1, 2, 3
+        se = fr[:, q].std(ddof=1) / 2.0
+        assert abs(fr[:, q].mean() - theory[q]) < max(3 * se, 0.02), (q, fr[:, q].mean(), theory[q])
+    assert 1.0 < n_mean < 8.0 and fr[:, -1].mean() < 0.5
