@@ -123,6 +123,18 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def aggregate_throughput(ms_local: float, units_per_rank: int, world: int, dist=None,
+                         device="cpu"):
+    """Whole-job throughput of independent replicas (weak scaling): the
+    slowest rank's time (max over ranks) and all ranks' units over it."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * units_per_rank / (ms_max * 1e-3)
+
+
 def algorithmic_bytes_per_particle_step(mean_bonds_per_bead: float) -> float:
     """Step kernel's share of the per-particle-step traffic: FP64 x and v read
     and written (96 B) plus the adjacency entries read (4 B per bond end)."""
@@ -403,11 +415,8 @@ def main():
     g.sync()
     st1 = g.stats()
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = world * inp.n * THETA * args.steps / (ms_max * 1e-3)
+    ms_max, value = aggregate_throughput(ms, inp.n * THETA * args.steps, world,
+                                         dist if world > 1 else None, dev)
     launches = int(st1["kernel_launches"] - st0["kernel_launches"])
     rebins = int(st1["rebins"] - st0["rebins"])
 
