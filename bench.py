@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--ensemble-steps", type=int, default=20,
                     help="timed reaction intervals of the ensemble measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--skin", type=float, default=0.0,
+                    help="Verlet skin to use (default: the library's autotuner picks it)")
     ap.add_argument("--serving-arrivals", type=int, default=64)
     ap.add_argument("--serving-step-scale", type=float, default=0.1)
     return ap.parse_args()
@@ -379,9 +381,12 @@ def main():
     sch = scheme()
     # the library's autotuner picks the Verlet skin for this workload (timed
     # on temporary copies of the system, outside the timed region)
-    skin, skin_ms = P.prx_autotune_skin(
-        P.make_desc(inp.n, inp.L, adj_cap=FUNC, seed=synth.BASE_SEED + rank), inp.x, inp.v,
-        inp.type, inp.state, P.make_reaction(**sch), steps=100, skins=SKINS)
+    if args.skin > 0:
+        skin, skin_ms = args.skin, {}
+    else:
+        skin, skin_ms = P.prx_autotune_skin(
+            P.make_desc(inp.n, inp.L, adj_cap=FUNC, seed=synth.BASE_SEED + rank), inp.x, inp.v,
+            inp.type, inp.state, P.make_reaction(**sch), steps=100, skins=SKINS)
     desc = P.make_desc(inp.n, inp.L, adj_cap=FUNC, seed=synth.BASE_SEED + rank, skin=skin)
     g = P.System(desc, inp.x, inp.v, inp.type, inp.state, stream=stream.cuda_stream)
     g.set_reaction(P.make_reaction(**sch))
