@@ -160,22 +160,17 @@ __device__ __forceinline__ void step_epilogue(const Sys& S, int ph, unsigned lon
   }
 }
 
-// k-th Verlet-list entry of slot i (relative offset mod n).  Entries past a
-// slot's count hold stale offsets of some earlier list: still valid slots.
+// k-th Verlet-list entry of slot i: the neighbour's slot (16-bit for systems
+// of at most 65,535 particles).  Entries past a slot's count hold stale
+// slots of some earlier list: still valid slots.
 template <bool NL16>
-__device__ __forceinline__ int nl_raw(const Sys& S, int k, uint32_t i) {
-  if constexpr (NL16) return __ldg(((const int16_t*)S.nl) + (size_t)k * S.n + i);
-  else return __ldg(((const int32_t*)S.nl) + (size_t)k * S.n + i);
-}
-__device__ __forceinline__ uint32_t nl_slot(const Sys& S, int r, uint32_t i) {
-  int j = (int)i + r;
-  if (j < 0) j += (int)S.n;
-  else if (j >= (int)S.n) j -= (int)S.n;
-  return (uint32_t)j;
+__device__ __forceinline__ uint32_t nl_raw(const Sys& S, int k, uint32_t i) {
+  if constexpr (NL16) return __ldg(((const uint16_t*)S.nl) + (size_t)k * S.n + i);
+  else return __ldg(((const uint32_t*)S.nl) + (size_t)k * S.n + i);
 }
 template <bool NL16>
 __device__ __forceinline__ uint32_t nl_get(const Sys& S, int k, uint32_t i) {
-  return nl_slot(S, nl_raw<NL16>(S, k, i), i);
+  return nl_raw<NL16>(S, k, i);
 }
 
 // Physical minimum-image displacement x_j - x_i: exact in fixed point,
@@ -253,7 +248,7 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
   if (i < S.n) {
     // every load that does not depend on another goes out first
     const int cnt = __ldg(S.nn + i);
-    int rn[4];
+    uint32_t rn[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) rn[u] = nl_raw<NL16>(S, u, i);
     const uint4 pi = __ldg(P + i);
@@ -267,9 +262,9 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
     for (int k = 0; k < cnt; k += 4) {
       uint4 pj[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) pj[u] = __ldg(P + (k + u < cnt ? nl_slot(S, rn[u], i) : i));
+      for (int u = 0; u < 4; ++u) pj[u] = __ldg(P + (k + u < cnt ? rn[u] : i));
 #pragma unroll
-      for (int u = 0; u < 4; ++u) rn[u] = k + 4 + u < S.list_cap ? nl_raw<NL16>(S, k + 4 + u, i) : 0;
+      for (int u = 0; u < 4; ++u) rn[u] = k + 4 + u < S.list_cap ? nl_raw<NL16>(S, k + 4 + u, i) : 0u;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         float dx, dy, dz;
@@ -824,9 +819,8 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
     int cnt = 0;
     bool overflow = false;
     const int cap = S.list_cap;
-    const int n = (int)S.n, half = n / 2;
     unsigned char* wp = (unsigned char*)S.nl + (size_t)i * (NL16 ? 2 : 4);
-    const size_t stride = (size_t)n * (NL16 ? 2 : 4);
+    const size_t stride = (size_t)S.n * (NL16 ? 2 : 4);
     const float sx = S.scale[0], sy = S.scale[1], sz = S.scale[2], rv2 = S.rv2_build;
     for (int c0 = 0; c0 < TOT; c0 += CAP) {
       const int cn = min(CAP, TOT - c0);
@@ -861,17 +855,10 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
             const float dy = __int2float_rn(pdiff(q.y, pi.y)) * sy;
             const float dz = __int2float_rn(pdiff(q.z, pi.z)) * sz;
             const bool hit = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < rv2 && q.w != i;
-            int r = (int)q.w - (int)i;
-            r = r > half ? r - n : r;
-            r = r < -half ? r + n : r;
             const bool put = hit && cnt < cap;
-            if constexpr (NL16) {
-              overflow |= hit && (cnt >= cap || r > 32767 || r < -32767);
-              st_global_pred_u16(wp, (uint16_t)(int16_t)r, put);
-            } else {
-              overflow |= hit && cnt >= cap;
-              st_global_pred_u32(wp, (uint32_t)r, put);
-            }
+            overflow |= hit && cnt >= cap;
+            if constexpr (NL16) st_global_pred_u16(wp, (uint16_t)q.w, put);
+            else st_global_pred_u32(wp, q.w, put);
             wp += put ? stride : 0;
             cnt += put ? 1 : 0;
           }

@@ -212,16 +212,13 @@ int setup_grid(prx_system* sys, double rc) {
                                        ((size_t)ncell + SCAN_TILE - 1) / SCAN_TILE) + 1;
   if ((rc2 = dalloc(sys, sys->grid_allocs, &S.blk_count, nblk))) return rc2;
   if ((rc2 = dalloc(sys, sys->grid_allocs, &S.blk_off, nblk))) return rc2;
-  // Verlet list: capacity from the mean count at this density, 16-bit
-  // relative entries when every neighbour is within 32767 slots (mod n)
+  // Verlet list: capacity from the mean count at this density; entries are
+  // the neighbours' slots, 16-bit up to 65,535 particles
   const double V = sys->d.box[0] * sys->d.box[1] * sys->d.box[2];
   const double rho = (double)S.n / V;
   const double mean_nb = rho * 4.0 / 3.0 * M_PI * rv * rv * rv;
   S.list_cap = std::max(32, std::min(255, (int)std::ceil(2.5 * mean_nb + 16.0)));
-  // 16-bit relative entries only when every offset (mod n) fits: with
-  // periodic wraps in y and z a neighbour can lie up to two cell layers away
-  // in slot order, so larger systems take 32-bit entries (measured: no cost)
-  S.nl16 = S.n < 32768 ? 1 : 0;
+  S.nl16 = S.n <= 65535 ? 1 : 0;
   {
     void* nl = nullptr;
     if ((rc2 = dalloc(sys, sys->grid_allocs, (uint8_t**)&nl,
@@ -639,8 +636,8 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
       if ((rc = up(S.nn, slot_nn, n))) return bail(rc);
       const size_t ne = (size_t)S.list_cap * n;
       if (S.nl16) {
-        std::vector<int16_t> v(ne);
-        for (size_t q = 0; q < ne; ++q) v[q] = (int16_t)slot_nl[q];
+        std::vector<uint16_t> v(ne);
+        for (size_t q = 0; q < ne; ++q) v[q] = (uint16_t)slot_nl[q];
         if ((rc = up(S.nl, v.data(), 2 * ne))) return bail(rc);
       } else {
         if ((rc = up(S.nl, slot_nl, 4 * ne))) return bail(rc);
@@ -810,7 +807,7 @@ int prx_estimate_bytes(const prx_system_desc* desc, uint64_t* bytes) {
   const double V = desc->box[0] * desc->box[1] * desc->box[2];
   const double mean_nb = (double)n / V * 4.0 / 3.0 * M_PI * rv * rv * rv;
   const uint64_t list_cap = (uint64_t)std::max(32, std::min(255, (int)std::ceil(2.5 * mean_nb + 16.0)));
-  const uint64_t nl_bytes = n < 32768 ? 2 : 4;  // as setup_grid
+  const uint64_t nl_bytes = n <= 65535 ? 2 : 4;  // as setup_grid
   const uint64_t per_set = n * (6 * 8 + 4 + 3 + 4 * cap);
   const uint64_t nblk = std::max<uint64_t>(n / RX_THREADS + 1, ncell / SCAN_TILE + 1) + 1;
   const uint64_t allocs = 40;  // separate cudaMalloc calls, each rounded up
@@ -1185,7 +1182,7 @@ int prx_save(prx_system* sys, const char* path) {
     CK(cudaMemcpy(cs.data(), sys->S.cell_start, 4 * cs.size(), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(nn.data(), sys->S.nn, n, cudaMemcpyDeviceToHost));
     if (sys->S.nl16) {
-      std::vector<int16_t> v((size_t)lcap * n);
+      std::vector<uint16_t> v((size_t)lcap * n);
       CK(cudaMemcpy(v.data(), sys->S.nl, 2 * v.size(), cudaMemcpyDeviceToHost));
       for (size_t q = 0; q < v.size(); ++q) nl[q] = v[q];
     } else {

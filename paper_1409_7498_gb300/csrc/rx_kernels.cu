@@ -60,13 +60,8 @@ __device__ __forceinline__ long long block_sum_ll(long long v) {
 
 template <bool NL16>
 __device__ __forceinline__ uint32_t nl_get_rx(const Sys& S, int k, uint32_t i) {
-  int r;
-  if constexpr (NL16) r = ((const int16_t*)S.nl)[(size_t)k * S.n + i];
-  else r = ((const int32_t*)S.nl)[(size_t)k * S.n + i];
-  int j = (int)i + r;
-  if (j < 0) j += (int)S.n;
-  else if (j >= (int)S.n) j -= (int)S.n;
-  return (uint32_t)j;
+  if constexpr (NL16) return ((const uint16_t*)S.nl)[(size_t)k * S.n + i];
+  else return ((const uint32_t*)S.nl)[(size_t)k * S.n + i];
 }
 
 // Work list of the eligible A's (their order does not matter: each A's
