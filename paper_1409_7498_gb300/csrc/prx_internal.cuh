@@ -89,6 +89,7 @@ struct RxParams {
   double p;         // k dt Theta
   double rr2;       // r_react^2 (exact test)
   float rr2_pre;    // (r_react + margin)^2 (FP32 prefilter, always conservative)
+  float rr2_in;     // r_react^2 minus twice the FP32 error bound: inside for sure
   uint32_t style;
   int32_t rule;     // PRX_SELECT_RANDOM or PRX_SELECT_NEAREST
   uint8_t maxval[PRX_MAX_TYPES];

@@ -866,6 +866,15 @@ int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx) {
   R.p = rx->k * sys->d.dt * (double)rx->theta;
   R.rr2 = rx->r_react * rx->r_react;
   R.rr2_pre = (float)((rx->r_react + 1e-3) * (rx->r_react + 1e-3));
+  {
+    // bound on |r^2(FP32, fixed point) - r^2(FP64)| near the cutoff: the
+    // fixed-point positions are within 3 units of L / 2^32, the conversion
+    // and FP32 arithmetic within 2e-7 (relative), for |d| ~ r_react <= 2
+    const double u = std::max(sys->d.box[0], std::max(sys->d.box[1], sys->d.box[2])) / 4294967296.0;
+    const double margin = 2.0 * std::sqrt(3.0) * rx->r_react * (6.0 * u + 2e-7 * rx->r_react) +
+                          4e-7 * R.rr2 + 1e-9;
+    R.rr2_in = std::nextafter((float)std::max(0.0, R.rr2 - 2.0 * margin), 0.0f);
+  }
   R.style = (uint32_t)rx->bond_style;
   R.rule = rx->selection;
   for (int t = 0; t < PRX_MAX_TYPES; ++t) R.maxval[t] = rx->max_valence[t];

@@ -185,14 +185,20 @@ __device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long l
         const float ex = __int2float_rn(pdiff(pj.x, pi.x)) * S.scale[0];
         const float ey = __int2float_rn(pdiff(pj.y, pi.y)) * S.scale[1];
         const float ez = __int2float_rn(pdiff(pj.z, pi.z)) * S.scale[2];
-        if (!(fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < R.rr2_pre)) continue;
+        const float r2f = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+        if (!(r2f < R.rr2_pre)) continue;
         // exact test, Table I step 1: d = x_T - x_A under the minimum image,
-        // r^2 = fma(dz, dz, fma(dy, dy, dx dx)), strict r^2 < r_react^2
-        const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
-        const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
-        const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
-        const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
-        if (!(r2 < R.rr2)) continue;
+        // r^2 = fma(dz, dz, fma(dy, dy, dx dx)), strict r^2 < r_react^2.  The
+        // FP32 value from the fixed-point positions is within a known bound
+        // of it, so below rr2_in (the cutoff minus twice that bound) the FP64
+        // test cannot fail; only pairs near the cutoff take it.
+        if (!(r2f < R.rr2_in)) {
+          const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
+          const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
+          const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
+          const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
+          if (!(r2 < R.rr2)) continue;
+        }
         bool bonded = false;
         for (uint32_t b = 0; b < nb; ++b) bonded |= (B.adj[(size_t)i * S.cap + b] & SLOT_MASK) == j;
         if (bonded) continue;
