@@ -461,11 +461,19 @@ __device__ __forceinline__ void obs_hist_body(const Sys& S, const Blk blk, long 
   __shared__ int32_t h[PRX_MAX_TYPES * PRX_MAX_STATES];
   for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x) h[k] = 0;
   __syncthreads();
-  const uint32_t i = blk.b * blockDim.x + threadIdx.x;
-  if (i < S.n) {
-    const uint32_t t = B.type[i];
-    const int s = B.state[i];
-    if (t < PRX_MAX_TYPES && s >= 0 && s < PRX_MAX_STATES) atomicAdd(&h[t * PRX_MAX_STATES + s], 1);
+  // Block-strided over the slots; within a warp, lanes with the same
+  // (type, state) bin are counted by one shared atomic of their leader.
+  const int lane = threadIdx.x & 31;
+  for (uint32_t base = blk.b * blockDim.x; base < S.n; base += blk.nb * blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    int key = -1;
+    if (i < S.n) {
+      const uint32_t t = B.type[i];
+      const int s = B.state[i];
+      if (t < PRX_MAX_TYPES && s >= 0 && s < PRX_MAX_STATES) key = (int)t * PRX_MAX_STATES + s;
+    }
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, key);
+    if (key >= 0 && lane == __ffs(grp) - 1) atomicAdd(&h[key], __popc(grp));
   }
   __syncthreads();
   const unsigned long long slot = record ? ctl->hist_count % S.hist_cap : S.hist_cap;
@@ -620,7 +628,7 @@ void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
   k_rx_apply<<<g, RX_THREADS, 0, st>>>(S, step_arg);
   H("rx_apply", 1);
   H("obs_hist", 0);
-  k_obs_hist<<<g, RX_THREADS, 0, st>>>(S, step_arg, 1);
+  k_obs_hist<<<gf, RX_THREADS, 0, st>>>(S, step_arg, 1);
   H("obs_hist", 1);
 }
 
