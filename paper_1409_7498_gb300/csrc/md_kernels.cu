@@ -701,10 +701,11 @@ __global__ void kb_rebin_remap(const Sys* __restrict__ T, const BlkMap* __restri
 // Verlet-list build.  One block per tile of TY consecutive cell rows (cy0 ..
 // cy0+TY-1 at one cz); threads = the tile's particles, contiguous in slot
 // order (in passes of blockDim when a tile is longer).  All (TY+2) x 3
-// neighbour rows are staged in shared memory (one pass in the common case),
-// each row extended by one periodic image cell at both ends, so every
-// particle's 3 x 3 x 3 cell neighbourhood is 9 contiguous ranges.  A pair
-// enters the list when its fixed-point distance is below r_c + skin.
+// neighbour rows are staged in shared memory as FP32 coordinates in the
+// tile's frame (one pass in the common case), each row extended by one
+// periodic image cell at both ends, so every particle's 3 x 3 x 3 cell
+// neighbourhood is 9 contiguous ranges.  A pair enters the list when its
+// FP32 distance is below r_c + skin (widened by the rounding bound).
 // ---------------------------------------------------------------------------
 // 16-byte copy global -> shared that does not wait for the data (cp.async,
 // L2 only); cp_async_wait_all() waits for every copy the thread issued.
@@ -714,18 +715,6 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Stores that happen only when `pred` holds, as one predicated instruction.
-__device__ __forceinline__ void st_global_pred_u16(void* p, uint16_t v, bool pred) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.global.u16 [%0], %1;\n\t}"
-      ::"l"(p), "h"(v), "r"((int)pred) : "memory");
-}
-__device__ __forceinline__ void st_global_pred_u32(void* p, uint32_t v, bool pred) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.global.u32 [%0], %1;\n\t}"
-      ::"l"(p), "r"(v), "r"((int)pred) : "memory");
-}
-
 struct RowInfo {
   int base;        // first staged index of the row
   int padL;        // particles of the left image cell (cell nx-1)
@@ -733,14 +722,74 @@ struct RowInfo {
   int tot;         // padL + rowcount + padR
   int row_lo;      // first slot of the row
   int left_start;  // first slot of cell nx-1
-  int pad0, pad1;
+  int c1;          // first slot of cell 1 (end of cell 0)
+  uint32_t yref;   // fixed-point lower edge of the (wrapped) row in y
+  uint32_t zref;   // and in z
+  float yoff;      // that edge's offset from the tile's lower edge, unwrapped
+  float zoff;
+  int pad;
 };
 constexpr int TILE_ROWS_MAX = 18;  // (TY + 2) x 3 for TY <= 4
+
+// FP32 coordinates of a staged particle in the tile's frame: y and z relative
+// to the tile's lower cell edges (each row's images unwrapped), x in [0, L)
+// with the left and right image cells shifted by -L and +L.  A slot keyed to
+// cell 0 (nx-1) whose position rounds to the far end of the box (possible by
+// one rounding step after a restore) is taken back to the near side.  The
+// values carry ~1e-5 sigma of rounding; the list radius has a margin for it.
+__device__ __forceinline__ float4 build_coords(const uint4 p, const RowInfo& r, int kr,
+                                               uint32_t slot, float sx, float sy, float sz,
+                                               float Lx) {
+  float xf = __uint2float_rn(p.x) * sx;
+  if (slot < (uint32_t)r.c1 && p.x >= 0x80000000u) xf -= Lx;
+  if (slot >= (uint32_t)r.left_start && p.x < 0x80000000u) xf += Lx;
+  if (kr < r.padL) xf -= Lx;
+  else if (kr >= r.padL + r.rowcount) xf += Lx;
+  const float yf = fmaf(__int2float_rn(pdiff(p.y, r.yref)), sy, r.yoff);
+  const float zf = fmaf(__int2float_rn(pdiff(p.z, r.zref)), sz, r.zoff);
+  return make_float4(xf, yf, zf, __uint_as_float(slot));
+}
+
+// One candidate: hit = r2 < rv2 and not the particle itself; a hit is
+// written to row `cnt` of the slot's column while cnt < cap, and cnt counts
+// every hit (cnt > cap afterwards means the list overflowed).  Predicated
+// PTX, so that the warp does not diverge on the (frequent) hits.
+template <bool NL16>
+__device__ __forceinline__ void list_candidate(unsigned char* col, uint32_t stride, float r2,
+                                               float rv2, uint32_t qslot, uint32_t i, int cap,
+                                               int& cnt) {
+  if constexpr (NL16) {
+    asm volatile(
+        "{\n\t.reg .pred h, w;\n\t.reg .u64 a;\n\t"
+        "setp.lt.f32 h, %1, %2;\n\t"
+        "setp.ne.and.u32 h, %3, %4, h;\n\t"
+        "setp.lt.and.s32 w, %0, %5, h;\n\t"
+        "mad.wide.u32 a, %0, %6, %7;\n\t"
+        "@w st.global.u16 [a], %8;\n\t"
+        "@h add.s32 %0, %0, 1;\n\t}"
+        : "+r"(cnt)
+        : "f"(r2), "f"(rv2), "r"(qslot), "r"(i), "r"(cap), "r"(stride), "l"(col),
+          "h"((uint16_t)qslot)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred h, w;\n\t.reg .u64 a;\n\t"
+        "setp.lt.f32 h, %1, %2;\n\t"
+        "setp.ne.and.u32 h, %3, %4, h;\n\t"
+        "setp.lt.and.s32 w, %0, %5, h;\n\t"
+        "mad.wide.u32 a, %0, %6, %7;\n\t"
+        "@w st.global.u32 [a], %3;\n\t"
+        "@h add.s32 %0, %0, 1;\n\t}"
+        : "+r"(cnt)
+        : "f"(r2), "f"(rv2), "r"(qslot), "r"(i), "r"(cap), "r"(stride), "l"(col)
+        : "memory");
+  }
+}
 
 template <bool NL16>
 __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, unsigned char* smem) {
   const int CAP = S.tile_cap;
-  uint4* sX = reinterpret_cast<uint4*>(smem);
+  float4* sX = reinterpret_cast<float4*>(smem);
   RowInfo* ri = reinterpret_cast<RowInfo*>(smem + 16 * (size_t)CAP);
   uint32_t* sCS = reinterpret_cast<uint32_t*>(ri + TILE_ROWS_MAX);
   __shared__ int sTOT;
@@ -767,14 +816,22 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
   __syncthreads();
   if (threadIdx.x < R) {
     const uint32_t* cs = sCS + threadIdx.x * (nx + 1);
+    const int dzi = threadIdx.x / RY, yi = threadIdx.x - dzi * RY;
+    const int uy = cy0 - 1 + yi, uz = cz - 1 + dzi;  // unwrapped row indices
+    const int qy = wrap_cell(uy, ny), qz = wrap_cell(uz, nz);
     RowInfo r;
     r.padL = (int)(cs[nx] - cs[nx - 1]);
     r.rowcount = (int)(cs[nx] - cs[0]);
     r.tot = r.padL + r.rowcount + (int)(cs[1] - cs[0]);
     r.row_lo = (int)cs[0];
     r.left_start = (int)cs[nx - 1];
+    r.c1 = (int)cs[1];
+    r.yref = (uint32_t)(((unsigned long long)qy << 32) / (unsigned)ny);
+    r.zref = (uint32_t)(((unsigned long long)qz << 32) / (unsigned)nz);
+    r.yoff = (float)((double)(uy - cy0) * (S.L[1] / ny));
+    r.zoff = (float)((double)(uz - cz) * (S.L[2] / nz));
     r.base = 0;
-    r.pad0 = r.pad1 = 0;
+    r.pad = 0;
     ri[threadIdx.x] = r;
   }
   __syncthreads();
@@ -788,6 +845,8 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
   }
   __syncthreads();
   const int TOT = sTOT;
+  const float sx = S.scale[0], sy = S.scale[1], sz = S.scale[2], rv2 = S.rv2_build;
+  const float Lx = (float)S.L[0];
 
   for (uint32_t base = rs; base < re; base += blockDim.x) {
     const uint32_t i = base + threadIdx.x;
@@ -813,35 +872,46 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
       const int hi = r.base + (cx + 2 > nx ? r.tot : r.padL + (int)cs[cx + 2] - r.row_lo);
       win[w] = (uint32_t)lo | ((uint32_t)hi << 16);
     }
-    // Appends are branch-free: every candidate computes its entry, and a
-    // predicated store writes it only on a hit, so the warp does not
-    // diverge on the (frequent) hits.  `wp` walks the slot's column.
+    float4 fi;
+    {
+      const RowInfo& r = ri[RY + yrel + 1];
+      fi = build_coords(pi, r, r.padL + ((int)i - r.row_lo), i, sx, sy, sz, Lx);
+    }
     int cnt = 0;
-    bool overflow = false;
     const int cap = S.list_cap;
-    unsigned char* wp = (unsigned char*)S.nl + (size_t)i * (NL16 ? 2 : 4);
-    const size_t stride = (size_t)S.n * (NL16 ? 2 : 4);
-    const float sx = S.scale[0], sy = S.scale[1], sz = S.scale[2], rv2 = S.rv2_build;
+    unsigned char* col = (unsigned char*)S.nl + (size_t)i * (NL16 ? 2 : 4);
+    const uint32_t stride = S.n * (NL16 ? 2u : 4u);
     for (int c0 = 0; c0 < TOT; c0 += CAP) {
       const int cn = min(CAP, TOT - c0);
       __syncthreads();
-      // every copy of a thread in flight at once (cp.async), then the slot
-      // goes into .w once the copies have landed
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int sr = warp; sr < R; sr += nwarps) {
-          const RowInfo r = ri[sr];
-          const int k0 = max(r.base, c0), k1 = min(r.base + r.tot, c0 + cn);
-          for (int ent = k0 + lane; ent < k1; ent += 32) {
-            const int kr = ent - r.base;
-            int slot;
-            if (kr < r.padL) slot = r.left_start + kr;
-            else if (kr < r.padL + r.rowcount) slot = r.row_lo + (kr - r.padL);
-            else slot = r.row_lo + (kr - r.padL - r.rowcount);
-            if (pass == 0) cp_async16(&sX[ent - c0], P + slot);
-            else sX[ent - c0].w = (uint32_t)slot;
-          }
+      // stage, one warp per row: raw copies in flight at once (cp.async),
+      // then each lane turns the entries it copied into tile-frame FP32
+      // coordinates in place (the same warp/lane mapping, so no block barrier)
+      for (int sr = warp; sr < R; sr += nwarps) {
+        const RowInfo& r = ri[sr];
+        const int k0 = max(r.base, c0), k1 = min(r.base + r.tot, c0 + cn);
+        const int padL = r.padL, rc = r.rowcount, lo = r.row_lo, ls = r.left_start, b = r.base;
+        for (int ent = k0 + lane; ent < k1; ent += 32) {
+          const int kr = ent - b;
+          const int slot = kr < padL ? ls + kr : (kr < padL + rc ? lo + kr - padL : lo + kr - padL - rc);
+          cp_async16(&sX[ent - c0], P + slot);
         }
-        if (pass == 0) cp_async_wait_all();
+      }
+      cp_async_wait_all();
+      __syncwarp();
+      for (int sr = warp; sr < R; sr += nwarps) {
+        const RowInfo r = ri[sr];
+        const int k0 = max(r.base, c0), k1 = min(r.base + r.tot, c0 + cn);
+        for (int ent = k0 + lane; ent < k1; ent += 32) {
+          const int kr = ent - r.base;
+          const int slot = kr < r.padL ? r.left_start + kr
+                                       : r.row_lo + (kr < r.padL + r.rowcount ? kr - r.padL
+                                                                              : kr - r.padL - r.rowcount);
+          const float4 raw = sX[ent - c0];
+          const uint4 p = make_uint4(__float_as_uint(raw.x), __float_as_uint(raw.y),
+                                     __float_as_uint(raw.z), 0u);
+          sX[ent - c0] = build_coords(p, r, kr, (uint32_t)slot, sx, sy, sz, Lx);
+        }
       }
       __syncthreads();
       if (act) {
@@ -849,25 +919,19 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
         for (int w = 0; w < 9; ++w) {
           const int lo = max((int)(win[w] & 0xFFFFu), c0) - c0;
           const int hi = min((int)(win[w] >> 16), c0 + cn) - c0;
+#pragma unroll 1
           for (int k = lo; k < hi; ++k) {
-            const uint4 q = sX[k];
-            const float dx = __int2float_rn(pdiff(q.x, pi.x)) * sx;
-            const float dy = __int2float_rn(pdiff(q.y, pi.y)) * sy;
-            const float dz = __int2float_rn(pdiff(q.z, pi.z)) * sz;
-            const bool hit = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < rv2 && q.w != i;
-            const bool put = hit && cnt < cap;
-            overflow |= hit && cnt >= cap;
-            if constexpr (NL16) st_global_pred_u16(wp, (uint16_t)q.w, put);
-            else st_global_pred_u32(wp, q.w, put);
-            wp += put ? stride : 0;
-            cnt += put ? 1 : 0;
+            const float4 q = sX[k];
+            const float dx = q.x - fi.x, dy = q.y - fi.y, dz = q.z - fi.z;
+            list_candidate<NL16>(col, stride, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), rv2,
+                                 __float_as_uint(q.w), i, cap, cnt);
           }
         }
       }
     }
     if (act) {
-      S.nn[i] = (uint8_t)cnt;
-      if (overflow) set_status(ctl, PRX_ECAPACITY);
+      S.nn[i] = (uint8_t)min(cnt, cap);
+      if (cnt > cap) set_status(ctl, PRX_ECAPACITY);
     }
   }
   // the last warp of the system's tiles flips the SoA set and clears the

@@ -200,7 +200,13 @@ int setup_grid(prx_system* sys, double rc) {
   const double dmax = 0.5 * skin - 2.0 * std::sqrt(3.0) * wmax - 1e-6;
   if (!(dmax > 0.0)) return fail(sys, PRX_EINVAL, "skin too small for the displacement trigger");
   S.disp2_max = (float)(dmax * dmax);
-  S.rv2_build = (float)((rv * (1.0 + 1e-5)) * (rv * (1.0 + 1e-5)));
+  // the list build compares FP32 tile-frame coordinates (~2e-7 L of rounding
+  // per coordinate): its radius is widened by more than that error
+  {
+    const double Lmax = std::max(sys->d.box[0], std::max(sys->d.box[1], sys->d.box[2]));
+    const double rvb = rv * (1.0 + 1e-5) + 1e-6 * Lmax;
+    S.rv2_build = (float)(rvb * rvb);
+  }
   S.ncell = (int)ncell;
   sys->grid_rcut = rc;
   free_list(sys->grid_allocs);
@@ -229,12 +235,13 @@ int setup_grid(prx_system* sys, double rc) {
   if ((rc2 = dalloc(sys, sys->grid_allocs, &S.nn, (size_t)S.n))) return rc2;
   {
     // list-build tiling: the largest tile of 1..4 cell rows whose particles
-    // fit 256 threads; staging buffer sized for all neighbour rows at once
+    // fit about two passes of 256 threads (fewer restaged neighbour rows per
+    // particle); staging buffer sized for all neighbour rows at once
     const double per_row = (double)S.n / ((double)S.nc[1] * S.nc[2]);
     const double per_cell = (double)S.n / (double)ncell;
     int ty = 1;
     for (int c = 2; c <= 4; ++c)
-      if (c * per_row + 3.0 * std::sqrt(c * per_row) + 16.0 <= 256.0) ty = c;
+      if (c * per_row + 3.0 * std::sqrt(c * per_row) + 16.0 <= 640.0) ty = c;
     ty = std::max(1, std::min(ty, S.nc[1]));
     S.tile_y = ty;
     S.tiles_y = (S.nc[1] + ty - 1) / ty;
