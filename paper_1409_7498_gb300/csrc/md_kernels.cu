@@ -627,7 +627,8 @@ __global__ void kb_rebin_cellsort(const Sys* __restrict__ T, const BlkMap* __res
 
 // New slot s takes old slot tmp[s]: copies every per-particle array into the
 // other set and writes the fixed-point position with a fresh displacement
-// reference.
+// reference; tmp[s] then receives the cell the sort put the slot in (read by
+// the list build).
 __device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk, bool wrap) {
   Ctl* ctl = S.ctl;
   const int set = ctl->set;
@@ -665,6 +666,7 @@ __device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk, 
   const uint32_t Y = periodic_fx(y, S.Lfx[1], S.M64[1]);
   const uint32_t Z = periodic_fx(z, S.Lfx[2], S.M64[2]);
   P[s] = make_uint4(X, Y, Z, coarse_ref(X, Y, Z, S.wshift));
+  S.tmp[s] = S.key[o];
 }
 
 __global__ void k_rebin_permute(Sys S, int wrap) {
@@ -848,13 +850,51 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
   const float sx = S.scale[0], sy = S.scale[1], sz = S.scale[2], rv2 = S.rv2_build;
   const float Lx = (float)S.L[0];
 
+  // Stages entries [c0, c0 + cn) of the neighbour rows, one warp per row:
+  // raw copies in flight at once (cp.async), then each lane turns the
+  // entries it copied into tile-frame FP32 coordinates in place (the same
+  // warp/lane mapping, so no block barrier in between).
+  auto stage = [&](int c0, int cn) {
+    for (int sr = warp; sr < R; sr += nwarps) {
+      const RowInfo& r = ri[sr];
+      const int k0 = max(r.base, c0), k1 = min(r.base + r.tot, c0 + cn);
+      const int padL = r.padL, rc = r.rowcount, lo = r.row_lo, ls = r.left_start, b = r.base;
+      for (int ent = k0 + lane; ent < k1; ent += 32) {
+        const int kr = ent - b;
+        const int slot = kr < padL ? ls + kr : (kr < padL + rc ? lo + kr - padL : lo + kr - padL - rc);
+        cp_async16(&sX[ent - c0], P + slot);
+      }
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    for (int sr = warp; sr < R; sr += nwarps) {
+      const RowInfo r = ri[sr];
+      const int k0 = max(r.base, c0), k1 = min(r.base + r.tot, c0 + cn);
+      for (int ent = k0 + lane; ent < k1; ent += 32) {
+        const int kr = ent - r.base;
+        const int slot = kr < r.padL ? r.left_start + kr
+                                     : r.row_lo + (kr < r.padL + r.rowcount ? kr - r.padL
+                                                                            : kr - r.padL - r.rowcount);
+        const float4 raw = sX[ent - c0];
+        const uint4 p = make_uint4(__float_as_uint(raw.x), __float_as_uint(raw.y),
+                                   __float_as_uint(raw.z), 0u);
+        sX[ent - c0] = build_coords(p, r, kr, (uint32_t)slot, sx, sy, sz, Lx);
+      }
+    }
+  };
+  const bool one = TOT <= CAP;  // the common case: every row staged once
+  if (one) {
+    stage(0, TOT);
+    __syncthreads();
+  }
+
   for (uint32_t base = rs; base < re; base += blockDim.x) {
     const uint32_t i = base + threadIdx.x;
     const bool act = i < re;
     const uint4 pi = act ? P[i] : make_uint4(0u, 0u, 0u, 0u);
     // the cell the sort put this slot in (not the one its current position
     // maps to: after a checkpoint restore the two can differ by one)
-    const uint32_t kc = act ? S.key[S.tmp[i]] : (uint32_t)((cz * ny + cy0) * nx);
+    const uint32_t kc = act ? S.tmp[i] : (uint32_t)((cz * ny + cy0) * nx);
     int cx = (int)(kc % (uint32_t)nx);
     int yrel = (int)((kc / (uint32_t)nx) % (uint32_t)ny) - cy0;
     if (yrel < 0 || yrel >= TYb) {  // cannot happen for a consistent sort
@@ -883,37 +923,11 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
     const uint32_t stride = S.n * (NL16 ? 2u : 4u);
     for (int c0 = 0; c0 < TOT; c0 += CAP) {
       const int cn = min(CAP, TOT - c0);
-      __syncthreads();
-      // stage, one warp per row: raw copies in flight at once (cp.async),
-      // then each lane turns the entries it copied into tile-frame FP32
-      // coordinates in place (the same warp/lane mapping, so no block barrier)
-      for (int sr = warp; sr < R; sr += nwarps) {
-        const RowInfo& r = ri[sr];
-        const int k0 = max(r.base, c0), k1 = min(r.base + r.tot, c0 + cn);
-        const int padL = r.padL, rc = r.rowcount, lo = r.row_lo, ls = r.left_start, b = r.base;
-        for (int ent = k0 + lane; ent < k1; ent += 32) {
-          const int kr = ent - b;
-          const int slot = kr < padL ? ls + kr : (kr < padL + rc ? lo + kr - padL : lo + kr - padL - rc);
-          cp_async16(&sX[ent - c0], P + slot);
-        }
+      if (!one) {  // neighbour rows longer than the buffer: staged per chunk
+        __syncthreads();
+        stage(c0, cn);
+        __syncthreads();
       }
-      cp_async_wait_all();
-      __syncwarp();
-      for (int sr = warp; sr < R; sr += nwarps) {
-        const RowInfo r = ri[sr];
-        const int k0 = max(r.base, c0), k1 = min(r.base + r.tot, c0 + cn);
-        for (int ent = k0 + lane; ent < k1; ent += 32) {
-          const int kr = ent - r.base;
-          const int slot = kr < r.padL ? r.left_start + kr
-                                       : r.row_lo + (kr < r.padL + r.rowcount ? kr - r.padL
-                                                                              : kr - r.padL - r.rowcount);
-          const float4 raw = sX[ent - c0];
-          const uint4 p = make_uint4(__float_as_uint(raw.x), __float_as_uint(raw.y),
-                                     __float_as_uint(raw.z), 0u);
-          sX[ent - c0] = build_coords(p, r, kr, (uint32_t)slot, sx, sy, sz, Lx);
-        }
-      }
-      __syncthreads();
       if (act) {
 #pragma unroll
         for (int w = 0; w < 9; ++w) {
