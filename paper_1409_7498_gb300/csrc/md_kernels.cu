@@ -12,6 +12,7 @@
 //   fields, so the FP64 pipe (about 70x slower than FP32 on this part) sees
 //   only the six DFMAs.
 #include <mutex>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "prx_internal.cuh"
@@ -231,7 +232,7 @@ __device__ __forceinline__ void integrate32(const Sys& S, Ctl* ctl, const SoA& B
 // ---------------------------------------------------------------------------
 // FP32 step kernel: one thread per slot, WCA over the Verlet list.
 // ---------------------------------------------------------------------------
-template <bool NL16, bool FORCES_ONLY>
+template <bool NL16, bool FORCES_ONLY, bool CUBIC>
 __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
                                              cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ unsigned int warps_left;
@@ -258,20 +259,36 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
     for (int b = 0; b < 4; ++b) arow[b] = b < (int)S.cap ? __ldg(B.adj + (size_t)i * S.cap + b) : 0u;
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
     // software pipeline over the list, four entries per stage: the next
-    // stage's list entries load while this stage's four gathers complete
+    // stage's list entries load while this stage's four gathers complete.
+    // The build pads every list to whole stages with the slot itself (r = 0,
+    // skipped).  In a cubic box displacements stay in position units and the
+    // neighbour force is scaled once at the end.
     for (int k = 0; k < cnt; k += 4) {
       uint4 pj[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) pj[u] = __ldg(P + (k + u < cnt ? rn[u] : i));
+      for (int u = 0; u < 4; ++u) pj[u] = __ldg(P + rn[u]);
 #pragma unroll
       for (int u = 0; u < 4; ++u) rn[u] = k + 4 + u < S.list_cap ? nl_raw<NL16>(S, k + 4 + u, i) : 0u;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        float dx, dy, dz;
-        disp(S, pj[u], pi, dx, dy, dz);
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        if (k + u < cnt && r2 < S.rc2f) wca32(S, dx, dy, dz, r2, fx, fy, fz, e);
+        if constexpr (CUBIC) {
+          const float ux = __int2float_rn(pdiff(pj[u].x, pi.x));
+          const float uy = __int2float_rn(pdiff(pj[u].y, pi.y));
+          const float uz = __int2float_rn(pdiff(pj[u].z, pi.z));
+          const float r2u = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
+          if (r2u > 0.f && r2u < S.rc2u) wca32(S, ux, uy, uz, r2u * S.s2f, fx, fy, fz, e);
+        } else {
+          float dx, dy, dz;
+          disp(S, pj[u], pi, dx, dy, dz);
+          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          if (r2 > 0.f && r2 < S.rc2f) wca32(S, dx, dy, dz, r2, fx, fy, fz, e);
+        }
       }
+    }
+    if constexpr (CUBIC) {
+      fx *= S.scale[0];
+      fy *= S.scale[0];
+      fz *= S.scale[0];
     }
     bool ok = true;
     for (int b = 0; b < (int)nb; ++b) {
@@ -298,10 +315,10 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
   if constexpr (!FORCES_ONLY) step_epilogue(S, ph, step, cond, use_cond, &warps_left, blk.nb);
 }
 
-template <bool NL16, bool FORCES_ONLY>
+template <bool NL16, bool FORCES_ONLY, bool CUBIC>
 __global__ void __launch_bounds__(256, 5)
     k_step_nl(Sys S, cudaGraphConditionalHandle cond, int use_cond) {
-  step_nl_body<NL16, FORCES_ONLY>(S, Blk{blockIdx.x, gridDim.x}, cond, use_cond);
+  step_nl_body<NL16, FORCES_ONLY, CUBIC>(S, Blk{blockIdx.x, gridDim.x}, cond, use_cond);
 }
 // Members of a batch may differ in list width: the branch is uniform per block.
 __global__ void __launch_bounds__(256, 4)
@@ -309,8 +326,13 @@ __global__ void __launch_bounds__(256, 4)
                cudaGraphConditionalHandle cond, int use_cond) {
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
-  if (S.nl16) step_nl_body<true, false>(S, Blk{m.b, m.nb}, cond, use_cond);
-  else step_nl_body<false, false>(S, Blk{m.b, m.nb}, cond, use_cond);
+  if (S.cubic) {
+    if (S.nl16) step_nl_body<true, false, true>(S, Blk{m.b, m.nb}, cond, use_cond);
+    else step_nl_body<false, false, true>(S, Blk{m.b, m.nb}, cond, use_cond);
+  } else {
+    if (S.nl16) step_nl_body<true, false, false>(S, Blk{m.b, m.nb}, cond, use_cond);
+    else step_nl_body<false, false, false>(S, Blk{m.b, m.nb}, cond, use_cond);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -944,8 +966,15 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
       }
     }
     if (act) {
-      S.nn[i] = (uint8_t)min(cnt, cap);
+      const int m = min(cnt, cap);
+      S.nn[i] = (uint8_t)m;
       if (cnt > cap) set_status(ctl, PRX_ECAPACITY);
+      // pad to a whole stage of four with the slot itself (the step kernel
+      // gathers four entries at a time; the self pair has r = 0 and no force)
+      for (int k = m; k < ((m + 3) & ~3); ++k) {
+        if constexpr (NL16) ((uint16_t*)S.nl)[(size_t)k * S.n + i] = (uint16_t)i;
+        else ((uint32_t*)S.nl)[(size_t)k * S.n + i] = i;
+      }
     }
   }
   // the last warp of the system's tiles flips the SoA set and clears the
@@ -986,12 +1015,18 @@ void launch_step(const Sys& S, cudaStream_t st, int fp64, int forces_only,
     if (!forces_only) k_integrate64<<<g, STEP_THREADS, 0, st>>>(S, h, use_cond);
   } else {
     const unsigned g = blocks_for(S.n, 256) > 0 ? blocks_for(S.n, 256) : 1;
-    if (S.nl16) {
-      if (forces_only) k_step_nl<true, true><<<g, 256, 0, st>>>(S, h, use_cond);
-      else k_step_nl<true, false><<<g, 256, 0, st>>>(S, h, use_cond);
+    auto K = [&](auto nl16, auto fo, auto cub) {
+      k_step_nl<decltype(nl16)::value, decltype(fo)::value, decltype(cub)::value>
+          <<<g, 256, 0, st>>>(S, h, use_cond);
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    if (S.cubic) {
+      if (S.nl16) forces_only ? K(T_{}, T_{}, T_{}) : K(T_{}, F_{}, T_{});
+      else forces_only ? K(F_{}, T_{}, T_{}) : K(F_{}, F_{}, T_{});
     } else {
-      if (forces_only) k_step_nl<false, true><<<g, 256, 0, st>>>(S, h, use_cond);
-      else k_step_nl<false, false><<<g, 256, 0, st>>>(S, h, use_cond);
+      if (S.nl16) forces_only ? K(T_{}, T_{}, F_{}) : K(T_{}, F_{}, F_{});
+      else forces_only ? K(F_{}, T_{}, F_{}) : K(F_{}, F_{}, F_{});
     }
   }
 }

@@ -131,6 +131,8 @@ struct Sys {
   int tile_y, tiles_y, tile_threads, tile_cap;
   // physics (FP32 and FP64 copies)
   float rc2f, sig2f, eps24f, eps4f, fcapf, fkf, fr02f, fr02if, rcf, sigf;
+  int cubic;        // equal edges: the neighbour loop runs in position units
+  float s2f, rc2u;  // scale^2 and the WCA cutoff^2 in position units^2
   double rc2, sig2, eps24, eps4, fcap, fk, fr02, rc, sig;
   double dt, a_fric, b_kick;  // v' = a v + b F ; x' = x + dt v'
   double gm;                  // gamma m (FP64 mode writes the friction force out)

@@ -196,6 +196,9 @@ int setup_grid(prx_system* sys, double rc) {
     S.wunit[k] = (float)(std::ldexp(1.0, sh) * (L / 4294967296.0));
     ncell *= nc;
   }
+  S.cubic = S.scale[0] == S.scale[1] && S.scale[1] == S.scale[2] ? 1 : 0;
+  S.s2f = S.scale[0] * S.scale[0];
+  S.rc2u = (float)(S.rc2 / ((double)S.scale[0] * (double)S.scale[0]));
   const double wmax = std::max((double)S.wunit[0], std::max((double)S.wunit[1], (double)S.wunit[2]));
   const double dmax = 0.5 * skin - 2.0 * std::sqrt(3.0) * wmax - 1e-6;
   if (!(dmax > 0.0)) return fail(sys, PRX_EINVAL, "skin too small for the displacement trigger");
@@ -223,7 +226,8 @@ int setup_grid(prx_system* sys, double rc) {
   const double V = sys->d.box[0] * sys->d.box[1] * sys->d.box[2];
   const double rho = (double)S.n / V;
   const double mean_nb = rho * 4.0 / 3.0 * M_PI * rv * rv * rv;
-  S.list_cap = std::max(32, std::min(255, (int)std::ceil(2.5 * mean_nb + 16.0)));
+  // (a multiple of 4: the build pads each list to whole stages of four)
+  S.list_cap = (std::max(32, std::min(252, (int)std::ceil(2.5 * mean_nb + 16.0))) + 3) & ~3;
   S.nl16 = S.n <= 65535 ? 1 : 0;
   {
     void* nl = nullptr;
@@ -813,7 +817,8 @@ int prx_estimate_bytes(const prx_system_desc* desc, uint64_t* bytes) {
   }
   const double V = desc->box[0] * desc->box[1] * desc->box[2];
   const double mean_nb = (double)n / V * 4.0 / 3.0 * M_PI * rv * rv * rv;
-  const uint64_t list_cap = (uint64_t)std::max(32, std::min(255, (int)std::ceil(2.5 * mean_nb + 16.0)));
+  const uint64_t list_cap =
+      (uint64_t)((std::max(32, std::min(252, (int)std::ceil(2.5 * mean_nb + 16.0))) + 3) & ~3);
   const uint64_t nl_bytes = n <= 65535 ? 2 : 4;  // as setup_grid
   const uint64_t per_set = n * (6 * 8 + 4 + 3 + 4 * cap);
   const uint64_t nblk = std::max<uint64_t>(n / RX_THREADS + 1, ncell / SCAN_TILE + 1) + 1;
