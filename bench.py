@@ -461,7 +461,7 @@ def main():
         ge = P.System(desc, pin["x"], pin["v"], pin["t"], pin["s"], stream=stream.cuda_stream)
         ge.set_reaction(P.make_reaction(**sch))
         d2h = 0
-        ke = 8
+        ke = max(args.steps, 1)  # the same number of steps as the device-timed region
         for q in range(ke):
             ge.run(THETA)
             ob = ge.observables()  # the step's result: populations, bonds, energy

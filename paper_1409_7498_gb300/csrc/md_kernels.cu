@@ -316,7 +316,7 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
 }
 
 template <bool NL16, bool FORCES_ONLY, bool CUBIC>
-__global__ void __launch_bounds__(256, 5)
+__global__ void __launch_bounds__(256, 6)
     k_step_nl(Sys S, cudaGraphConditionalHandle cond, int use_cond) {
   step_nl_body<NL16, FORCES_ONLY, CUBIC>(S, Blk{blockIdx.x, gridDim.x}, cond, use_cond);
 }
@@ -1004,7 +1004,48 @@ __global__ void __launch_bounds__(256)
 
 inline unsigned blocks_for(uint64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Input staging for a plain creation (slot = particle index).  Positions are
+// wrapped by at most one box edge (v >= L: v - L; v < 0: v + L, FP64), the
+// same operations as the host-side restore path.
+__global__ void k_stage_input(Sys S, const double* __restrict__ buf, int which) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S.n) return;
+  const SoA& B = S.s0;
+  double c[3];
+  unsigned err = 0u;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double v = buf[3 * (size_t)s + k];
+    if (which == 0) {
+      if (!isfinite(v)) {
+        err = max(err, 1u);
+      } else {
+        if (v >= S.L[k]) v = __dsub_rn(v, S.L[k]);
+        if (v < 0.0) v = __dadd_rn(v, S.L[k]);
+        if (!(v >= 0.0 && v < S.L[k])) err = max(err, 2u);
+      }
+    }
+    c[k] = v;
+  }
+  if (which == 0) {
+    B.x[s] = c[0];
+    B.y[s] = c[1];
+    B.z[s] = c[2];
+    B.id[s] = s;
+    if (B.type[s] >= PRX_MAX_TYPES) err = max(err, 3u);
+    if (err) atomicMax(&S.ctl->input_err, err);
+  } else {
+    B.vx[s] = c[0];
+    B.vy[s] = c[1];
+    B.vz[s] = c[2];
+  }
+}
+
 }  // namespace
+
+void launch_stage_input(const Sys& S, cudaStream_t st, const double* buf, int which) {
+  if (S.n) k_stage_input<<<blocks_for(S.n, 256), 256, 0, st>>>(S, buf, which);
+}
 
 void launch_step(const Sys& S, cudaStream_t st, int fp64, int forces_only,
                  cudaGraphConditionalHandle h, int use_cond) {

@@ -80,7 +80,8 @@ struct Ctl {
   unsigned long long rx_base;  // bond-list offset of the current reaction
   long long trace[4];          // candidates, retained, a_winners, formed
   unsigned int n_active;       // eligible A's of the current reaction step
-  unsigned int pad_;
+  unsigned int input_err;      // creation: first bad input kind (1 non-finite
+                               // position, 2 outside the box, 3 type >= 8)
 };
 
 struct RxParams {
@@ -336,6 +337,11 @@ int rebin_kernel_count();
 int rx_kernel_count(int rule);
 int step_kernel_count(int fp64);
 size_t build_tile_smem(const Sys& S);
+// Creation without a saved slot order: particle p goes to slot p.  `buf`
+// holds the caller's (n, 3) positions (which = 0: validated, wrapped once
+// into the box, ids and types checked) or velocities (which = 1), copied to
+// the device; errors land in ctl->input_err.
+void launch_stage_input(const Sys& S, cudaStream_t st, const double* buf, int which);
 int configure_build_kernel(size_t smem_bytes);
 
 }  // namespace prx

@@ -402,7 +402,11 @@ struct HostSlots {
   std::vector<uint4> P;
 };
 
-int fetch_slots(prx_system* sys, HostSlots& h, bool pos, bool vel, bool topo) {
+// What fetch_slots copies besides the ids (bit mask).
+enum : unsigned { FS_POS = 1u, FS_VEL = 2u, FS_TYPE = 4u, FS_STATE = 8u, FS_TOPO = 16u };
+
+int fetch_slots(prx_system* sys, HostSlots& h, unsigned what) {
+  const bool pos = what & FS_POS, vel = what & FS_VEL, topo = what & FS_TOPO;
   int rc = read_ctl(sys);
   if (rc) return rc;
   const size_t n = sys->S.n;
@@ -421,12 +425,18 @@ int fetch_slots(prx_system* sys, HostSlots& h, bool pos, bool vel, bool topo) {
     CK(cudaMemcpyAsync(h.vy.data(), B.vy, 8 * n, cudaMemcpyDeviceToHost, sys->stream));
     CK(cudaMemcpyAsync(h.vz.data(), B.vz, 8 * n, cudaMemcpyDeviceToHost, sys->stream));
   }
+  if ((what & FS_TYPE) && n) {
+    h.type.resize(n);
+    CK(cudaMemcpyAsync(h.type.data(), B.type, n, cudaMemcpyDeviceToHost, sys->stream));
+  }
+  if ((what & FS_STATE) && n) {
+    h.state.resize(n);
+    CK(cudaMemcpyAsync(h.state.data(), B.state, n, cudaMemcpyDeviceToHost, sys->stream));
+  }
   if (topo && n) {
-    h.type.resize(n); h.state.resize(n); h.nadj.resize(n); h.adj.resize(n * sys->S.cap);
+    h.nadj.resize(n); h.adj.resize(n * sys->S.cap);
     h.P.resize(n);
     const uint4* Pd = sys->ctl_host->phase ? sys->S.P1 : sys->S.P0;
-    CK(cudaMemcpyAsync(h.type.data(), B.type, n, cudaMemcpyDeviceToHost, sys->stream));
-    CK(cudaMemcpyAsync(h.state.data(), B.state, n, cudaMemcpyDeviceToHost, sys->stream));
     CK(cudaMemcpyAsync(h.nadj.data(), B.nadj, n, cudaMemcpyDeviceToHost, sys->stream));
     CK(cudaMemcpyAsync(h.adj.data(), B.adj, 4 * n * sys->S.cap, cudaMemcpyDeviceToHost, sys->stream));
     CK(cudaMemcpyAsync(h.P.data(), Pd, sizeof(uint4) * n, cudaMemcpyDeviceToHost, sys->stream));
@@ -540,63 +550,6 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
     return bail(rc);
   if ((rc = setup_grid(sys, grid_rc > rc_w ? grid_rc : rc_w))) return bail(rc);
 
-  // host staging in slot order
-  std::vector<uint32_t> ids(n);
-  for (uint32_t s = 0; s < n; ++s) ids[s] = slot_ids ? slot_ids[s] : s;
-  std::vector<uint32_t> slot_of(n, 0xFFFFFFFFu);
-  for (uint32_t s = 0; s < n; ++s) {
-    if (ids[s] >= n || slot_of[ids[s]] != 0xFFFFFFFFu) return bail(fail(sys, PRX_EINVAL, "bad slot order"));
-    slot_of[ids[s]] = s;
-  }
-  std::vector<double> hx(n), hy(n), hz(n), hvx(n, 0.0), hvy(n, 0.0), hvz(n, 0.0);
-  std::vector<uint8_t> ht(n), hn(n, 0);
-  std::vector<int8_t> hs(n);
-  std::vector<uint32_t> hadj((size_t)n * S.cap, 0u);
-  for (uint32_t s = 0; s < n; ++s) {
-    const uint32_t p = ids[s];
-    double c[3];
-    for (int k = 0; k < 3; ++k) {
-      const double v = pos[3 * (size_t)p + k];
-      if (!std::isfinite(v)) return bail(fail(sys, PRX_EINVAL, "non-finite position"));
-      c[k] = slot_cells ? v : wrap_host(v, desc->box[k]);
-      if (!slot_cells && !(c[k] >= 0.0 && c[k] < desc->box[k]))
-        return bail(fail(sys, PRX_EINVAL, "position more than one box edge outside the box"));
-    }
-    hx[s] = c[0];
-    hy[s] = c[1];
-    hz[s] = c[2];
-    if (vel) {
-      hvx[s] = vel[3 * (size_t)p];
-      hvy[s] = vel[3 * (size_t)p + 1];
-      hvz[s] = vel[3 * (size_t)p + 2];
-    }
-    if (type[p] >= PRX_MAX_TYPES) return bail(fail(sys, PRX_EINVAL, "type >= 8"));
-    ht[s] = type[p];
-    hs[s] = state[p];
-  }
-  if (slot_adj_ids) {
-    for (uint32_t s = 0; s < n; ++s) {
-      if (slot_nadj[s] > S.cap) return bail(fail(sys, PRX_ECAPACITY, "adjacency row beyond capacity"));
-      hn[s] = slot_nadj[s];
-      for (uint32_t b = 0; b < slot_nadj[s]; ++b) {
-        const uint32_t e = slot_adj_ids[(size_t)s * S.cap + b];
-        if ((e & SLOT_MASK) >= n) return bail(fail(sys, PRX_EINVAL, "bad adjacency entry"));
-        hadj[(size_t)s * S.cap + b] = slot_of[e & SLOT_MASK] | (e & ~SLOT_MASK);
-      }
-    }
-  } else {
-    for (uint64_t b = 0; b < n_bonds; ++b) {
-      const prx_bond& bd = bonds[b];
-      if (bd.a >= n || bd.t >= n || bd.a == bd.t || bd.style > 1u)
-        return bail(fail(sys, PRX_EINVAL, "bad initial bond"));
-      const uint32_t pa = slot_of[bd.a], pt = slot_of[bd.t];
-      if (hn[pa] >= S.cap || hn[pt] >= S.cap) return bail(fail(sys, PRX_ECAPACITY, "initial bonds exceed adj_cap"));
-      hadj[(size_t)pa * S.cap + hn[pa]++] = pt | (bd.style << 31);
-      hadj[(size_t)pt * S.cap + hn[pt]++] = pa | (bd.style << 31);
-    }
-  }
-  if (n_bonds > S.bond_cap) return bail(fail(sys, PRX_ECAPACITY, "more bonds than the bond list holds"));
-
   const SoA& B = S.s0;
   auto up = [&](void* dst, const void* src, size_t bytes) -> int {
     if (!bytes) return PRX_OK;
@@ -604,12 +557,119 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
       return fail(sys, PRX_ECUDA, "upload failed");
     return PRX_OK;
   };
-  if ((rc = up(B.x, hx.data(), 8ull * n)) || (rc = up(B.y, hy.data(), 8ull * n)) || (rc = up(B.z, hz.data(), 8ull * n)) ||
-      (rc = up(B.vx, hvx.data(), 8ull * n)) || (rc = up(B.vy, hvy.data(), 8ull * n)) ||
-      (rc = up(B.vz, hvz.data(), 8ull * n)) || (rc = up(B.id, ids.data(), 4ull * n)) ||
-      (rc = up(B.type, ht.data(), n)) || (rc = up(B.state, hs.data(), n)) || (rc = up(B.nadj, hn.data(), n)) ||
-      (rc = up(B.adj, hadj.data(), 4ull * n * S.cap)))
-    return bail(rc);
+  // a plain creation (particle p in slot p) stages positions, velocities and
+  // ids on the device; a restore (saved slot order) goes through the host
+  const bool plain = !slot_ids && !slot_cells && !slot_adj_ids;
+  if (plain) {
+    std::vector<uint8_t> hn;
+    std::vector<uint32_t> hadj;
+    if (n_bonds) {
+      hn.assign(n, 0);
+      hadj.assign((size_t)n * S.cap, 0u);
+      for (uint64_t b = 0; b < n_bonds; ++b) {
+        const prx_bond& bd = bonds[b];
+        if (bd.a >= n || bd.t >= n || bd.a == bd.t || bd.style > 1u)
+          return bail(fail(sys, PRX_EINVAL, "bad initial bond"));
+        if (hn[bd.a] >= S.cap || hn[bd.t] >= S.cap)
+          return bail(fail(sys, PRX_ECAPACITY, "initial bonds exceed adj_cap"));
+        hadj[(size_t)bd.a * S.cap + hn[bd.a]++] = bd.t | (bd.style << 31);
+        hadj[(size_t)bd.t * S.cap + hn[bd.t]++] = bd.a | (bd.style << 31);
+      }
+    }
+    if (n_bonds > S.bond_cap) return bail(fail(sys, PRX_ECAPACITY, "more bonds than the bond list holds"));
+    Ctl z;
+    memset(&z, 0, sizeof(z));
+    if ((rc = up(S.ctl, &z, sizeof(Ctl))) || (rc = up(B.type, type, n)) || (rc = up(B.state, state, n)))
+      return bail(rc);
+    if ((rc = up(S.fout, pos, 24ull * n))) return bail(rc);
+    launch_stage_input(S, sys->stream, S.fout, 0);
+    if (vel) {
+      if ((rc = up(S.fout, vel, 24ull * n))) return bail(rc);
+      launch_stage_input(S, sys->stream, S.fout, 1);
+    } else if (n && (cudaMemsetAsync(B.vx, 0, 8ull * n, sys->stream) != cudaSuccess ||
+                     cudaMemsetAsync(B.vy, 0, 8ull * n, sys->stream) != cudaSuccess ||
+                     cudaMemsetAsync(B.vz, 0, 8ull * n, sys->stream) != cudaSuccess)) {
+      return bail(fail(sys, PRX_ECUDA, "memset failed"));
+    }
+    if (n_bonds) {
+      if ((rc = up(B.nadj, hn.data(), n)) || (rc = up(B.adj, hadj.data(), 4ull * n * S.cap))) return bail(rc);
+    } else if (n && (cudaMemsetAsync(B.nadj, 0, n, sys->stream) != cudaSuccess ||
+                     cudaMemsetAsync(B.adj, 0, 4ull * n * S.cap, sys->stream) != cudaSuccess)) {
+      return bail(fail(sys, PRX_ECUDA, "memset failed"));
+    }
+    if (cudaGetLastError() != cudaSuccess) return bail(fail(sys, PRX_ECUDA, "input staging launch failed"));
+    if ((rc = read_ctl(sys))) return bail(rc);
+    switch (sys->ctl_host->input_err) {
+      case 0: break;
+      case 1: return bail(fail(sys, PRX_EINVAL, "non-finite position"));
+      case 2: return bail(fail(sys, PRX_EINVAL, "position more than one box edge outside the box"));
+      default: return bail(fail(sys, PRX_EINVAL, "type >= 8"));
+    }
+  } else {
+    // host staging in slot order
+    std::vector<uint32_t> ids(n);
+    for (uint32_t s = 0; s < n; ++s) ids[s] = slot_ids ? slot_ids[s] : s;
+    std::vector<uint32_t> slot_of(n, 0xFFFFFFFFu);
+    for (uint32_t s = 0; s < n; ++s) {
+      if (ids[s] >= n || slot_of[ids[s]] != 0xFFFFFFFFu) return bail(fail(sys, PRX_EINVAL, "bad slot order"));
+      slot_of[ids[s]] = s;
+    }
+    std::vector<double> hx(n), hy(n), hz(n), hvx(n, 0.0), hvy(n, 0.0), hvz(n, 0.0);
+    std::vector<uint8_t> ht(n), hn(n, 0);
+    std::vector<int8_t> hs(n);
+    std::vector<uint32_t> hadj((size_t)n * S.cap, 0u);
+    for (uint32_t s = 0; s < n; ++s) {
+      const uint32_t p = ids[s];
+      double c[3];
+      for (int k = 0; k < 3; ++k) {
+        const double v = pos[3 * (size_t)p + k];
+        if (!std::isfinite(v)) return bail(fail(sys, PRX_EINVAL, "non-finite position"));
+        c[k] = slot_cells ? v : wrap_host(v, desc->box[k]);
+        if (!slot_cells && !(c[k] >= 0.0 && c[k] < desc->box[k]))
+          return bail(fail(sys, PRX_EINVAL, "position more than one box edge outside the box"));
+      }
+      hx[s] = c[0];
+      hy[s] = c[1];
+      hz[s] = c[2];
+      if (vel) {
+        hvx[s] = vel[3 * (size_t)p];
+        hvy[s] = vel[3 * (size_t)p + 1];
+        hvz[s] = vel[3 * (size_t)p + 2];
+      }
+      if (type[p] >= PRX_MAX_TYPES) return bail(fail(sys, PRX_EINVAL, "type >= 8"));
+      ht[s] = type[p];
+      hs[s] = state[p];
+    }
+    if (slot_adj_ids) {
+      for (uint32_t s = 0; s < n; ++s) {
+        if (slot_nadj[s] > S.cap) return bail(fail(sys, PRX_ECAPACITY, "adjacency row beyond capacity"));
+        hn[s] = slot_nadj[s];
+        for (uint32_t b = 0; b < slot_nadj[s]; ++b) {
+          const uint32_t e = slot_adj_ids[(size_t)s * S.cap + b];
+          if ((e & SLOT_MASK) >= n) return bail(fail(sys, PRX_EINVAL, "bad adjacency entry"));
+          hadj[(size_t)s * S.cap + b] = slot_of[e & SLOT_MASK] | (e & ~SLOT_MASK);
+        }
+      }
+    } else {
+      for (uint64_t b = 0; b < n_bonds; ++b) {
+        const prx_bond& bd = bonds[b];
+        if (bd.a >= n || bd.t >= n || bd.a == bd.t || bd.style > 1u)
+          return bail(fail(sys, PRX_EINVAL, "bad initial bond"));
+        const uint32_t pa = slot_of[bd.a], pt = slot_of[bd.t];
+        if (hn[pa] >= S.cap || hn[pt] >= S.cap) return bail(fail(sys, PRX_ECAPACITY, "initial bonds exceed adj_cap"));
+        hadj[(size_t)pa * S.cap + hn[pa]++] = pt | (bd.style << 31);
+        hadj[(size_t)pt * S.cap + hn[pt]++] = pa | (bd.style << 31);
+      }
+    }
+    if (n_bonds > S.bond_cap) return bail(fail(sys, PRX_ECAPACITY, "more bonds than the bond list holds"));
+
+    if ((rc = up(B.x, hx.data(), 8ull * n)) || (rc = up(B.y, hy.data(), 8ull * n)) || (rc = up(B.z, hz.data(), 8ull * n)) ||
+        (rc = up(B.vx, hvx.data(), 8ull * n)) || (rc = up(B.vy, hvy.data(), 8ull * n)) ||
+        (rc = up(B.vz, hvz.data(), 8ull * n)) || (rc = up(B.id, ids.data(), 4ull * n)) ||
+        (rc = up(B.type, ht.data(), n)) || (rc = up(B.state, hs.data(), n)) || (rc = up(B.nadj, hn.data(), n)) ||
+        (rc = up(B.adj, hadj.data(), 4ull * n * S.cap)))
+      return bail(rc);
+  }
   if (n_bonds) {
     if ((rc = up(S.bonds, bonds, sizeof(prx_bond) * n_bonds))) return bail(rc);
   }
@@ -980,7 +1040,7 @@ int prx_compute_forces(prx_system* sys, double* f_out, double* epot_out) {
   CK(cudaMemcpyAsync(f.data(), sys->S.fout, 24 * n, cudaMemcpyDeviceToHost, sys->stream));
   CK(cudaMemcpyAsync(e.data(), sys->S.eout, 8 * n, cudaMemcpyDeviceToHost, sys->stream));
   HostSlots h;
-  int rc = fetch_slots(sys, h, false, false, false);
+  int rc = fetch_slots(sys, h, 0u);
   if (rc) return rc;
   std::vector<double> e_by_id(n);
   for (size_t s = 0; s < n; ++s) {
@@ -1006,7 +1066,7 @@ int prx_get_step(prx_system* sys, uint64_t* step) {
 int prx_get_positions(prx_system* sys, double* out) {
   if (!sys || (!out && sys->S.n)) return PRX_EINVAL;
   HostSlots h;
-  int rc = fetch_slots(sys, h, true, false, false);
+  int rc = fetch_slots(sys, h, FS_POS);
   if (rc) return rc;
   for (size_t s = 0; s < h.id.size(); ++s) {
     const size_t p = h.id[s];
@@ -1020,7 +1080,7 @@ int prx_get_positions(prx_system* sys, double* out) {
 int prx_get_velocities(prx_system* sys, double* out) {
   if (!sys || (!out && sys->S.n)) return PRX_EINVAL;
   HostSlots h;
-  int rc = fetch_slots(sys, h, false, true, false);
+  int rc = fetch_slots(sys, h, FS_VEL);
   if (rc) return rc;
   for (size_t s = 0; s < h.id.size(); ++s) {
     const size_t p = h.id[s];
@@ -1034,7 +1094,7 @@ int prx_get_velocities(prx_system* sys, double* out) {
 int prx_get_states(prx_system* sys, int8_t* out) {
   if (!sys || (!out && sys->S.n)) return PRX_EINVAL;
   HostSlots h;
-  int rc = fetch_slots(sys, h, false, false, true);
+  int rc = fetch_slots(sys, h, FS_STATE);
   if (rc) return rc;
   for (size_t s = 0; s < h.id.size(); ++s) out[h.id[s]] = h.state[s];
   return sync_status(sys);
@@ -1043,7 +1103,7 @@ int prx_get_states(prx_system* sys, int8_t* out) {
 int prx_get_types(prx_system* sys, uint8_t* out) {
   if (!sys || (!out && sys->S.n)) return PRX_EINVAL;
   HostSlots h;
-  int rc = fetch_slots(sys, h, false, false, true);
+  int rc = fetch_slots(sys, h, FS_TYPE);
   if (rc) return rc;
   for (size_t s = 0; s < h.id.size(); ++s) out[h.id[s]] = h.type[s];
   return sync_status(sys);
@@ -1055,6 +1115,12 @@ int prx_get_bonds(prx_system* sys, prx_bond* out, uint64_t cap, uint64_t* n_out)
   if (rc) return rc;
   const uint64_t nb = sys->ctl_host->nbonds;
   *n_out = nb;
+  const uint64_t m = std::min(cap, nb);
+  if (!m || !out) {  // the count alone
+    rc = sync_status(sys);
+    if (rc) return rc;
+    return cap < nb ? fail(sys, PRX_ECAPACITY, "bond buffer too small") : PRX_OK;
+  }
   std::vector<prx_bond> b(nb);
   if (nb) {
     CK(cudaMemcpyAsync(b.data(), sys->S.bonds, sizeof(prx_bond) * nb, cudaMemcpyDeviceToHost, sys->stream));
@@ -1065,8 +1131,7 @@ int prx_get_bonds(prx_system* sys, prx_bond* out, uint64_t cap, uint64_t* n_out)
     if (x.a != y.a) return x.a < y.a;
     return x.t < y.t;
   });
-  const uint64_t m = std::min(cap, nb);
-  if (m && out) memcpy(out, b.data(), sizeof(prx_bond) * m);
+  memcpy(out, b.data(), sizeof(prx_bond) * m);
   rc = sync_status(sys);
   if (rc) return rc;
   return cap < nb ? fail(sys, PRX_ECAPACITY, "bond buffer too small") : PRX_OK;
@@ -1185,7 +1250,7 @@ int prx_profile_end(prx_system* sys, prx_kernel_time* out, uint32_t cap, uint32_
 int prx_save(prx_system* sys, const char* path) {
   if (!sys || !path) return PRX_EINVAL;
   HostSlots h;
-  int rc = fetch_slots(sys, h, true, true, true);
+  int rc = fetch_slots(sys, h, FS_POS | FS_VEL | FS_TYPE | FS_STATE | FS_TOPO);
   if (rc) return rc;
   rc = sync_status(sys);
   if (rc) return rc;
