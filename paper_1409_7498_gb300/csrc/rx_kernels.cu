@@ -270,14 +270,20 @@ __device__ __forceinline__ void rx_select_T_body(const Sys& S, const Blk blk, lo
       const unsigned long long mine = key64(keyed_draw(S.seed, step, idT, idi, TAG_SEL_T));
       bool keep = true;
       const int cnt = S.nn[T];
-      for (int k = 0; k < cnt; ++k) {
-        const uint32_t a = nl_get_rx<NL16>(S, k, T);
-        if (a == i || S.win[a] != T) continue;
-        const uint32_t ida = B.id[a];
-        const unsigned long long other = key64(keyed_draw(S.seed, step, idT, ida, TAG_SEL_T));
-        if (other < mine || (other == mine && ida < idi)) {
-          keep = false;
-          break;
+      // four list entries of T at a time (independent loads go out together)
+      for (int k0 = 0; k0 < cnt && keep; k0 += 4) {
+        uint32_t aa[4], wa[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) aa[u] = k0 + u < cnt ? nl_get_rx<NL16>(S, k0 + u, T) : i;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) wa[u] = S.win[aa[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t a = aa[u];
+          if (!keep || k0 + u >= cnt || a == i || wa[u] != T) continue;
+          const uint32_t ida = B.id[a];
+          const unsigned long long other = key64(keyed_draw(S.seed, step, idT, ida, TAG_SEL_T));
+          if (other < mine || (other == mine && ida < idi)) keep = false;
         }
       }
       if (keep) fin = T;
