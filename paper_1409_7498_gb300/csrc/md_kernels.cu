@@ -623,11 +623,39 @@ __global__ void kb_rebin_scatter(const Sys* __restrict__ T, const BlkMap* __rest
 }
 
 // Sorts each cell's members by old slot: the order inside a cell then does
-// not depend on the order in which the scatter's atomics completed.
+// not depend on the order in which the scatter's atomics completed.  Then
+// records every member's new slot (new_of_old), for the permutation.
+__device__ __forceinline__ void cas_u32(uint32_t& a, uint32_t& b) {
+  const uint32_t lo = min(a, b), hi = max(a, b);
+  a = lo;
+  b = hi;
+}
 __device__ __forceinline__ void rebin_cellsort_body(const Sys& S, const Blk blk) {
   const uint32_t c = blk.b * blockDim.x + threadIdx.x;
   if (c >= (uint32_t)S.ncell) return;
   const uint32_t s0 = S.cell_start[c], s1 = S.cell_start[c + 1];
+  if (s1 - s0 <= 8u) {
+    // the common case: an 8-input sorting network in registers (absent
+    // members padded with the largest key)
+    uint32_t v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = s0 + q < s1 ? S.tmp[s0 + q] : 0xFFFFFFFFu;
+    cas_u32(v[0], v[1]); cas_u32(v[2], v[3]); cas_u32(v[4], v[5]); cas_u32(v[6], v[7]);
+    cas_u32(v[0], v[2]); cas_u32(v[1], v[3]); cas_u32(v[4], v[6]); cas_u32(v[5], v[7]);
+    cas_u32(v[1], v[2]); cas_u32(v[5], v[6]); cas_u32(v[0], v[4]); cas_u32(v[3], v[7]);
+    cas_u32(v[1], v[5]); cas_u32(v[2], v[6]);
+    cas_u32(v[1], v[4]); cas_u32(v[3], v[6]);
+    cas_u32(v[2], v[4]); cas_u32(v[3], v[5]);
+    cas_u32(v[3], v[4]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (s0 + q < s1) {
+        S.tmp[s0 + q] = v[q];
+        S.new_of_old[v[q]] = s0 + q;
+      }
+    }
+    return;
+  }
   for (uint32_t a = s0 + 1; a < s1; ++a) {
     const uint32_t v = S.tmp[a];
     uint32_t b = a;
@@ -637,6 +665,7 @@ __device__ __forceinline__ void rebin_cellsort_body(const Sys& S, const Blk blk)
     }
     S.tmp[b] = v;
   }
+  for (uint32_t a = s0; a < s1; ++a) S.new_of_old[S.tmp[a]] = a;
 }
 
 __global__ void k_rebin_cellsort(Sys S) { rebin_cellsort_body(S, Blk{blockIdx.x, gridDim.x}); }
@@ -648,9 +677,9 @@ __global__ void kb_rebin_cellsort(const Sys* __restrict__ T, const BlkMap* __res
 }
 
 // New slot s takes old slot tmp[s]: copies every per-particle array into the
-// other set and writes the fixed-point position with a fresh displacement
-// reference; tmp[s] then receives the cell the sort put the slot in (read by
-// the list build).
+// other set (bond partners renamed to their new slots) and writes the
+// fixed-point position with a fresh displacement reference; tmp[s] then
+// receives the cell the sort put the slot in (read by the list build).
 __device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk, bool wrap) {
   Ctl* ctl = S.ctl;
   const int set = ctl->set;
@@ -681,9 +710,10 @@ __device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk, 
   B.state[s] = A.state[o];
   const uint32_t nb = A.nadj[o];
   B.nadj[s] = (uint8_t)nb;
-  for (uint32_t b = 0; b < nb; ++b) B.adj[(size_t)s * S.cap + b] = A.adj[(size_t)o * S.cap + b];
-  S.new_of_old[o] = s;
-  S.slot_of_id[pid] = s;
+  for (uint32_t b = 0; b < nb; ++b) {  // partners renamed to their new slots
+    const uint32_t e = A.adj[(size_t)o * S.cap + b];
+    B.adj[(size_t)s * S.cap + b] = S.new_of_old[e & SLOT_MASK] | (e & ~SLOT_MASK);
+  }
   const uint32_t X = periodic_fx(x, S.Lfx[0], S.M64[0]);
   const uint32_t Y = periodic_fx(y, S.Lfx[1], S.M64[1]);
   const uint32_t Z = periodic_fx(z, S.Lfx[2], S.M64[2]);
@@ -699,26 +729,6 @@ __global__ void kb_rebin_permute(const Sys* __restrict__ T, const BlkMap* __rest
   const Sys& S = T[m.sys];
   if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
   rebin_permute_body(S, Blk{m.b, m.nb}, true);
-}
-
-__device__ __forceinline__ void rebin_remap_body(const Sys& S, const Blk blk) {
-  Ctl* ctl = S.ctl;
-  const SoA B = ctl->set ? S.s0 : S.s1;  // the set just written
-  const uint32_t s = blk.b * blockDim.x + threadIdx.x;
-  if (s >= S.n) return;
-  const uint32_t nb = B.nadj[s];
-  for (uint32_t b = 0; b < nb; ++b) {
-    const uint32_t e = B.adj[(size_t)s * S.cap + b];
-    B.adj[(size_t)s * S.cap + b] = S.new_of_old[e & SLOT_MASK] | (e & ~SLOT_MASK);
-  }
-}
-
-__global__ void k_rebin_remap(Sys S) { rebin_remap_body(S, Blk{blockIdx.x, gridDim.x}); }
-__global__ void kb_rebin_remap(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
-  const BlkMap m = M[blockIdx.x];
-  const Sys& S = T[m.sys];
-  if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
-  rebin_remap_body(S, Blk{m.b, m.nb});
 }
 
 // ---------------------------------------------------------------------------
@@ -1108,11 +1118,11 @@ int raise_smem_limit(int which, size_t bytes) {
 
 int configure_build_kernel(size_t smem_bytes) { return raise_smem_limit(0, smem_bytes); }
 
-int rebin_kernel_count() { return 9; }
+int rebin_kernel_count() { return 8; }
 
-// Whole rebuild: keys (mode 0: from the fixed-point positions of the last
-// step; 1: from the FP64 positions; 2: given), scan, scatter,
-// per-cell sort, permutation, adjacency remap, Verlet lists.  `hook`
+// Whole rebuild: keys and counts (mode 0: from the fixed-point positions of
+// the last step; 1: from the FP64 positions; 2: given), scan, scatter,
+// per-cell sort, permutation (with the adjacency renamed), Verlet lists.  `hook`
 // (optional) is called before (0) and after (1) each launch with the
 // kernel's name, for event timing.
 void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, const char*, int),
@@ -1148,9 +1158,6 @@ void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, c
   H("rebin_permute", 0);
   k_rebin_permute<<<gp, 256, 0, st>>>(S, mode != 2);
   H("rebin_permute", 1);
-  H("rebin_remap", 0);
-  k_rebin_remap<<<gp, 256, 0, st>>>(S);
-  H("rebin_remap", 1);
   const unsigned gt = (unsigned)(S.tiles_y * S.nc[2]);
   const size_t sm = build_tile_smem(S);
   H("build_nlist", 0);
@@ -1175,11 +1182,10 @@ void launch_batch_rebuild(const BatchLaunch& L, cudaStream_t st) {
   kb_rebin_scatter<<<L.n_part, 256, 0, st>>>(L.T, L.part);
   kb_rebin_cellsort<<<L.n_cell, 256, 0, st>>>(L.T, L.cell);
   kb_rebin_permute<<<L.n_part, 256, 0, st>>>(L.T, L.part);
-  kb_rebin_remap<<<L.n_part, 256, 0, st>>>(L.T, L.part);
   kb_build_nlist<<<L.n_build, L.build_threads, L.build_smem, st>>>(L.T, L.build);
 }
 
-int batch_rebuild_kernel_count() { return 10; }
+int batch_rebuild_kernel_count() { return 9; }
 
 int configure_batch_build_kernel(size_t smem_bytes) { return raise_smem_limit(1, smem_bytes); }
 

@@ -147,7 +147,7 @@ struct Sys {
   uint4 *P0, *P1;
   uint32_t* cell_start;
   uint32_t *count, *fill;
-  uint32_t *key, *tmp, *new_of_old, *slot_of_id;
+  uint32_t *key, *tmp, *new_of_old;
   uint32_t *win, *fin, *blk_count, *blk_off;
   BondRec* bonds;
   unsigned long long bond_cap;

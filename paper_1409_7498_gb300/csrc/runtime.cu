@@ -542,7 +542,7 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
   }
   if ((rc = dalloc(sys, L, &S.P0, n)) || (rc = dalloc(sys, L, &S.P1, n)) || (rc = dalloc(sys, L, &S.key, n)) ||
       (rc = dalloc(sys, L, &S.tmp, n)) || (rc = dalloc(sys, L, &S.new_of_old, n)) ||
-      (rc = dalloc(sys, L, &S.slot_of_id, n)) || (rc = dalloc(sys, L, &S.win, n)) ||
+      (rc = dalloc(sys, L, &S.win, n)) ||
       (rc = dalloc(sys, L, &S.fin, n)) || (rc = dalloc(sys, L, &S.bonds, (size_t)S.bond_cap)) ||
       (rc = dalloc(sys, L, &S.hist, (size_t)S.hist_cap + 1)) || (rc = dalloc(sys, L, &S.ctl, 1)) ||
       (rc = dalloc(sys, L, &S.red, 4 * ((size_t)(n + RX_THREADS - 1) / RX_THREADS + 1))) ||
@@ -883,7 +883,7 @@ int prx_estimate_bytes(const prx_system_desc* desc, uint64_t* bytes) {
   const uint64_t per_set = n * (6 * 8 + 4 + 3 + 4 * cap);
   const uint64_t nblk = std::max<uint64_t>(n / RX_THREADS + 1, ncell / SCAN_TILE + 1) + 1;
   const uint64_t allocs = 40;  // separate cudaMalloc calls, each rounded up
-  *bytes = 2 * per_set + n * (2 * 16 + 6 * 4) + (n * cap / 2 + 1) * sizeof(prx_bond) +
+  *bytes = 2 * per_set + n * (2 * 16 + 5 * 4) + (n * cap / 2 + 1) * sizeof(prx_bond) +
            (kHistCap + 1ull) * sizeof(prx_history_record) + sizeof(Ctl) + 32 * (n / RX_THREADS + 2) +
            32 * n + ncell * 12 + 8 * nblk + list_cap * n * nl_bytes + n + allocs * 4096;
   return PRX_OK;
