@@ -350,33 +350,37 @@ __device__ __forceinline__ void rx_scan_body(const Sys& S, const uint32_t nblk) 
   Ctl* ctl = S.ctl;
   __shared__ uint32_t warp_tot[32];
   __shared__ uint32_t carry_s;
-  if (threadIdx.x == 0) carry_s = 0u;
-  __syncthreads();
+  // one pass: each thread scans a run of consecutive block counts; the runs'
+  // sums are scanned across the block with warp shuffles
+  const uint32_t per = (nblk + blockDim.x - 1) / blockDim.x;
+  const uint32_t i0 = threadIdx.x * per, i1 = min(i0 + per, nblk);
+  uint32_t v = 0;
+  for (uint32_t q = i0; q < i1; ++q) v += S.blk_count[q];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (uint32_t base = 0; base < nblk; base += blockDim.x) {
-    const uint32_t idx = base + threadIdx.x;
-    const uint32_t v = idx < nblk ? S.blk_count[idx] : 0u;
-    uint32_t x = v;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t t = lane < nw ? warp_tot[lane] : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= o) x += y;
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+      if (lane >= o) t += y;
     }
-    if (lane == 31) warp_tot[wid] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t run = 0;
-      for (int w = 0; w < nw; ++w) {
-        const uint32_t t = warp_tot[w];
-        warp_tot[w] = run;
-        run += t;
-      }
-    }
-    __syncthreads();
-    if (idx < nblk) S.blk_off[idx] = carry_s + warp_tot[wid] + x - v;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry_s += warp_tot[wid] + x;
-    __syncthreads();
+    if (lane < nw) warp_tot[lane] = t;  // inclusive
+    if (lane == nw - 1) carry_s = t;
+  }
+  __syncthreads();
+  uint32_t run = (wid ? warp_tot[wid - 1] : 0u) + x - v;
+  for (uint32_t q = i0; q < i1; ++q) {
+    const uint32_t c = S.blk_count[q];
+    S.blk_off[q] = run;
+    run += c;
   }
   if (threadIdx.x == 0) {
     const unsigned long long total = carry_s;
