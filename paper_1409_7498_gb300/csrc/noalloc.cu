@@ -82,7 +82,7 @@ __global__ void k_na_find(NaArgs a) {
       if (bonded) continue;
       ++cand;
       const uint4 wa = keyed_draw(a.seed, a.step, i, j, TAG_ACCEPT);
-      if (!(u53(wa.x, wa.y) < a.R.p)) continue;
+      if (!u53_below(wa.x, wa.y, a.R.p53)) continue;
       ++ret;
       const unsigned long long k = na_key64(keyed_draw(a.seed, a.step, i, j, TAG_SEL_A));
       if (best == NONE || k < bestkey || (k == bestkey && j < best)) {
@@ -246,6 +246,7 @@ extern "C" int prx_react_noalloc(const prx_reaction_desc* rx, const double* box,
   a.R.dA = rx->dA;
   a.R.dT = rx->dT;
   a.R.p = rx->k * dt * (double)rx->theta;
+  a.R.p53 = p53_of(a.R.p);
   a.R.rr2 = rx->r_react * rx->r_react;
   a.R.rr2_pre = 0.f;
   a.R.style = (uint32_t)rx->bond_style;

@@ -936,6 +936,7 @@ int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx) {
   R.dA = rx->dA;
   R.dT = rx->dT;
   R.p = rx->k * sys->d.dt * (double)rx->theta;
+  R.p53 = p53_of(R.p);
   R.rr2 = rx->r_react * rx->r_react;
   R.rr2_pre = (float)((rx->r_react + 1e-3) * (rx->r_react + 1e-3));
   {

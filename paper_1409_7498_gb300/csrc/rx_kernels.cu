@@ -206,7 +206,7 @@ __device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long l
         const uint32_t idj = B.id[j];
         // step 2: retained when u < k dt Theta (Eq. 4)
         const uint4 wa = keyed_draw(S.seed, step, idi, idj, TAG_ACCEPT);
-        if (!(u53(wa.x, wa.y) < R.p)) continue;
+        if (!u53_below(wa.x, wa.y, R.p53)) continue;
         ++nret;
         // step 5: one T per A, uniformly at random
         const unsigned long long key = key64(keyed_draw(S.seed, step, idi, idj, TAG_SEL_A));
@@ -259,7 +259,7 @@ __device__ __forceinline__ void rx_select_T_body(const Sys& S, const Blk blk, lo
       winner = true;
       const uint32_t ida = B.id[i], idt = B.id[T];
       const uint4 w = keyed_draw(S.seed, step, min(ida, idt), max(ida, idt), TAG_NEAREST);
-      if (u53(w.x, w.y) < R.p) fin = T;
+      if (u53_below(w.x, w.y, R.p53)) fin = T;
     }
     S.fin[i] = fin;
   } else if (i < S.n) {
