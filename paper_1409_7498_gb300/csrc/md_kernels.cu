@@ -586,7 +586,35 @@ __device__ __forceinline__ void scan_down_body(const Sys& S, const Blk blk) {
     if (base + k < n) out[base + k + 1] = run;
   }
 }
+// The same with the tile's offset summed from the tile sums by the block
+// itself (no scan_top pass; for grids of at most 1,024 tiles).
+__device__ __forceinline__ void scan_down_self_body(const Sys& S, const Blk blk) {
+  const uint32_t* __restrict__ in = S.count;
+  const uint32_t n = (uint32_t)S.ncell;
+  uint32_t* __restrict__ out = S.cell_start;
+  uint32_t part = 0;
+  for (uint32_t t = threadIdx.x; t < blk.b; t += blockDim.x) part += S.blk_off[t];
+  uint32_t off;
+  (void)block_exclusive_scan_256(part, off);
+  const uint32_t base = blk.b * SCAN_TILE + threadIdx.x * (SCAN_TILE / 256);
+  uint32_t loc[SCAN_TILE / 256];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_TILE / 256; ++k) {
+    loc[k] = (base + k < n) ? in[base + k] : 0u;
+    s += loc[k];
+  }
+  uint32_t total;
+  uint32_t run = off + block_exclusive_scan_256(s, total);
+  if (blk.b == 0 && threadIdx.x == 0) out[0] = 0u;
+#pragma unroll
+  for (int k = 0; k < SCAN_TILE / 256; ++k) {
+    run += loc[k];
+    if (base + k < n) out[base + k + 1] = run;
+  }
+}
 __global__ void k_scan_down(Sys S) { scan_down_body(S, Blk{blockIdx.x, gridDim.x}); }
+__global__ void k_scan_down_self(Sys S) { scan_down_self_body(S, Blk{blockIdx.x, gridDim.x}); }
 __global__ void kb_scan_down(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
@@ -1118,7 +1146,11 @@ int raise_smem_limit(int which, size_t bytes) {
 
 int configure_build_kernel(size_t smem_bytes) { return raise_smem_limit(0, smem_bytes); }
 
-int rebin_kernel_count() { return 8; }
+constexpr unsigned kScanSelfTiles = 1024;  // tiles up to which the scan has two passes
+
+int rebin_kernel_count(const Sys& S) {
+  return (S.ncell + SCAN_TILE - 1) / SCAN_TILE <= (int)kScanSelfTiles ? 7 : 8;
+}
 
 // Whole rebuild: keys and counts (mode 0: from the fixed-point positions of
 // the last step; 1: from the FP64 positions; 2: given), scan, scatter,
@@ -1143,12 +1175,18 @@ void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, c
   H("scan_tiles", 0);
   k_scan_tiles<<<tiles, 256, 0, st>>>(S);
   H("scan_tiles", 1);
-  H("scan_top", 0);
-  k_scan_top<<<1, 256, 0, st>>>(S);
-  H("scan_top", 1);
-  H("scan_down", 0);
-  k_scan_down<<<tiles, 256, 0, st>>>(S);
-  H("scan_down", 1);
+  if (tiles <= kScanSelfTiles) {
+    H("scan_down", 0);
+    k_scan_down_self<<<tiles, 256, 0, st>>>(S);
+    H("scan_down", 1);
+  } else {
+    H("scan_top", 0);
+    k_scan_top<<<1, 256, 0, st>>>(S);
+    H("scan_top", 1);
+    H("scan_down", 0);
+    k_scan_down<<<tiles, 256, 0, st>>>(S);
+    H("scan_down", 1);
+  }
   H("rebin_scatter", 0);
   k_rebin_scatter<<<gp, 256, 0, st>>>(S);
   H("rebin_scatter", 1);

@@ -347,7 +347,7 @@ void launch_observables(const Sys& S, cudaStream_t st, int nblocks);
 void launch_pair_hist(const Sys& S, cudaStream_t st, const PairClass& a, const PairClass& b,
                       const double* e2, int nbins, unsigned long long* counts,
                       unsigned long long* nab);
-int rebin_kernel_count();
+int rebin_kernel_count(const Sys& S);
 int rx_kernel_count(int rule);
 int step_kernel_count(int fp64);
 size_t build_tile_smem(const Sys& S);

@@ -1196,7 +1196,7 @@ int prx_get_stats(prx_system* sys, prx_stats* out) {
   // every rebuild, inside a graph's IF node or launched directly, is the same
   // sequence of kernels and increments the device counter once
   out->kernel_launches = sys->step_launches * (uint64_t)step_kernel_count(sys->d.force_precision) +
-                         sys->ctl_host->rebins * (uint64_t)rebin_kernel_count() +
+                         sys->ctl_host->rebins * (uint64_t)rebin_kernel_count(sys->S) +
                          sys->graph_rx_launches * (uint64_t)rx_kernel_count(sys->S.R.rule) + sys->other_launches;
   for (int k = 0; k < 3; ++k) {
     out->cells[k] = (uint32_t)sys->S.nc[k];
