@@ -123,14 +123,15 @@ __device__ __forceinline__ uint32_t nearest_partner(const Sys& S, const SoA& B, 
   const int cnt = S.nn[i];
   for (int k = 0; k < cnt; ++k) {
     const uint32_t j = nl_get_rx<NL16>(S, k, i);
-    const bool ok = want_T ? in_window(R.mask_T, R.t_lo, R.t_hi, B.type[j], B.state[j])
-                           : in_window(R.mask_A, R.a_lo, R.a_hi, B.type[j], B.state[j]);
-    if (!ok) continue;
+    // distance prefilter first (as in the random rule's search)
     const uint4 pj = P[j];
     const float ex = __int2float_rn(pdiff(pj.x, pi.x)) * S.scale[0];
     const float ey = __int2float_rn(pdiff(pj.y, pi.y)) * S.scale[1];
     const float ez = __int2float_rn(pdiff(pj.z, pi.z)) * S.scale[2];
     if (!(fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < R.rr2_pre)) continue;
+    const bool ok = want_T ? in_window(R.mask_T, R.t_lo, R.t_hi, B.type[j], B.state[j])
+                           : in_window(R.mask_A, R.a_lo, R.a_hi, B.type[j], B.state[j]);
+    if (!ok) continue;
     const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
     const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
     const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
@@ -153,6 +154,25 @@ __device__ __forceinline__ uint32_t nearest_partner(const Sys& S, const SoA& B, 
 // Steps 1-5 for one eligible A: its Verlet list holds every particle within
 // the force cutoff, hence every candidate within r_react <= r_c.  Grid-stride
 // over the work list of eligible A's.
+// Table I steps 2 and 5 for one candidate pair (A = idi, T = slot j):
+// retained when u < k dt Theta (Eq. 4), then the smallest selection key wins
+// (ties to the smaller id).
+__device__ __forceinline__ void rx_accept_and_key(const Sys& S, const SoA& B,
+                                                  unsigned long long step, uint32_t idi, uint32_t j,
+                                                  uint64_t p53, long long& nret, uint32_t& best,
+                                                  unsigned long long& bestkey, uint32_t& bestid) {
+  const uint32_t idj = B.id[j];
+  const uint4 wa = keyed_draw(S.seed, step, idi, idj, TAG_ACCEPT);
+  if (!u53_below(wa.x, wa.y, p53)) return;
+  ++nret;
+  const unsigned long long key = key64(keyed_draw(S.seed, step, idi, idj, TAG_SEL_A));
+  if (best == NONE || key < bestkey || (key == bestkey && idj < bestid)) {
+    best = j;
+    bestkey = key;
+    bestid = idj;
+  }
+}
+
 template <bool NL16>
 __device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long long step_arg) {
   const RxParams& R = S.R;
@@ -176,17 +196,25 @@ __device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long l
       unsigned long long bestkey = 0ull;
       uint32_t bestid = 0u;
       const int cnt = S.nn[i];
+      // Pass 1 marks the list positions of the candidates (steps 1 and the
+      // bond check); pass 2 draws for them.  The draws (two Philox calls per
+      // candidate) then run once per candidate of the busiest lane, not once
+      // per list position at which any lane of the warp has one.
+      unsigned long long mask = 0ull;
       for (int k = 0; k < cnt; ++k) {
         const uint32_t j = nl_get_rx<NL16>(S, k, i);
-        if (!in_window(R.mask_T, R.t_lo, R.t_hi, B.type[j], B.state[j])) continue;
         // FP32 prefilter on the fixed-point displacement (error ~1e-7): it can
-        // only widen the set that the exact FP64 test below decides on
+        // only widen the set that the exact FP64 test below decides on.  It
+        // comes before the T-window test: the position gather is one sector
+        // per entry either way, the type and state bytes are two more, and
+        // only a third of the entries lie within r_react.
         const uint4 pj = P[j];
         const float ex = __int2float_rn(pdiff(pj.x, pi.x)) * S.scale[0];
         const float ey = __int2float_rn(pdiff(pj.y, pi.y)) * S.scale[1];
         const float ez = __int2float_rn(pdiff(pj.z, pi.z)) * S.scale[2];
         const float r2f = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
         if (!(r2f < R.rr2_pre)) continue;
+        if (!in_window(R.mask_T, R.t_lo, R.t_hi, B.type[j], B.state[j])) continue;
         // exact test, Table I step 1: d = x_T - x_A under the minimum image,
         // r^2 = fma(dz, dz, fma(dy, dy, dx dx)), strict r^2 < r_react^2.  The
         // FP32 value from the fixed-point positions is within a known bound
@@ -202,19 +230,18 @@ __device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long l
         bool bonded = false;
         for (uint32_t b = 0; b < nb; ++b) bonded |= (B.adj[(size_t)i * S.cap + b] & SLOT_MASK) == j;
         if (bonded) continue;
-        ++ncand;
-        const uint32_t idj = B.id[j];
-        // step 2: retained when u < k dt Theta (Eq. 4)
-        const uint4 wa = keyed_draw(S.seed, step, idi, idj, TAG_ACCEPT);
-        if (!u53_below(wa.x, wa.y, R.p53)) continue;
-        ++nret;
-        // step 5: one T per A, uniformly at random
-        const unsigned long long key = key64(keyed_draw(S.seed, step, idi, idj, TAG_SEL_A));
-        if (best == NONE || key < bestkey || (key == bestkey && idj < bestid)) {
-          best = j;
-          bestkey = key;
-          bestid = idj;
+        if (k < 64) {
+          mask |= 1ull << k;
+        } else {  // beyond 64 list entries (very dense systems): draw at once
+          ++ncand;
+          rx_accept_and_key(S, B, step, idi, j, R.p53, nret, best, bestkey, bestid);
         }
+      }
+      while (mask) {
+        const int k = __ffsll((long long)mask) - 1;
+        mask &= mask - 1ull;
+        ++ncand;
+        rx_accept_and_key(S, B, step, idi, nl_get_rx<NL16>(S, k, i), R.p53, nret, best, bestkey, bestid);
       }
     }
     S.win[i] = best;
