@@ -210,6 +210,19 @@ int prx_get_types(prx_system* sys, uint8_t* out /* [n] by id */);
  * PRX_ECAPACITY if cap is smaller (out then holds the first cap). */
 int prx_get_bonds(prx_system* sys, prx_bond* out, uint64_t cap, uint64_t* n_out);
 int prx_get_observables(prx_system* sys, prx_observables* out);
+
+/* Pipelined observables (the populations of Secs. V-VI, bonds, kinetic
+ * energy, momentum) for monitoring a running system without stalling it.
+ * prx_observables_begin enqueues their computation and the copy into pinned
+ * host slot `slot` (0..PRX_OBS_SLOTS-1) on the system's stream and returns
+ * at once; runs enqueued afterwards proceed on the device meanwhile.
+ * prx_observables_end waits for that slot and fills *out with the values as
+ * of the begin call.  PRX_EINVAL for a slot out of range or one without a
+ * pending begin; a device error status is reported by the end call.  Not
+ * allowed for batch members (the batch owns their stream). */
+#define PRX_OBS_SLOTS 4
+int prx_observables_begin(prx_system* sys, int slot);
+int prx_observables_end(prx_system* sys, int slot, prx_observables* out);
 /* The last min(cap, recorded) per-reaction records, oldest first.  The
  * device keeps the most recent `history_cap` records (default 8192). */
 int prx_get_history(prx_system* sys, prx_history_record* out, uint64_t cap, uint64_t* n_out);

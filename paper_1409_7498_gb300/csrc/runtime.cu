@@ -47,6 +47,13 @@ struct prx_system {
   cudaStream_t cap = nullptr;
   Sys S{};
   Ctl* ctl_host = nullptr;  // pinned mirror for read-back
+  struct ObsHost {          // pinned read-back of the observables
+    double sums[4];         // kinetic energy / 2, momentum
+    HistRec rec;            // populations
+    Ctl ctl;                // step, bonds, status
+  }* obs_host = nullptr;    // PRX_OBS_SLOTS pipelined slots + one for the synchronous call
+  cudaEvent_t obs_ev[PRX_OBS_SLOTS] = {};
+  bool obs_pending[PRX_OBS_SLOTS] = {};
   std::vector<void*> dev_allocs;
   std::vector<void*> grid_allocs;
   double grid_rcut = 0.0;
@@ -528,6 +535,8 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
     return bail(fail(sys, PRX_ECUDA, "capture stream creation failed"));
   if (cudaMallocHost(&sys->ctl_host, sizeof(Ctl)) != cudaSuccess)
     return bail(fail(sys, PRX_ENOMEM, "pinned control block"));
+  if (cudaMallocHost(&sys->obs_host, sizeof(*sys->obs_host) * (PRX_OBS_SLOTS + 1)) != cudaSuccess)
+    return bail(fail(sys, PRX_ENOMEM, "pinned observables block"));
   memset(sys->ctl_host, 0, sizeof(Ctl));
 
   auto& L = sys->dev_allocs;
@@ -908,6 +917,9 @@ void prx_destroy(prx_system* sys) {
   free_list(sys->grid_allocs);
   free_list(sys->dev_allocs);
   if (sys->ctl_host) cudaFreeHost(sys->ctl_host);
+  if (sys->obs_host) cudaFreeHost(sys->obs_host);
+  for (cudaEvent_t& e : sys->obs_ev)
+    if (e) cudaEventDestroy(e);
   if (sys->cap) cudaStreamDestroy(sys->cap);
   if (sys->own_stream && sys->stream) cudaStreamDestroy(sys->stream);
   delete sys;
@@ -1138,31 +1150,71 @@ int prx_get_bonds(prx_system* sys, prx_bond* out, uint64_t cap, uint64_t* n_out)
   return cap < nb ? fail(sys, PRX_ECAPACITY, "bond buffer too small") : PRX_OK;
 }
 
-int prx_get_observables(prx_system* sys, prx_observables* out) {
-  if (!sys || !out) return PRX_EINVAL;
-  memset(out, 0, sizeof(*out));
+// Enqueues the observables and their copy into pinned slot q (no wait).
+int enqueue_observables(prx_system* sys, int q) {
   const uint32_t n = sys->S.n;
   const int nblk = (int)((n + RX_THREADS - 1) / RX_THREADS);
+  auto* oh = sys->obs_host + q;
   if (n) {
     launch_observables(sys->S, sys->stream, nblk);
-    sys->other_launches += 2;
+    sys->other_launches += 3;
     CK(cudaGetLastError());
-    std::vector<double> red(4 * (size_t)nblk);
-    HistRec rec;
-    CK(cudaMemcpyAsync(red.data(), sys->S.red, sizeof(double) * red.size(), cudaMemcpyDeviceToHost, sys->stream));
-    CK(cudaMemcpyAsync(&rec, &sys->S.hist[sys->S.hist_cap], sizeof(HistRec), cudaMemcpyDeviceToHost, sys->stream));
-    CK(cudaStreamSynchronize(sys->stream));
-    for (int b = 0; b < nblk; ++b) {
-      out->ke_half += red[4 * b];
-      for (int k = 0; k < 3; ++k) out->momentum[k] += red[4 * b + 1 + k];
-    }
-    for (int t = 0; t < PRX_MAX_TYPES; ++t)
-      for (int s = 0; s < PRX_MAX_STATES; ++s) out->counts[t][s] = rec.counts[t][s];
+    CK(cudaMemcpyAsync(oh->sums, sys->S.red + 4 * (size_t)nblk, sizeof(oh->sums), cudaMemcpyDeviceToHost,
+                       sys->stream));
+    CK(cudaMemcpyAsync(&oh->rec, &sys->S.hist[sys->S.hist_cap], sizeof(HistRec), cudaMemcpyDeviceToHost,
+                       sys->stream));
   }
-  int rc = sync_status(sys);
-  out->step = (int64_t)sys->ctl_host->step;
-  out->bonds = (int64_t)sys->ctl_host->nbonds;
-  return rc;
+  CK(cudaMemcpyAsync(&oh->ctl, sys->S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, sys->stream));
+  return PRX_OK;
+}
+
+// Fills *out from pinned slot q (its copies complete).
+int fill_observables(prx_system* sys, int q, prx_observables* out) {
+  const auto* oh = sys->obs_host + q;
+  memset(out, 0, sizeof(*out));
+  if (sys->S.n) {
+    out->ke_half = oh->sums[0];
+    for (int k = 0; k < 3; ++k) out->momentum[k] = oh->sums[1 + k];
+    for (int t = 0; t < PRX_MAX_TYPES; ++t)
+      for (int s = 0; s < PRX_MAX_STATES; ++s) out->counts[t][s] = oh->rec.counts[t][s];
+  }
+  out->step = (int64_t)oh->ctl.step;
+  out->bonds = (int64_t)oh->ctl.nbonds;
+  *sys->ctl_host = oh->ctl;
+  const int st = oh->ctl.status;
+  if (st) return fail(sys, st, std::string("device reported ") + prx_status_string(st));
+  return PRX_OK;
+}
+
+int prx_get_observables(prx_system* sys, prx_observables* out) {
+  if (!sys || !out) return PRX_EINVAL;
+  int rc = enqueue_observables(sys, PRX_OBS_SLOTS);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(sys->stream));  // one wait for sums, populations and control block
+  return fill_observables(sys, PRX_OBS_SLOTS, out);
+}
+
+int prx_observables_begin(prx_system* sys, int slot) {
+  if (!sys) return PRX_EINVAL;
+  if (sys->batch) return refuse_member(sys);
+  if (slot < 0 || slot >= PRX_OBS_SLOTS) return fail(sys, PRX_EINVAL, "observables slot out of range");
+  if (sys->obs_pending[slot]) return fail(sys, PRX_EINVAL, "observables slot still pending");
+  if (!sys->obs_ev[slot] && cudaEventCreateWithFlags(&sys->obs_ev[slot], cudaEventDisableTiming) != cudaSuccess)
+    return fail(sys, PRX_ECUDA, "event creation failed");
+  int rc = enqueue_observables(sys, slot);
+  if (rc) return rc;
+  CK(cudaEventRecord(sys->obs_ev[slot], sys->stream));
+  sys->obs_pending[slot] = true;
+  return PRX_OK;
+}
+
+int prx_observables_end(prx_system* sys, int slot, prx_observables* out) {
+  if (!sys || !out) return PRX_EINVAL;
+  if (slot < 0 || slot >= PRX_OBS_SLOTS || !sys->obs_pending[slot])
+    return fail(sys, PRX_EINVAL, "no pending observables in this slot");
+  sys->obs_pending[slot] = false;
+  CK(cudaEventSynchronize(sys->obs_ev[slot]));
+  return fill_observables(sys, slot, out);
 }
 
 int prx_get_history(prx_system* sys, prx_history_record* out, uint64_t cap, uint64_t* n_out) {

@@ -566,6 +566,23 @@ __global__ void __launch_bounds__(RX_THREADS) k_obs_sums(Sys S, double mass) {
   if (threadIdx.x < 4) S.red[4 * (size_t)blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
 }
 
+// The per-block sums reduced to one value each, in a fixed order (thread t
+// adds blocks t, t + 256, ...; then a fixed tree): red[4 nblk .. 4 nblk + 3].
+__global__ void __launch_bounds__(RX_THREADS) k_obs_final(Sys S, uint32_t nblk) {
+  __shared__ double part[4][RX_THREADS];
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (uint32_t b = threadIdx.x; b < nblk; b += blockDim.x)
+    for (int q = 0; q < 4; ++q) a[q] += S.red[4 * (size_t)b + q];
+  for (int q = 0; q < 4; ++q) part[q][threadIdx.x] = a[q];
+  __syncthreads();
+  for (int w = RX_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 4; ++q) part[q][threadIdx.x] += part[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) S.red[4 * (size_t)nblk + threadIdx.x] = part[threadIdx.x][0];
+}
+
 // Batched reaction steps clear each member's counters in a kernel.
 __global__ void kb_rx_begin(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
   const Sys& S = T[M[blockIdx.x].sys];
@@ -679,11 +696,12 @@ void launch_pair_hist(const Sys& S, cudaStream_t st, const PairClass& a, const P
 }
 
 // On-demand observables: the spare history slot (index hist_cap) receives the
-// populations; S.red the per-block sums.
+// populations; S.red the per-block sums and, after them, their totals.
 void launch_observables(const Sys& S, cudaStream_t st, int nblocks) {
   cudaMemsetAsync(&S.hist[S.hist_cap], 0, sizeof(HistRec), st);
   k_obs_hist<<<nblocks, RX_THREADS, 0, st>>>(S, -1, 0);
   k_obs_sums<<<nblocks, RX_THREADS, 0, st>>>(S, S.mass);
+  k_obs_final<<<1, RX_THREADS, 0, st>>>(S, (uint32_t)nblocks);
 }
 
 int batch_rx_kernel_count() { return 8; }

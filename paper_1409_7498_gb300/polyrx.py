@@ -21,6 +21,7 @@ PRX_BOND_FENE, PRX_BOND_MIRROR_LJ = 0, 1
 PRX_SELECT_RANDOM, PRX_SELECT_NEAREST = 0, 1
 PRX_FORCE_FP32, PRX_FORCE_FP64 = 0, 1
 PRX_MAX_TYPES, PRX_MAX_STATES, PRX_MAX_ADJ = 8, 16, 8
+PRX_OBS_SLOTS = 4  # pinned slots of the pipelined observables
 
 
 class PolyrxError(RuntimeError):
@@ -118,6 +119,8 @@ def lib():
         "prx_get_types": ([VP, VP], I),
         "prx_get_bonds": ([VP, VP, U64, P(U64)], I),
         "prx_get_observables": ([VP, P(prx_observables)], I),
+        "prx_observables_begin": ([VP, I], I),
+        "prx_observables_end": ([VP, I, P(prx_observables)], I),
         "prx_get_history": ([VP, VP, U64, P(U64)], I),
         "prx_get_stats": ([VP, P(prx_stats)], I),
         "prx_save": ([VP, C.c_char_p], I),
@@ -277,12 +280,26 @@ def prx_get_bonds(h):
     return out
 
 
+def prx_observables_begin(h, slot: int):
+    _check(lib().prx_observables_begin(h, int(slot)), h)
+
+
+def prx_observables_end(h, slot: int) -> dict:
+    o = prx_observables()
+    _check(lib().prx_observables_end(h, int(slot), C.byref(o)), h)
+    return _obs_dict(o)
+
+
 def prx_get_observables(h) -> dict:
     o = prx_observables()
     _check(lib().prx_get_observables(h, C.byref(o)), h)
+    return _obs_dict(o)
+
+
+def _obs_dict(o) -> dict:
     return dict(step=o.step, bonds=o.bonds,
-                counts=np.array([[o.counts[t][s] for s in range(16)] for t in range(8)], np.int64),
-                ke_half=o.ke_half, momentum=np.array(list(o.momentum)))
+                counts=np.ctypeslib.as_array(o.counts).astype(np.int64),
+                ke_half=o.ke_half, momentum=np.ctypeslib.as_array(o.momentum).copy())
 
 
 def prx_get_history(h, cap: int = 1 << 20):
@@ -537,6 +554,14 @@ class System:
 
     def observables(self):
         return prx_get_observables(self.h)
+
+    def observables_begin(self, slot: int):
+        """Enqueues the observables into pinned slot `slot` (no wait)."""
+        prx_observables_begin(self.h, slot)
+
+    def observables_end(self, slot: int) -> dict:
+        """Waits for slot `slot` and returns its observables."""
+        return prx_observables_end(self.h, slot)
 
     def history(self):
         return prx_get_history(self.h)

@@ -362,6 +362,46 @@ def test_observables_and_history_consistent(P):
     assert ob["bonds"] == (4 - st[A]).sum()
 
 
+def test_pipelined_observables_match_the_synchronous_read(P):
+    """prx_observables_begin/end return, for each slot, exactly what the
+    synchronous read returns at the same step, while later runs proceed."""
+    seed = 29
+    inp = synth.step_growth_sites(5003, 4, seed)
+    sch = synth.step_growth_scheme(4, k=0.3)
+
+    def make():
+        g = gpu_system(P, inp.L, inp.x, inp.v, inp.type, inp.state, cap=4, seed=seed)
+        g.set_reaction(gpu_reaction(P, sch))
+        return g
+
+    with make() as g:
+        g.run(100)
+        ref0 = g.observables()
+        g.run(100)
+        ref1 = g.observables()
+    with make() as g:
+        g.run(100)
+        g.observables_begin(0)
+        g.run(100)
+        g.observables_begin(1)
+        with pytest.raises(P.PolyrxError) as e:
+            g.observables_begin(1)  # still pending
+        assert e.value.code == P.PRX_EINVAL
+        got0 = g.observables_end(0)
+        got1 = g.observables_end(1)
+        for bad in (lambda: g.observables_end(0), lambda: g.observables_begin(P.PRX_OBS_SLOTS),
+                    lambda: g.observables_begin(-1)):
+            with pytest.raises(P.PolyrxError) as e:
+                bad()
+            assert e.value.code == P.PRX_EINVAL
+    for got, ref in ((got0, ref0), (got1, ref1)):
+        assert got["step"] == ref["step"] and got["bonds"] == ref["bonds"]
+        assert (got["counts"] == ref["counts"]).all()
+        assert got["ke_half"] == ref["ke_half"]
+        assert (got["momentum"] == ref["momentum"]).all()
+    assert got0["step"] == 100 and got1["step"] == 200 and got1["bonds"] > got0["bonds"]
+
+
 def test_ragged_sizes_profile_and_launch_counts(P):
     for n in (1, 2, 127, 128, 129, 4097):
         L = max(4.4, synth.box_edge(n))
