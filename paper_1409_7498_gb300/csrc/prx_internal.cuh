@@ -14,9 +14,11 @@
 //                    for the displacement trigger); double-buffered across
 //                    steps (neighbours read the old copy while the new one is
 //                    written)
-//   nl  : Verlet neighbour list, column-major [list_cap][n], entries are the
-//         neighbour's slot relative to the owner's (mod n, 16-bit when every
-//         offset fits, else 32-bit); nn : u8[n] entry counts
+//   nl  : Verlet neighbour list, column-major [list_cap][n] (list_cap a
+//         multiple of 4), entries are the neighbours' slots (16-bit up to
+//         65,535 particles, else 32-bit), each list padded with the owner's
+//         own slot to a whole stage of four; nn : u8[n] entry counts
+//         (without the padding)
 //   cell_start : u32[ncell+1]  CSR offsets of the cells (z-major), valid at
 //         the last rebuild; used only to build the lists
 // A device control block (Ctl) holds the current set / buffer phase, the
@@ -130,7 +132,7 @@ struct Sys {
   uint8_t* nn;
   int nl16;                       // 1: 16-bit entries
   int list_cap;
-  float rv2_build;                // (r_c + skin + margin)^2, list build test
+  float rv2_build;                // (r_c + skin + rounding margin)^2, list build test (FP32)
   // list-build tiling (cells of edge >= r_c + skin)
   int tile_y, tiles_y, tile_threads, tile_cap;
   // physics (FP32 and FP64 copies)
