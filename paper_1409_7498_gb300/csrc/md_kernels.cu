@@ -323,7 +323,8 @@ __global__ void __launch_bounds__(256, 6)
 // Members of a batch may differ in list width: the branch is uniform per block.
 __global__ void __launch_bounds__(256, 4)
     kb_step_nl(const Sys* __restrict__ T, const BlkMap* __restrict__ M,
-               cudaGraphConditionalHandle cond, int use_cond) {
+               cudaGraphConditionalHandle cond, int use_cond, uint32_t* __restrict__ act_n) {
+  if (blockIdx.x == 0 && threadIdx.x < 5) act_n[threadIdx.x] = 0u;  // for this step's rebuild plan
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
   if (S.cubic) {
@@ -474,7 +475,8 @@ __global__ void k_rebin_keys_x(Sys S) {
   S.key[i] = k;
   atomicAdd(&S.count[k], 1u);
 }
-__global__ void kb_rebin_keys(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+__global__ void kb_rebin_keys(const Sys* __restrict__ T, const BlkMap* __restrict__ M, const uint32_t* __restrict__ C) {
+  if (blockIdx.x >= *C) return;  // compacted map: members that rebuild
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
   if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
@@ -510,7 +512,8 @@ __device__ __forceinline__ void scan_tiles_body(const Sys& S, const Blk blk) {
   if (threadIdx.x == 0) S.blk_off[blk.b] = red[0];
 }
 __global__ void k_scan_tiles(Sys S) { scan_tiles_body(S, Blk{blockIdx.x, gridDim.x}); }
-__global__ void kb_scan_tiles(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+__global__ void kb_scan_tiles(const Sys* __restrict__ T, const BlkMap* __restrict__ M, const uint32_t* __restrict__ C) {
+  if (blockIdx.x >= *C) return;
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
   if (!S.ctl->rebin_flag) return;
@@ -559,7 +562,8 @@ __device__ __forceinline__ void scan_top_body(const Sys& S) {
   }
 }
 __global__ void k_scan_top(Sys S) { scan_top_body(S); }
-__global__ void kb_scan_top(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+__global__ void kb_scan_top(const Sys* __restrict__ T, const BlkMap* __restrict__ M, const uint32_t* __restrict__ C) {
+  if (blockIdx.x >= *C) return;
   const Sys& S = T[M[blockIdx.x].sys];
   if (!S.ctl->rebin_flag) return;
   scan_top_body(S);
@@ -615,7 +619,8 @@ __device__ __forceinline__ void scan_down_self_body(const Sys& S, const Blk blk)
 }
 __global__ void k_scan_down(Sys S) { scan_down_body(S, Blk{blockIdx.x, gridDim.x}); }
 __global__ void k_scan_down_self(Sys S) { scan_down_self_body(S, Blk{blockIdx.x, gridDim.x}); }
-__global__ void kb_scan_down(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+__global__ void kb_scan_down(const Sys* __restrict__ T, const BlkMap* __restrict__ M, const uint32_t* __restrict__ C) {
+  if (blockIdx.x >= *C) return;
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
   if (!S.ctl->rebin_flag) return;
@@ -623,7 +628,8 @@ __global__ void kb_scan_down(const Sys* __restrict__ T, const BlkMap* __restrict
 }
 
 // Batched rebuilds clear the cell counters in a kernel (a single system uses memsets).
-__global__ void kb_rebin_clear(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+__global__ void kb_rebin_clear(const Sys* __restrict__ T, const BlkMap* __restrict__ M, const uint32_t* __restrict__ C) {
+  if (blockIdx.x >= *C) return;
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
   if (!S.ctl->rebin_flag) return;
@@ -643,7 +649,8 @@ __device__ __forceinline__ void rebin_scatter_body(const Sys& S, const Blk blk) 
 }
 
 __global__ void k_rebin_scatter(Sys S) { rebin_scatter_body(S, Blk{blockIdx.x, gridDim.x}); }
-__global__ void kb_rebin_scatter(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+__global__ void kb_rebin_scatter(const Sys* __restrict__ T, const BlkMap* __restrict__ M, const uint32_t* __restrict__ C) {
+  if (blockIdx.x >= *C) return;
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
   if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
@@ -697,7 +704,8 @@ __device__ __forceinline__ void rebin_cellsort_body(const Sys& S, const Blk blk)
 }
 
 __global__ void k_rebin_cellsort(Sys S) { rebin_cellsort_body(S, Blk{blockIdx.x, gridDim.x}); }
-__global__ void kb_rebin_cellsort(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+__global__ void kb_rebin_cellsort(const Sys* __restrict__ T, const BlkMap* __restrict__ M, const uint32_t* __restrict__ C) {
+  if (blockIdx.x >= *C) return;
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
   if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
@@ -752,7 +760,8 @@ __device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk, 
 __global__ void k_rebin_permute(Sys S, int wrap) {
   rebin_permute_body(S, Blk{blockIdx.x, gridDim.x}, wrap != 0);
 }
-__global__ void kb_rebin_permute(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+__global__ void kb_rebin_permute(const Sys* __restrict__ T, const BlkMap* __restrict__ M, const uint32_t* __restrict__ C) {
+  if (blockIdx.x >= *C) return;
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
   if (!S.ctl->rebin_flag) return;  // this member needs no rebuild
@@ -1031,8 +1040,9 @@ __global__ void __launch_bounds__(256) k_build_nlist(Sys S) {
   build_nlist_body<NL16>(S, Blk{blockIdx.x, gridDim.x}, smem_b);
 }
 __global__ void __launch_bounds__(256)
-    kb_build_nlist(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+    kb_build_nlist(const Sys* __restrict__ T, const BlkMap* __restrict__ M, const uint32_t* __restrict__ C) {
   extern __shared__ __align__(16) unsigned char smem_b[];
+  if (blockIdx.x >= *C) return;
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
   if (!S.ctl->rebin_flag) return;
@@ -1041,6 +1051,34 @@ __global__ void __launch_bounds__(256)
 }
 
 inline unsigned blocks_for(uint64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Rebuild plan of a batch: the entries of the five block maps (stored one
+// after the other: part, cell, tile, one, build) that belong to members
+// whose rebuild flag is set, compacted into `act` at the same family offsets,
+// with their counts in act_n.  The lanes of a warp that append to the same
+// family reserve their places with one atomic; the order of the compacted
+// entries does not matter (every block's work depends only on its entry).
+__global__ void kb_rebuild_plan(const Sys* __restrict__ T, const BlkMap* __restrict__ maps,
+                                uint4 off, uint32_t n_all, BlkMap* __restrict__ act,
+                                uint32_t* __restrict__ act_n) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  int fam = -1;
+  BlkMap m{};
+  if (e < n_all) {
+    m = maps[e];
+    if (T[m.sys].ctl->rebin_flag)
+      fam = e < off.x ? 0 : e < off.y ? 1 : e < off.z ? 2 : e < off.w ? 3 : 4;
+  }
+  const unsigned grp = __match_any_sync(0xFFFFFFFFu, fam);
+  const int lane = threadIdx.x & 31, lead = __ffs(grp) - 1;
+  uint32_t base = 0u;
+  if (fam >= 0 && lane == lead) base = atomicAdd(&act_n[fam], (uint32_t)__popc(grp));
+  base = __shfl_sync(0xFFFFFFFFu, base, lead);
+  if (fam >= 0) {
+    const uint32_t start = fam == 0 ? 0u : fam == 1 ? off.x : fam == 2 ? off.y : fam == 3 ? off.z : off.w;
+    act[start + base + __popc(grp & ((1u << lane) - 1u))] = m;
+  }
+}
 
 // Input staging for a plain creation (slot = particle index).  Positions are
 // wrapped by at most one box edge (v >= L: v - L; v < 0: v + L, FP64), the
@@ -1206,24 +1244,32 @@ void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, c
 
 void launch_batch_step(const BatchLaunch& L, cudaStream_t st, cudaGraphConditionalHandle h,
                        int use_cond) {
-  kb_step_nl<<<L.n_part, 256, 0, st>>>(L.T, L.part, h, use_cond);
+  kb_step_nl<<<L.n_part, 256, 0, st>>>(L.T, L.part, h, use_cond, L.act_n);
 }
 
-// The rebuild pipeline over every member; members whose flag is clear
-// return at once from each kernel.
+// The rebuild pipeline over the members whose flag is set: a plan kernel
+// compacts their blocks, then every kernel runs the full grid of its family,
+// its blocks beyond the compacted count returning at once.
 void launch_batch_rebuild(const BatchLaunch& L, cudaStream_t st) {
-  kb_rebin_clear<<<L.n_cell, 256, 0, st>>>(L.T, L.cell);
-  kb_rebin_keys<<<L.n_part, 256, 0, st>>>(L.T, L.part);
-  kb_scan_tiles<<<L.n_tile, 256, 0, st>>>(L.T, L.tile);
-  kb_scan_top<<<L.n_one, 256, 0, st>>>(L.T, L.one);
-  kb_scan_down<<<L.n_tile, 256, 0, st>>>(L.T, L.tile);
-  kb_rebin_scatter<<<L.n_part, 256, 0, st>>>(L.T, L.part);
-  kb_rebin_cellsort<<<L.n_cell, 256, 0, st>>>(L.T, L.cell);
-  kb_rebin_permute<<<L.n_part, 256, 0, st>>>(L.T, L.part);
-  kb_build_nlist<<<L.n_build, L.build_threads, L.build_smem, st>>>(L.T, L.build);
+  const uint32_t o1 = L.n_part, o2 = o1 + L.n_cell, o3 = o2 + L.n_tile, o4 = o3 + L.n_one;
+  const uint32_t n_all = o4 + L.n_build;
+  kb_rebuild_plan<<<blocks_for(n_all, 256), 256, 0, st>>>(L.T, L.part, make_uint4(o1, o2, o3, o4), n_all,
+                                                           L.act, L.act_n);
+  const BlkMap *part = L.act, *cell = L.act + o1, *tile = L.act + o2, *one = L.act + o3, *build = L.act + o4;
+  const uint32_t *c_part = L.act_n, *c_cell = L.act_n + 1, *c_tile = L.act_n + 2, *c_one = L.act_n + 3,
+                 *c_build = L.act_n + 4;
+  kb_rebin_clear<<<L.n_cell, 256, 0, st>>>(L.T, cell, c_cell);
+  kb_rebin_keys<<<L.n_part, 256, 0, st>>>(L.T, part, c_part);
+  kb_scan_tiles<<<L.n_tile, 256, 0, st>>>(L.T, tile, c_tile);
+  kb_scan_top<<<L.n_one, 256, 0, st>>>(L.T, one, c_one);
+  kb_scan_down<<<L.n_tile, 256, 0, st>>>(L.T, tile, c_tile);
+  kb_rebin_scatter<<<L.n_part, 256, 0, st>>>(L.T, part, c_part);
+  kb_rebin_cellsort<<<L.n_cell, 256, 0, st>>>(L.T, cell, c_cell);
+  kb_rebin_permute<<<L.n_part, 256, 0, st>>>(L.T, part, c_part);
+  kb_build_nlist<<<L.n_build, L.build_threads, L.build_smem, st>>>(L.T, build, c_build);
 }
 
-int batch_rebuild_kernel_count() { return 9; }
+int batch_rebuild_kernel_count() { return 10; }
 
 int configure_batch_build_kernel(size_t smem_bytes) { return raise_smem_limit(1, smem_bytes); }
 

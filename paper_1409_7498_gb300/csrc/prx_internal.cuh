@@ -329,6 +329,11 @@ struct BatchLaunch {
   unsigned n_part, n_cell, n_tile, n_one, n_build;
   int build_threads;
   size_t build_smem;
+  // rebuild work of the members whose flag is set, compacted each rebuild
+  // step: the same five families (part, cell, tile, one, build) at the same
+  // offsets as the full maps, and their entry counts (zeroed by the step)
+  BlkMap* act;
+  uint32_t* act_n;
 };
 
 // ---- host-side launchers (defined in the kernel translation units) ----------

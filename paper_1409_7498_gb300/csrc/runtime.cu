@@ -86,8 +86,9 @@ struct prx_batch {
   BatchCtl* bctl_host = nullptr;
   Sys* T = nullptr;
   size_t T_cap = 0;
-  BlkMap* maps = nullptr;
+  BlkMap* maps = nullptr;    // the block maps, then as many entries for their compaction
   size_t maps_cap = 0;
+  uint32_t* act_n = nullptr;  // compacted counts of the rebuild plan
   BatchLaunch L{};
   uint32_t n_active = 0;
   bool any_rx = false;
@@ -800,13 +801,15 @@ int batch_prepare(prx_batch* b) {
     CKB(cudaMalloc(&b->T, sizeof(Sys) * b->n_active));
     b->T_cap = b->n_active;
   }
-  if (nmaps > b->maps_cap) {
+  if (2 * nmaps > b->maps_cap) {
     if (b->maps) cudaFree(b->maps);
     b->maps = nullptr;
     b->maps_cap = 0;
-    CKB(cudaMalloc(&b->maps, sizeof(BlkMap) * nmaps));
-    b->maps_cap = nmaps;
+    CKB(cudaMalloc(&b->maps, sizeof(BlkMap) * 2 * nmaps));
+    b->maps_cap = 2 * nmaps;
   }
+  if (!b->act_n) CKB(cudaMalloc(&b->act_n, sizeof(uint32_t) * 8));
+  CKB(cudaMemset(b->act_n, 0, sizeof(uint32_t) * 8));
   std::vector<BlkMap> all;
   all.reserve(nmaps);
   BatchLaunch& L = b->L;
@@ -823,6 +826,8 @@ int batch_prepare(prx_batch* b) {
   place(build, &L.build, &L.n_build);
   L.build_threads = build_threads;
   L.build_smem = build_smem;
+  L.act = b->maps + nmaps;
+  L.act_n = b->act_n;
   CKB(cudaMemcpy(b->T, table.data(), sizeof(Sys) * table.size(), cudaMemcpyHostToDevice));
   CKB(cudaMemcpy(b->maps, all.data(), sizeof(BlkMap) * all.size(), cudaMemcpyHostToDevice));
   if (configure_batch_build_kernel(build_smem))
@@ -1585,6 +1590,7 @@ void prx_batch_destroy(prx_batch* b) {
   batch_destroy_graphs(b);
   if (b->T) cudaFree(b->T);
   if (b->maps) cudaFree(b->maps);
+  if (b->act_n) cudaFree(b->act_n);
   if (b->bctl) cudaFree(b->bctl);
   if (b->bctl_host) cudaFreeHost(b->bctl_host);
   if (b->cap) cudaStreamDestroy(b->cap);
