@@ -92,7 +92,7 @@ struct RxParams {
   uint32_t mask_A, mask_T;
   int32_t a_lo, a_hi, t_lo, t_hi, dA, dT;
   double p;         // k dt Theta
-  uint64_t p53;     // ceil(p 2^53) (2^53 when p >= 1): u53 < p as an integer test
+  uint64_t p53;     // ceil(p 2^53) (2^53 when p >= 1): u < p as an integer test
   double rr2;       // r_react^2 (exact test)
   float rr2_pre;    // (r_react + margin)^2 (FP32 prefilter, always conservative)
   float rr2_in;     // r_react^2 minus twice the FP32 error bound: inside for sure
@@ -214,12 +214,9 @@ inline uint64_t p53_of(double p) {
   if (!(p > 0.0)) return 0ull;
   return (uint64_t)std::ceil(std::ldexp(p, 53));
 }
-__device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
-  unsigned long long w = ((unsigned long long)hi << 32) | lo;
-  return __dmul_rn(__ull2double_rn(w >> 11), 0x1.0p-53);
-}
-// u53(hi, lo) < p, decided on the integer pipe: u53 = m 2^-53 with the
-// integer m = w >> 11, and m 2^-53 < p exactly when m < ceil(p 2^53).
+// u < p for the uniform u = m 2^-53 in [0, 1) of a draw, m = the top 53 bits
+// of the 64-bit word w = hi:lo (m = w >> 11), decided on the integer pipe:
+// m 2^-53 < p exactly when m < ceil(p 2^53).
 __device__ __forceinline__ bool u53_below(uint32_t hi, uint32_t lo, uint64_t p53) {
   return ((((unsigned long long)hi << 32) | lo) >> 11) < p53;
 }
