@@ -1,14 +1,20 @@
-"""Integer forms of FP64 decisions used on the GPU, checked against the FP64
-definitions on the CPU (no GPU).
+"""Integer and FP32 forms of FP64 decisions used on the GPU, checked against
+the FP64 definitions on the CPU (no GPU).
 
-The acceptance test of Eq. 4 draws u = m 2^-53 with m the top 53 bits of a
-64-bit Philox word; the GPU compares m < ceil(p 2^53) instead of u < p in
-FP64.  The two decisions agree for every m and every double p: m 2^-53 is
-exact, p 2^53 is exact (scaling by a power of two), and for an integer m,
-m < x exactly when m < ceil(x).  Checked here on random words, on words next
-to the threshold and on edge values of p.
+1. The acceptance test of Eq. 4 draws u = m 2^-53 with m the top 53 bits of
+   a 64-bit Philox word; the GPU compares m < ceil(p 2^53) instead of u < p
+   in FP64.  The two agree for every m and every double p: m 2^-53 is exact,
+   p 2^53 is exact (scaling by a power of two), and for an integer m,
+   m < x exactly when m < ceil(x).
+2. The reaction search decides the distance test (Table I step 1, strict
+   r^2 < r_react^2 in FP64 under the minimum image) from an FP32 r^2 of the
+   fixed-point positions when that value is clearly inside (below rr2_in),
+   and drops pairs whose FP32 r^2 is not below rr2_pre.  Neither shortcut may
+   disagree with the FP64 decision; the bound behind rr2_in is checked on
+   pairs placed at the cutoff in boxes from 10 to 1,000 sigma.
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 
@@ -37,3 +43,91 @@ def test_integer_acceptance_equals_fp64_comparison():
         ms += [m for m in (t - 2, t - 1, t, t + 1, 0, (1 << 53) - 1) if 0 <= m < (1 << 53)]
         for m in ms:
             assert (m < t) == fp64_decision(m, p), (p, m, t)
+
+
+# --- fixed-point positions and the FP32 r^2, as the library computes them ---
+def fixed_point_constants(L: float):
+    """Lfx = round(L 2^32), M64 = round(2^64 / L) (the library's rounding of
+    these constants may differ by one unit; the bound has room for it)."""
+    return round(L * 2.0 ** 32), int(Fraction(2 ** 64) / Fraction(L) + Fraction(1, 2))
+
+
+def periodic_fx(x: float, Lfx: int, M64: int) -> int:
+    """X = (trunc(x 2^32) + Lfx) M64 / 2^64 mod 2^32 (x 2^32 is exact)."""
+    a = (int(x * 2.0 ** 32) + Lfx) % (1 << 64)
+    return ((a * M64) >> 64) % (1 << 32)
+
+
+def f32(v) -> np.float32:
+    return np.float32(v)
+
+
+def fma32(a, b, c) -> np.float32:
+    # exact product of two floats in binary64, one rounding of the sum there,
+    # then to binary32 (a possible double rounding is far inside the bound)
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def r2_fp32(Xi, Xj, scales) -> np.float32:
+    """int32 difference of the fixed-point positions, rounded once to FP32,
+    times the per-axis scale L / 2^32, then fma(ez, ez, fma(ey, ey, ex ex))."""
+    e = []
+    for a, b, s in zip(Xi, Xj, scales):
+        d = (b - a) % (1 << 32)
+        d = d - (1 << 32) if d >= (1 << 31) else d
+        e.append(np.float32(np.float32(d) * s))
+    return fma32(e[2], e[2], fma32(e[1], e[1], np.float32(e[0] * e[0])))
+
+
+def r2_fp64(xi, xj, L) -> float:
+    """The FP64 test's value: d = x_j - x_i, minimum image, then
+    fma(dz, dz, fma(dy, dy, dx dx)), each operation correctly rounded."""
+    d = []
+    for a, b, l in zip(xi, xj, L):
+        v = b - a
+        if v > 0.5 * l:
+            v = v - l
+        elif v < -0.5 * l:
+            v = v + l
+        d.append(v)
+    t = d[0] * d[0]
+    t = float(Fraction(d[1]) * Fraction(d[1]) + Fraction(t))
+    return float(Fraction(d[2]) * Fraction(d[2]) + Fraction(t))
+
+
+def reaction_thresholds(r_react: float, L):
+    """rr2, rr2_pre, rr2_in and the error bound, as set_reaction sets them."""
+    rr2 = r_react * r_react
+    rr2_pre = f32((r_react + 1e-3) * (r_react + 1e-3))
+    u = max(L) / 4294967296.0
+    margin = 2.0 * math.sqrt(3.0) * r_react * (6.0 * u + 2e-7 * r_react) + 4e-7 * rr2 + 1e-9
+    rr2_in = np.nextafter(f32(max(0.0, rr2 - 2.0 * margin)), np.float32(0.0))
+    return rr2, rr2_pre, rr2_in, margin
+
+
+def test_fp32_distance_shortcuts_never_change_the_fp64_decision():
+    rng = np.random.default_rng(7498)
+    r_react = 1.1
+    worst = 0.0
+    for L in ((10.0, 10.0, 10.0), (107.24910150874837,) * 3, (699.0, 5.28, 5.28), (1000.0,) * 3):
+        rr2, rr2_pre, rr2_in, margin = reaction_thresholds(r_react, L)
+        Lfx_M = [fixed_point_constants(l) for l in L]
+        scale = [f32(l / 4294967296.0) for l in L]
+        for q in range(1500):
+            # positions anywhere, near the walls too, and up to a skin outside
+            xi = [float(rng.choice([rng.uniform(0, l), rng.uniform(-0.2, 0.2) % l,
+                                    rng.uniform(l - 0.2, l + 0.2)])) for l in L]
+            d = rng.normal(size=3)
+            r = r_react * (1.0 + float(rng.choice([rng.uniform(-1e-6, 1e-6), rng.uniform(-3e-3, 3e-3)])))
+            xj = [a + r * c / float(np.linalg.norm(d)) for a, c in zip(xi, d)]
+            Xi = [periodic_fx(a, *Lfx_M[k]) for k, a in enumerate(xi)]
+            Xj = [periodic_fx(a, *Lfx_M[k]) for k, a in enumerate(xj)]
+            r2f = float(r2_fp32(Xi, Xj, scale))
+            r2 = r2_fp64(xi, xj, L)
+            worst = max(worst, abs(r2f - r2) / margin)
+            inside = r2 < rr2
+            if r2f < rr2_in:
+                assert inside, (L, xi, xj, r2f, r2)
+            if inside:
+                assert r2f < rr2_pre, (L, xi, xj, r2f, r2)
+    assert worst < 0.5, worst  # the derived bound holds with room (measured ~0.22)
