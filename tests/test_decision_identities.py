@@ -131,3 +131,61 @@ def test_fp32_distance_shortcuts_never_change_the_fp64_decision():
             if inside:
                 assert r2f < rr2_pre, (L, xi, xj, r2f, r2)
     assert worst < 0.5, worst  # the derived bound holds with room (measured ~0.22)
+
+
+# --- the list build's FP32 tile-frame test ---------------------------------
+def build_coord(X, Y, Z, cell, row_off, img, L, nc, cy0, cz0):
+    """A bead's FP32 coordinates in a tile's frame, as the list build stages
+    them: x in [0, L) (a bead keyed to the first / last cell whose position
+    rounds to the far end is taken back), shifted by -L / +L in the left /
+    right image cell; y and z relative to the tile's lower cell edges through
+    the lower edge of the bead's (wrapped) row and that row's unwrapped
+    offset.  cell = the bead's keyed (cx, cy, cz); row_off = (uy - cy0,
+    uz - cz0) of the staged row; img = -1, 0, +1."""
+    sx, sy, sz = (f32(l / 4294967296.0) for l in L)
+    Lx = f32(L[0])
+    xf = np.float32(np.float32(X) * sx)
+    if cell[0] == 0 and X >= 1 << 31:
+        xf = np.float32(xf - Lx)
+    if cell[0] == nc[0] - 1 and X < 1 << 31:
+        xf = np.float32(xf + Lx)
+    xf = np.float32(xf + img * Lx) if img else xf
+    out = [xf]
+    for V, q, off, l, n, s in ((Y, cell[1], row_off[0], L[1], nc[1], sy), (Z, cell[2], row_off[1], L[2], nc[2], sz)):
+        ref = (q << 32) // n
+        d = (V - ref) % (1 << 32)
+        d = d - (1 << 32) if d >= (1 << 31) else d
+        out.append(fma32(np.float32(d), s, f32(off * (l / n))))
+    return out
+
+
+def test_list_build_fp32_radius_keeps_every_pair_within_the_list_radius():
+    rng = np.random.default_rng(1409)
+    rc, skin = 2.0 ** (1.0 / 6.0), 0.4
+    rv = rc + skin
+    for L in ((12.0, 12.0, 12.0), (107.24910150874837,) * 3, (699.0, 5.28, 5.28), (1000.0,) * 3):
+        nc = [int(math.floor(l / (rv * (1.0 + 1e-9)))) for l in L]
+        rvb = rv * (1.0 + 1e-5) + 1e-6 * max(L)
+        rv2_build = f32(rvb * rvb)
+        Lfx_M = [fixed_point_constants(l) for l in L]
+        for q in range(1500):
+            xi = [float(rng.uniform(0, l)) for l in L]
+            d = rng.normal(size=3)
+            r = rv * (1.0 - float(rng.choice([rng.uniform(0, 1e-6), rng.uniform(0, 3e-3)])))
+            xj = [(a + r * c / float(np.linalg.norm(d))) % l for a, c, l in zip(xi, d, L)]
+            P = [[periodic_fx(v, *Lfx_M[k]) for k, v in enumerate(x)] for x in (xi, xj)]
+            cells = [[(p[k] * nc[k]) >> 32 for k in range(3)] for p in P]
+            # the staged copy of j the tile of i's row reads: the neighbouring
+            # row offsets and, across the x wrap, the image cell
+            off = []
+            for k in (1, 2):
+                dc = cells[1][k] - cells[0][k]
+                dc = dc - nc[k] if dc > 1 else dc + nc[k] if dc < -1 else dc
+                off.append(dc)
+            dx = cells[1][0] - cells[0][0]
+            img = -1 if dx > 1 else 1 if dx < -1 else 0
+            fi = build_coord(*P[0], cells[0], (0, 0), 0, L, nc, cells[0][1], cells[0][2])
+            fj = build_coord(*P[1], cells[1], off, img, L, nc, cells[0][1], cells[0][2])
+            e = [np.float32(b - a) for a, b in zip(fi, fj)]
+            r2 = fma32(e[2], e[2], fma32(e[1], e[1], np.float32(e[0] * e[0])))
+            assert r2 < rv2_build, (L, xi, xj, float(r2), float(rv2_build))
