@@ -1119,6 +1119,35 @@ __global__ void k_stage_input(Sys S, const double* __restrict__ buf, int which) 
 
 }  // namespace
 
+// Read-back in particle order: slot s of the current set goes to index id[s]
+// of `out` (device): 0 states (i8), 1 types (u8), 2 positions wrapped once
+// into the box (the permutation's rule), [n][3], 3 velocities [n][3].
+__global__ void k_gather_by_id(Sys S, int what, void* __restrict__ out) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S.n) return;
+  const SoA B = S.ctl->set ? S.s1 : S.s0;
+  const uint32_t p = B.id[s];
+  if (what == 0) {
+    ((int8_t*)out)[p] = B.state[s];
+  } else if (what == 1) {
+    ((uint8_t*)out)[p] = B.type[s];
+  } else if (what == 2) {
+    double* o = (double*)out + 3 * (size_t)p;
+    o[0] = wrap_into_box(B.x[s], S.L[0]);
+    o[1] = wrap_into_box(B.y[s], S.L[1]);
+    o[2] = wrap_into_box(B.z[s], S.L[2]);
+  } else {
+    double* o = (double*)out + 3 * (size_t)p;
+    o[0] = B.vx[s];
+    o[1] = B.vy[s];
+    o[2] = B.vz[s];
+  }
+}
+
+void launch_gather_by_id(const Sys& S, cudaStream_t st, int what, void* out) {
+  if (S.n) k_gather_by_id<<<blocks_for(S.n, 256), 256, 0, st>>>(S, what, out);
+}
+
 void launch_stage_input(const Sys& S, cudaStream_t st, const double* buf, int which) {
   if (S.n) k_stage_input<<<blocks_for(S.n, 256), 256, 0, st>>>(S, buf, which);
 }

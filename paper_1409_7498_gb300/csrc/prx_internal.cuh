@@ -360,6 +360,9 @@ size_t build_tile_smem(const Sys& S);
 // into the box, ids and types checked) or velocities (which = 1), copied to
 // the device; errors land in ctl->input_err.
 void launch_stage_input(const Sys& S, cudaStream_t st, const double* buf, int which);
+// Per-particle arrays in particle (id) order into device buffer `out`:
+// 0 states, 1 types, 2 positions wrapped into the box, 3 velocities.
+void launch_gather_by_id(const Sys& S, cudaStream_t st, int what, void* out);
 int configure_build_kernel(size_t smem_bytes);
 
 }  // namespace prx

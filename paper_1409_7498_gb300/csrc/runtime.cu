@@ -1081,50 +1081,32 @@ int prx_get_step(prx_system* sys, uint64_t* step) {
   return rc;
 }
 
-int prx_get_positions(prx_system* sys, double* out) {
+// Per-particle read-back: arranged in particle order on the device (into
+// the force scratch buffer), then one copy into the caller's buffer.
+int readback_by_id(prx_system* sys, int what, void* out, size_t bytes) {
   if (!sys || (!out && sys->S.n)) return PRX_EINVAL;
-  HostSlots h;
-  int rc = fetch_slots(sys, h, FS_POS);
-  if (rc) return rc;
-  for (size_t s = 0; s < h.id.size(); ++s) {
-    const size_t p = h.id[s];
-    out[3 * p] = wrap_host(h.x[s], sys->d.box[0]);
-    out[3 * p + 1] = wrap_host(h.y[s], sys->d.box[1]);
-    out[3 * p + 2] = wrap_host(h.z[s], sys->d.box[2]);
+  if (sys->S.n) {
+    launch_gather_by_id(sys->S, sys->stream, what, sys->S.fout);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, sys->S.fout, bytes, cudaMemcpyDeviceToHost, sys->stream));
   }
   return sync_status(sys);
+}
+
+int prx_get_positions(prx_system* sys, double* out) {
+  return readback_by_id(sys, 2, out, sys ? 24ull * sys->S.n : 0);
 }
 
 int prx_get_velocities(prx_system* sys, double* out) {
-  if (!sys || (!out && sys->S.n)) return PRX_EINVAL;
-  HostSlots h;
-  int rc = fetch_slots(sys, h, FS_VEL);
-  if (rc) return rc;
-  for (size_t s = 0; s < h.id.size(); ++s) {
-    const size_t p = h.id[s];
-    out[3 * p] = h.vx[s];
-    out[3 * p + 1] = h.vy[s];
-    out[3 * p + 2] = h.vz[s];
-  }
-  return sync_status(sys);
+  return readback_by_id(sys, 3, out, sys ? 24ull * sys->S.n : 0);
 }
 
 int prx_get_states(prx_system* sys, int8_t* out) {
-  if (!sys || (!out && sys->S.n)) return PRX_EINVAL;
-  HostSlots h;
-  int rc = fetch_slots(sys, h, FS_STATE);
-  if (rc) return rc;
-  for (size_t s = 0; s < h.id.size(); ++s) out[h.id[s]] = h.state[s];
-  return sync_status(sys);
+  return readback_by_id(sys, 0, out, sys ? (size_t)sys->S.n : 0);
 }
 
 int prx_get_types(prx_system* sys, uint8_t* out) {
-  if (!sys || (!out && sys->S.n)) return PRX_EINVAL;
-  HostSlots h;
-  int rc = fetch_slots(sys, h, FS_TYPE);
-  if (rc) return rc;
-  for (size_t s = 0; s < h.id.size(); ++s) out[h.id[s]] = h.type[s];
-  return sync_status(sys);
+  return readback_by_id(sys, 1, out, sys ? (size_t)sys->S.n : 0);
 }
 
 int prx_get_bonds(prx_system* sys, prx_bond* out, uint64_t cap, uint64_t* n_out) {
