@@ -113,19 +113,36 @@ int fail(prx_system* s, int code, const std::string& msg) {
       return fail(sys, PRX_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
   } while (0)
 
-template <class T>
-int dalloc(prx_system* sys, std::vector<void*>& list, T** p, size_t count) {
-  void* q = nullptr;
-  size_t bytes = sizeof(T) * (count ? count : 1);
-  cudaError_t e = cudaMalloc(&q, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(sys, PRX_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+// The fixed per-system arrays, carved out of one device allocation (each
+// part aligned to 256 bytes like a cudaMalloc of its own): creation and
+// destruction then cost one allocation call each.
+struct DevArena {
+  struct Req {
+    void** p;
+    size_t bytes;
+  };
+  std::vector<Req> reqs;
+  template <class T>
+  void add(T** p, size_t count) {
+    reqs.push_back(Req{(void**)p, sizeof(T) * (count ? count : 1)});
   }
-  list.push_back(q);
-  *p = (T*)q;
-  return PRX_OK;
-}
+  int commit(prx_system* sys, std::vector<void*>& list) {
+    size_t total = 0;
+    for (const Req& r : reqs) total += (r.bytes + 255) & ~(size_t)255;
+    void* base = nullptr;
+    if (cudaMalloc(&base, total) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(sys, PRX_ENOMEM, "cudaMalloc of " + std::to_string(total) + " bytes failed");
+    }
+    list.push_back(base);
+    char* c = (char*)base;
+    for (const Req& r : reqs) {
+      *r.p = c;
+      c += (r.bytes + 255) & ~(size_t)255;
+    }
+    return PRX_OK;
+  }
+};
 
 double wca_rc(const prx_system_desc& d) { return std::pow(2.0, 1.0 / 6.0) * d.wca_sigma; }
 
@@ -222,13 +239,11 @@ int setup_grid(prx_system* sys, double rc) {
   sys->grid_rcut = rc;
   free_list(sys->grid_allocs);
   int rc2;
-  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.cell_start, (size_t)ncell + 1))) return rc2;
-  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.count, (size_t)ncell))) return rc2;
-  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.fill, (size_t)ncell))) return rc2;
+  DevArena A;
+  A.add(&S.cell_start, (size_t)ncell + 1), A.add(&S.count, (size_t)ncell), A.add(&S.fill, (size_t)ncell);
   const size_t nblk = std::max<size_t>((S.n + RX_THREADS - 1) / RX_THREADS,
                                        ((size_t)ncell + SCAN_TILE - 1) / SCAN_TILE) + 1;
-  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.blk_count, nblk))) return rc2;
-  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.blk_off, nblk))) return rc2;
+  A.add(&S.blk_count, nblk), A.add(&S.blk_off, nblk);
   // Verlet list: capacity from the mean count at this density; entries are
   // the neighbours' slots, 16-bit up to 65,535 particles
   const double V = sys->d.box[0] * sys->d.box[1] * sys->d.box[2];
@@ -237,14 +252,9 @@ int setup_grid(prx_system* sys, double rc) {
   // (a multiple of 4: the build pads each list to whole stages of four)
   S.list_cap = (std::max(32, std::min(252, (int)std::ceil(2.5 * mean_nb + 16.0))) + 3) & ~3;
   S.nl16 = S.n <= 65535 ? 1 : 0;
-  {
-    void* nl = nullptr;
-    if ((rc2 = dalloc(sys, sys->grid_allocs, (uint8_t**)&nl,
-                      (size_t)S.list_cap * S.n * (S.nl16 ? 2 : 4))))
-      return rc2;
-    S.nl = nl;
-  }
-  if ((rc2 = dalloc(sys, sys->grid_allocs, &S.nn, (size_t)S.n))) return rc2;
+  A.add((uint8_t**)&S.nl, (size_t)S.list_cap * S.n * (S.nl16 ? 2 : 4));
+  A.add(&S.nn, (size_t)S.n);
+  if ((rc2 = A.commit(sys, sys->grid_allocs))) return rc2;
   {
     // list-build tiling: the largest tile of 1..4 cell rows whose particles
     // fit about two passes of 256 threads (fewer restaged neighbour rows per
@@ -540,24 +550,20 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
     return bail(fail(sys, PRX_ENOMEM, "pinned observables block"));
   memset(sys->ctl_host, 0, sizeof(Ctl));
 
-  auto& L = sys->dev_allocs;
+  DevArena A;
   SoA* sets[2] = {&S.s0, &S.s1};
   for (SoA* B : sets) {
-    if ((rc = dalloc(sys, L, &B->x, n)) || (rc = dalloc(sys, L, &B->y, n)) || (rc = dalloc(sys, L, &B->z, n)) ||
-        (rc = dalloc(sys, L, &B->vx, n)) || (rc = dalloc(sys, L, &B->vy, n)) || (rc = dalloc(sys, L, &B->vz, n)) ||
-        (rc = dalloc(sys, L, &B->id, n)) || (rc = dalloc(sys, L, &B->type, n)) ||
-        (rc = dalloc(sys, L, &B->state, n)) || (rc = dalloc(sys, L, &B->nadj, n)) ||
-        (rc = dalloc(sys, L, &B->adj, (size_t)n * S.cap)))
-      return bail(rc);
+    A.add(&B->x, n), A.add(&B->y, n), A.add(&B->z, n);
+    A.add(&B->vx, n), A.add(&B->vy, n), A.add(&B->vz, n);
+    A.add(&B->id, n), A.add(&B->type, n), A.add(&B->state, n), A.add(&B->nadj, n);
+    A.add(&B->adj, (size_t)n * S.cap);
   }
-  if ((rc = dalloc(sys, L, &S.P0, n)) || (rc = dalloc(sys, L, &S.P1, n)) || (rc = dalloc(sys, L, &S.key, n)) ||
-      (rc = dalloc(sys, L, &S.tmp, n)) || (rc = dalloc(sys, L, &S.new_of_old, n)) ||
-      (rc = dalloc(sys, L, &S.win, n)) ||
-      (rc = dalloc(sys, L, &S.fin, n)) || (rc = dalloc(sys, L, &S.bonds, (size_t)S.bond_cap)) ||
-      (rc = dalloc(sys, L, &S.hist, (size_t)S.hist_cap + 1)) || (rc = dalloc(sys, L, &S.ctl, 1)) ||
-      (rc = dalloc(sys, L, &S.red, 4 * ((size_t)(n + RX_THREADS - 1) / RX_THREADS + 1))) ||
-      (rc = dalloc(sys, L, &S.fout, 3 * (size_t)n)) || (rc = dalloc(sys, L, &S.eout, (size_t)n)))
-    return bail(rc);
+  A.add(&S.P0, n), A.add(&S.P1, n), A.add(&S.key, n), A.add(&S.tmp, n), A.add(&S.new_of_old, n);
+  A.add(&S.win, n), A.add(&S.fin, n), A.add(&S.bonds, (size_t)S.bond_cap);
+  A.add(&S.hist, (size_t)S.hist_cap + 1), A.add(&S.ctl, 1);
+  A.add(&S.red, 4 * ((size_t)(n + RX_THREADS - 1) / RX_THREADS + 1));
+  A.add(&S.fout, 3 * (size_t)n), A.add(&S.eout, (size_t)n);
+  if ((rc = A.commit(sys, sys->dev_allocs))) return bail(rc);
   if ((rc = setup_grid(sys, grid_rc > rc_w ? grid_rc : rc_w))) return bail(rc);
 
   const SoA& B = S.s0;
