@@ -445,8 +445,15 @@ def main():
         tr = json.load(open(tr_path))
         h = hashlib.sha256()
         for rel in tr.get("digest_of", []):
-            with open(os.path.join(ROOT, rel), "rb") as f:
-                h.update(f.read())
+            # "path" (the whole file) or "path::until::text" (the file up to
+            # the first occurrence of text: the step kernel's part of it)
+            path, _, until = rel.partition("::until::")
+            with open(os.path.join(ROOT, path), "rb") as f:
+                src = f.read()
+            if until:
+                cut = src.find(until.encode())
+                src = src[:cut] if cut >= 0 else b""
+            h.update(src)
         if tr.get("kernel_source_digest") == h.hexdigest():
             traffic = tr.get("bytes_per_launch")
 
