@@ -320,20 +320,16 @@ __global__ void __launch_bounds__(256, 6)
     k_step_nl(Sys S, cudaGraphConditionalHandle cond, int use_cond) {
   step_nl_body<NL16, FORCES_ONLY, CUBIC>(S, Blk{blockIdx.x, gridDim.x}, cond, use_cond);
 }
-// Members of a batch may differ in list width: the branch is uniform per block.
-__global__ void __launch_bounds__(256, 4)
+// Members of a batch may differ in list width and box shape: the batch step
+// runs one launch per (list width, cubic) variant present, each over the
+// blocks of its members, with the single-system kernel's register budget.
+template <bool NL16, bool CUBIC>
+__global__ void __launch_bounds__(256, 5)
     kb_step_nl(const Sys* __restrict__ T, const BlkMap* __restrict__ M,
                cudaGraphConditionalHandle cond, int use_cond, uint32_t* __restrict__ act_n) {
   if (blockIdx.x == 0 && threadIdx.x < 5) act_n[threadIdx.x] = 0u;  // for this step's rebuild plan
   const BlkMap m = M[blockIdx.x];
-  const Sys& S = T[m.sys];
-  if (S.cubic) {
-    if (S.nl16) step_nl_body<true, false, true>(S, Blk{m.b, m.nb}, cond, use_cond);
-    else step_nl_body<false, false, true>(S, Blk{m.b, m.nb}, cond, use_cond);
-  } else {
-    if (S.nl16) step_nl_body<true, false, false>(S, Blk{m.b, m.nb}, cond, use_cond);
-    else step_nl_body<false, false, false>(S, Blk{m.b, m.nb}, cond, use_cond);
-  }
+  step_nl_body<NL16, false, CUBIC>(T[m.sys], Blk{m.b, m.nb}, cond, use_cond);
 }
 
 // ---------------------------------------------------------------------------
@@ -1273,7 +1269,11 @@ void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, c
 
 void launch_batch_step(const BatchLaunch& L, cudaStream_t st, cudaGraphConditionalHandle h,
                        int use_cond) {
-  kb_step_nl<<<L.n_part, 256, 0, st>>>(L.T, L.part, h, use_cond, L.act_n);
+  // variants in the order of the part map: (nl16, cubic) = 00, 01, 10, 11
+  if (L.step_n[0]) kb_step_nl<false, false><<<L.step_n[0], 256, 0, st>>>(L.T, L.part + L.step_off[0], h, use_cond, L.act_n);
+  if (L.step_n[1]) kb_step_nl<false, true><<<L.step_n[1], 256, 0, st>>>(L.T, L.part + L.step_off[1], h, use_cond, L.act_n);
+  if (L.step_n[2]) kb_step_nl<true, false><<<L.step_n[2], 256, 0, st>>>(L.T, L.part + L.step_off[2], h, use_cond, L.act_n);
+  if (L.step_n[3]) kb_step_nl<true, true><<<L.step_n[3], 256, 0, st>>>(L.T, L.part + L.step_off[3], h, use_cond, L.act_n);
 }
 
 // The rebuild pipeline over the members whose flag is set: a plan kernel

@@ -331,6 +331,9 @@ struct BatchLaunch {
   // offsets as the full maps, and their entry counts (zeroed by the step)
   BlkMap* act;
   uint32_t* act_n;
+  // the part map is ordered by step-kernel variant (nl16, cubic): 00, 01,
+  // 10, 11; the blocks of variant v are part[step_off[v] .. + step_n[v])
+  unsigned step_off[4], step_n[4];
 };
 
 // ---- host-side launchers (defined in the kernel translation units) ----------

@@ -89,6 +89,7 @@ struct prx_batch {
   BlkMap* maps = nullptr;    // the block maps, then as many entries for their compaction
   size_t maps_cap = 0;
   uint32_t* act_n = nullptr;  // compacted counts of the rebuild plan
+  int n_step_variants = 0;     // step-kernel launches per batch step
   BatchLaunch L{};
   uint32_t n_active = 0;
   bool any_rx = false;
@@ -786,12 +787,21 @@ int batch_prepare(prx_batch* b) {
   };
   int build_threads = 32;
   size_t build_smem = 0;
+  // the part map ordered by step-kernel variant (list width, cubic box)
+  unsigned step_off[4] = {0, 0, 0, 0}, step_n[4] = {0, 0, 0, 0};
+  b->n_step_variants = 0;
+  for (int v = 0; v < 4; ++v) {
+    step_off[v] = (unsigned)part.size();
+    for (uint32_t q = 0; q < b->n_active; ++q)
+      if ((table[q].nl16 ? 2 : 0) + (table[q].cubic ? 1 : 0) == v) add(part, q, (table[q].n + 255) / 256);
+    step_n[v] = (unsigned)part.size() - step_off[v];
+    if (step_n[v]) b->n_step_variants += 1;
+  }
   for (uint32_t q = 0; q < b->n_active; ++q) {
     Sys& S = table[q];
     S.in_batch = 1;
     S.batch = b->bctl;
     S.n_members = b->n_active;
-    add(part, q, (S.n + 255) / 256);
     add(cell, q, ((uint64_t)S.ncell + 255) / 256);
     add(tile, q, ((uint64_t)S.ncell + SCAN_TILE - 1) / SCAN_TILE);
     add(one, q, 1);
@@ -834,6 +844,10 @@ int batch_prepare(prx_batch* b) {
   L.build_smem = build_smem;
   L.act = b->maps + nmaps;
   L.act_n = b->act_n;
+  for (int v = 0; v < 4; ++v) {
+    L.step_off[v] = step_off[v];
+    L.step_n[v] = step_n[v];
+  }
   CKB(cudaMemcpy(b->T, table.data(), sizeof(Sys) * table.size(), cudaMemcpyHostToDevice));
   CKB(cudaMemcpy(b->maps, all.data(), sizeof(BlkMap) * all.size(), cudaMemcpyHostToDevice));
   if (configure_batch_build_kernel(build_smem))
@@ -1657,7 +1671,7 @@ int prx_batch_run(prx_batch* b, uint64_t nsteps) {
   }
   b->steps += total;
   if (b->theta) b->phase = (b->phase + total) % b->theta;
-  if (b->n_active) b->kernel_steps += total;
+  if (b->n_active) b->kernel_steps += total * (uint64_t)b->n_step_variants;
   for (prx_system* m : b->members) m->host_step += total;
   return PRX_OK;
 }
