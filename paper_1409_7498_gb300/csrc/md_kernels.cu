@@ -259,7 +259,8 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
     for (int b = 0; b < 4; ++b) arow[b] = b < (int)S.cap ? __ldg(B.adj + (size_t)i * S.cap + b) : 0u;
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
     // software pipeline over the list, four entries per stage: the next
-    // stage's list entries load while this stage's four gathers complete.
+    // stage's list entries (when this list has one) load while this stage's
+    // four gathers complete.
     // The build pads every list to whole stages with the slot itself (r = 0,
     // skipped).  In a cubic box displacements stay in position units and the
     // neighbour force is scaled once at the end.
@@ -268,7 +269,7 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
 #pragma unroll
       for (int u = 0; u < 4; ++u) pj[u] = __ldg(P + rn[u]);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) rn[u] = k + 4 + u < S.list_cap ? nl_raw<NL16>(S, k + 4 + u, i) : 0u;
+      for (int u = 0; u < 4; ++u) rn[u] = k + 4 < cnt ? nl_raw<NL16>(S, k + 4 + u, i) : 0u;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if constexpr (CUBIC) {
