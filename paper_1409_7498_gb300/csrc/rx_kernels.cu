@@ -190,7 +190,6 @@ __device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long l
       best = nearest_partner<NL16>(S, B, P, i, true, ncand);
     } else {
       const uint4 pi = P[i];
-      const double xi = B.x[i], yi = B.y[i], zi = B.z[i];
       const uint32_t idi = B.id[i];
       const uint32_t nb = B.nadj[i];
       unsigned long long bestkey = 0ull;
@@ -220,10 +219,10 @@ __device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long l
         // FP32 value from the fixed-point positions is within a known bound
         // of it, so below rr2_in (the cutoff minus twice that bound) the FP64
         // test cannot fail; only pairs near the cutoff take it.
-        if (!(r2f < R.rr2_in)) {
-          const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
-          const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
-          const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
+        if (!(r2f < R.rr2_in)) {  // A's FP64 position loaded only here (rare)
+          const double ddx = min_image(__dsub_rn(B.x[j], B.x[i]), S.L[0], S.halfL[0]);
+          const double ddy = min_image(__dsub_rn(B.y[j], B.y[i]), S.L[1], S.halfL[1]);
+          const double ddz = min_image(__dsub_rn(B.z[j], B.z[i]), S.L[2], S.halfL[2]);
           const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
           if (!(r2 < R.rr2)) continue;
         }
