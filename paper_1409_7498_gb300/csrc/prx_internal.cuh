@@ -81,7 +81,6 @@ struct Ctl {
   unsigned long long reactions;
   unsigned long long nbonds;
   unsigned long long hist_count;
-  unsigned long long rx_base;  // bond-list offset of the current reaction
   long long trace[4];          // candidates, retained, a_winners, formed
   unsigned int n_active;       // eligible A's of the current reaction step
   unsigned int input_err;      // creation: first bad input kind (1 non-finite
@@ -153,7 +152,7 @@ struct Sys {
   uint32_t* cell_start;
   uint32_t *count, *fill;
   uint32_t *key, *tmp, *new_of_old;
-  uint32_t *win, *fin, *blk_count, *blk_off;
+  uint32_t *win, *blk_count, *blk_off;
   BondRec* bonds;
   unsigned long long bond_cap;
   HistRec* hist;

@@ -560,7 +560,7 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
     A.add(&B->adj, (size_t)n * S.cap);
   }
   A.add(&S.P0, n), A.add(&S.P1, n), A.add(&S.key, n), A.add(&S.tmp, n), A.add(&S.new_of_old, n);
-  A.add(&S.win, n), A.add(&S.fin, n), A.add(&S.bonds, (size_t)S.bond_cap);
+  A.add(&S.win, n), A.add(&S.bonds, (size_t)S.bond_cap);
   A.add(&S.hist, (size_t)S.hist_cap + 1), A.add(&S.ctl, 1);
   A.add(&S.red, 4 * ((size_t)(n + RX_THREADS - 1) / RX_THREADS + 1));
   A.add(&S.fout, 3 * (size_t)n), A.add(&S.eout, (size_t)n);
@@ -917,7 +917,7 @@ int prx_estimate_bytes(const prx_system_desc* desc, uint64_t* bytes) {
   const uint64_t per_set = n * (6 * 8 + 4 + 3 + 4 * cap);
   const uint64_t nblk = std::max<uint64_t>(n / RX_THREADS + 1, ncell / SCAN_TILE + 1) + 1;
   const uint64_t allocs = 40;  // separate cudaMalloc calls, each rounded up
-  *bytes = 2 * per_set + n * (2 * 16 + 5 * 4) + (n * cap / 2 + 1) * sizeof(prx_bond) +
+  *bytes = 2 * per_set + n * (2 * 16 + 4 * 4) + (n * cap / 2 + 1) * sizeof(prx_bond) +
            (kHistCap + 1ull) * sizeof(prx_history_record) + sizeof(Ctl) + 32 * (n / RX_THREADS + 2) +
            32 * n + ncell * 12 + 8 * nblk + list_cap * n * nl_bytes + n + allocs * 4096;
   return PRX_OK;
@@ -1133,7 +1133,8 @@ int prx_get_bonds(prx_system* sys, prx_bond* out, uint64_t cap, uint64_t* n_out)
   if (!sys || !n_out) return PRX_EINVAL;
   int rc = read_ctl(sys);
   if (rc) return rc;
-  const uint64_t nb = sys->ctl_host->nbonds;
+  // (a failed reaction step can leave the counter past the list's capacity)
+  const uint64_t nb = std::min<uint64_t>(sys->ctl_host->nbonds, sys->S.bond_cap);
   *n_out = nb;
   const uint64_t m = std::min(cap, nb);
   if (!m || !out) {  // the count alone
@@ -1314,7 +1315,8 @@ int prx_save(prx_system* sys, const char* path) {
   if (rc) return rc;
   rc = sync_status(sys);
   if (rc) return rc;
-  const uint64_t n = sys->S.n, cap = sys->S.cap, nb = sys->ctl_host->nbonds;
+  const uint64_t n = sys->S.n, cap = sys->S.cap,
+                 nb = std::min<uint64_t>(sys->ctl_host->nbonds, sys->S.bond_cap);
   std::vector<prx_bond> bonds(nb);
   if (nb) {
     CK(cudaMemcpy(bonds.data(), sys->S.bonds, sizeof(prx_bond) * nb, cudaMemcpyDeviceToHost));

@@ -70,6 +70,10 @@ __device__ __forceinline__ void rx_compact_body(const Sys& S, const Blk blk) {
   const RxParams& R = S.R;
 
   Ctl* ctl = S.ctl;
+  if (blk.b == 0) {  // clear the history record this reaction will fill
+    int32_t* cnt = &S.hist[ctl->hist_count % S.hist_cap].counts[0][0];
+    for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x) cnt[k] = 0;
+  }
   const SoA B = ctl->set ? S.s1 : S.s0;
   const uint32_t i = blk.b * blockDim.x + threadIdx.x;
   bool el = false;
@@ -269,69 +273,6 @@ __global__ void __launch_bounds__(RX_THREADS)
 // Steps 6-7 for one A winner: every other A that picked the same T lies
 // within r_react of T, hence in T's Verlet list.
 template <bool NL16>
-__device__ __forceinline__ void rx_select_T_body(const Sys& S, const Blk blk, long long step_arg) {
-  Ctl* ctl = S.ctl;
-  const unsigned long long step = step_arg >= 0 ? (unsigned long long)step_arg : ctl->step;
-  const SoA B = ctl->set ? S.s1 : S.s0;
-  const uint32_t i = blk.b * blockDim.x + threadIdx.x;
-  const RxParams& R = S.R;
-  uint32_t fin = NONE;
-  bool winner = false;
-  if (i < S.n && R.rule == PRX_SELECT_NEAREST) {
-    // LAMMPS rule: an A and the T it picked react when the T picked it too
-    // and u < k dt Theta, drawn with the pair's smaller id first
-    const uint32_t T = in_window(R.mask_A, R.a_lo, R.a_hi, B.type[i], B.state[i]) ? S.win[i] : NONE;
-    if (T != NONE && S.win[T] == i) {
-      winner = true;
-      const uint32_t ida = B.id[i], idt = B.id[T];
-      const uint4 w = keyed_draw(S.seed, step, min(ida, idt), max(ida, idt), TAG_NEAREST);
-      if (u53_below(w.x, w.y, R.p53)) fin = T;
-    }
-    S.fin[i] = fin;
-  } else if (i < S.n) {
-    const uint32_t T = S.win[i];
-    if (T != NONE) {
-      winner = true;
-      const uint32_t idi = B.id[i], idT = B.id[T];
-      const unsigned long long mine = key64(keyed_draw(S.seed, step, idT, idi, TAG_SEL_T));
-      bool keep = true;
-      const int cnt = S.nn[T];
-      // four list entries of T at a time (independent loads go out together)
-      for (int k0 = 0; k0 < cnt && keep; k0 += 4) {
-        uint32_t aa[4], wa[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) aa[u] = k0 + u < cnt ? nl_get_rx<NL16>(S, k0 + u, T) : i;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) wa[u] = S.win[aa[u]];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const uint32_t a = aa[u];
-          if (!keep || k0 + u >= cnt || a == i || wa[u] != T) continue;
-          const uint32_t ida = B.id[a];
-          const unsigned long long other = key64(keyed_draw(S.seed, step, idT, ida, TAG_SEL_T));
-          if (other < mine || (other == mine && ida < idi)) keep = false;
-        }
-      }
-      if (keep) fin = T;
-    }
-    S.fin[i] = fin;
-  }
-  const int nfin = __syncthreads_count(fin != NONE);
-  const int nwin = __syncthreads_count(winner);
-  if (threadIdx.x == 0) {
-    S.blk_count[blk.b] = (uint32_t)nfin;
-    if (R.rule == PRX_SELECT_NEAREST) {  // mutual pairs, accepted pairs
-      if (nwin) atomicAdd((unsigned long long*)&ctl->trace[1], (unsigned long long)nwin);
-      if (nfin) atomicAdd((unsigned long long*)&ctl->trace[2], (unsigned long long)nfin);
-    } else if (nwin) {
-      atomicAdd((unsigned long long*)&ctl->trace[2], (unsigned long long)nwin);
-    }
-  }
-}
-
-// LAMMPS rule: every eligible T picks its nearest eligible A (win[] of T
-// slots; win[] of A slots holds the A's nearest T).
-template <bool NL16>
 __device__ __forceinline__ void rx_find_T_body(const Sys& S, const Blk blk) {
   const RxParams& R = S.R;
   if (R.rule != PRX_SELECT_NEAREST) return;
@@ -357,136 +298,143 @@ __global__ void __launch_bounds__(RX_THREADS)
   else rx_find_T_body<false>(S, Blk{m.b, m.nb});
 }
 
+// Table I steps 6-9 in one pass over the eligible A's (the compacted list
+// S.tmp): the T that an A picked keeps the A with the smallest key_T
+// (random rule), or a mutual nearest pair is accepted with probability
+// k dt Theta (nearest rule); an A that keeps its T forms the bond at once:
+// adjacency of both, states, and a record in the bond list.  The decisions
+// read only the choices (win) and ids, which no bond changes, and each A
+// and each T take part in at most one bond, so forming bonds while other
+// A's still decide changes nothing.  Bond-list positions come from one
+// atomic per warp: the list's order may vary between runs (it is read back
+// sorted), its content does not.
 template <bool NL16>
-__global__ void __launch_bounds__(RX_THREADS) k_rx_select_T(Sys S, long long step_arg) {
-  rx_select_T_body<NL16>(S, Blk{blockIdx.x, gridDim.x}, step_arg);
+__device__ __forceinline__ uint32_t rx_decide(const Sys& S, const SoA& B, unsigned long long step,
+                                              uint32_t i, bool& winner) {
+  const RxParams& R = S.R;
+  const uint32_t T = S.win[i];
+  winner = false;
+  if (T == NONE) return NONE;
+  if (R.rule == PRX_SELECT_NEAREST) {
+    // LAMMPS rule: an A and the T it picked react when the T picked it too
+    // and u < k dt Theta, drawn with the pair's smaller id first
+    if (S.win[T] != i) return NONE;
+    winner = true;
+    const uint32_t ida = B.id[i], idt = B.id[T];
+    const uint4 w = keyed_draw(S.seed, step, min(ida, idt), max(ida, idt), TAG_NEAREST);
+    return u53_below(w.x, w.y, R.p53) ? T : NONE;
+  }
+  winner = true;
+  const uint32_t idi = B.id[i], idT = B.id[T];
+  const unsigned long long mine = key64(keyed_draw(S.seed, step, idT, idi, TAG_SEL_T));
+  bool keep = true;
+  const int cnt = S.nn[T];
+  // four list entries of T at a time (independent loads go out together)
+  for (int k0 = 0; k0 < cnt && keep; k0 += 4) {
+    uint32_t aa[4], wa[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) aa[u] = k0 + u < cnt ? nl_get_rx<NL16>(S, k0 + u, T) : i;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) wa[u] = S.win[aa[u]];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t a = aa[u];
+      if (!keep || k0 + u >= cnt || a == i || wa[u] != T) continue;
+      const uint32_t ida = B.id[a];
+      const unsigned long long other = key64(keyed_draw(S.seed, step, idT, ida, TAG_SEL_T));
+      if (other < mine || (other == mine && ida < idi)) keep = false;
+    }
+  }
+  return keep ? T : NONE;
+}
+
+template <bool NL16>
+__device__ __forceinline__ void rx_select_apply_body(const Sys& S, const Blk blk, long long step_arg) {
+  const RxParams& R = S.R;
+  Ctl* ctl = S.ctl;
+  const unsigned long long step = step_arg >= 0 ? (unsigned long long)step_arg : ctl->step;
+  const SoA B = ctl->set ? S.s1 : S.s0;
+  const uint32_t nact = ctl->n_active;
+  const int lane = threadIdx.x & 31;
+  long long nwin = 0, nfin = 0;
+  // block-strided over the eligible A's, warp-uniform trip count
+  for (uint32_t base = blk.b * blockDim.x; base < nact; base += blk.nb * blockDim.x) {
+    const uint32_t w = base + threadIdx.x;
+    uint32_t i = NONE, T = NONE;
+    if (w < nact) {
+      i = S.tmp[w];
+      bool winner;
+      T = rx_decide<NL16>(S, B, step, i, winner);
+      nwin += winner ? 1 : 0;
+    }
+    bool form = false;
+    uint32_t na = 0, nt = 0;
+    if (T != NONE) {
+      ++nfin;
+      const uint32_t ta = B.type[i], tt = B.type[T];
+      const uint32_t capA = R.maxval[ta] < S.cap ? R.maxval[ta] : S.cap;
+      const uint32_t capT = R.maxval[tt] < S.cap ? R.maxval[tt] : S.cap;
+      na = B.nadj[i];
+      nt = B.nadj[T];
+      form = na < capA && nt < capT;
+      if (!form) set_status(ctl, PRX_ECAPACITY);
+    }
+    // one bond-list reservation per warp
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, form);
+    if (!bal) continue;
+    unsigned long long first = 0ull;
+    if (lane == __ffs(bal) - 1) first = atomicAdd(&ctl->nbonds, (unsigned long long)__popc(bal));
+    first = __shfl_sync(0xFFFFFFFFu, first, __ffs(bal) - 1);
+    if (!form) continue;
+    const unsigned long long pos = first + __popc(bal & ((1u << lane) - 1u));
+    if (pos >= S.bond_cap) {
+      set_status(ctl, PRX_ECAPACITY);
+      continue;
+    }
+    const uint32_t sbit = R.style << 31;
+    B.adj[(size_t)i * S.cap + na] = T | sbit;
+    B.nadj[i] = (uint8_t)(na + 1);
+    B.adj[(size_t)T * S.cap + nt] = i | sbit;
+    B.nadj[T] = (uint8_t)(nt + 1);
+    B.state[i] = (int8_t)(B.state[i] + R.dA);
+    B.state[T] = (int8_t)(B.state[T] + R.dT);
+    BondRec rec;
+    rec.a = B.id[i];
+    rec.t = B.id[T];
+    rec.step = (int64_t)step;
+    rec.style = R.style;
+    rec.reserved = 0u;
+    S.bonds[pos] = rec;
+  }
+  const long long cw = block_sum_ll(nwin);
+  const long long cf = block_sum_ll(nfin);
+  if (threadIdx.x == 0) {
+    if (R.rule == PRX_SELECT_NEAREST) {  // mutual pairs, accepted pairs
+      if (cw) atomicAdd((unsigned long long*)&ctl->trace[1], (unsigned long long)cw);
+      if (cf) atomicAdd((unsigned long long*)&ctl->trace[2], (unsigned long long)cf);
+    } else if (cw) {
+      atomicAdd((unsigned long long*)&ctl->trace[2], (unsigned long long)cw);
+    }
+    if (cf) atomicAdd((unsigned long long*)&ctl->trace[3], (unsigned long long)cf);
+  }
+}
+
+template <bool NL16>
+__global__ void __launch_bounds__(RX_THREADS) k_rx_select_apply(Sys S, long long step_arg) {
+  rx_select_apply_body<NL16>(S, Blk{blockIdx.x, gridDim.x}, step_arg);
 }
 __global__ void __launch_bounds__(RX_THREADS)
-    kb_rx_select_T(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
+    kb_rx_select_apply(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
   const BlkMap m = M[blockIdx.x];
   const Sys& S = T[m.sys];
   if (!S.has_rx) return;  // this member has no reaction scheme
-  if (S.nl16) rx_select_T_body<true>(S, Blk{m.b, m.nb}, -1LL);
-  else rx_select_T_body<false>(S, Blk{m.b, m.nb}, -1LL);
+  if (S.nl16) rx_select_apply_body<true>(S, Blk{m.b, m.nb}, -1LL);
+  else rx_select_apply_body<false>(S, Blk{m.b, m.nb}, -1LL);
 }
 
 // One block: exclusive scan of the per-block counts, bond-list base, and a
 // cleared history record for this reaction step.
-__device__ __forceinline__ void rx_scan_body(const Sys& S, const uint32_t nblk) {
-  Ctl* ctl = S.ctl;
-  __shared__ uint32_t warp_tot[32];
-  __shared__ uint32_t carry_s;
-  // one pass: each thread scans a run of consecutive block counts; the runs'
-  // sums are scanned across the block with warp shuffles
-  const uint32_t per = (nblk + blockDim.x - 1) / blockDim.x;
-  const uint32_t i0 = threadIdx.x * per, i1 = min(i0 + per, nblk);
-  uint32_t v = 0;
-  for (uint32_t q = i0; q < i1; ++q) v += S.blk_count[q];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) warp_tot[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t t = lane < nw ? warp_tot[lane] : 0u;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
-      if (lane >= o) t += y;
-    }
-    if (lane < nw) warp_tot[lane] = t;  // inclusive
-    if (lane == nw - 1) carry_s = t;
-  }
-  __syncthreads();
-  uint32_t run = (wid ? warp_tot[wid - 1] : 0u) + x - v;
-  for (uint32_t q = i0; q < i1; ++q) {
-    const uint32_t c = S.blk_count[q];
-    S.blk_off[q] = run;
-    run += c;
-  }
-  if (threadIdx.x == 0) {
-    const unsigned long long total = carry_s;
-    const unsigned long long base = ctl->nbonds;
-    ctl->rx_base = base;
-    if (base + total > S.bond_cap) {
-      set_status(ctl, PRX_ECAPACITY);
-      ctl->nbonds = S.bond_cap;
-    } else {
-      ctl->nbonds = base + total;
-    }
-    ctl->trace[3] = (long long)total;
-  }
-  // clear the history record this reaction will fill
-  HistRec* rec = &S.hist[ctl->hist_count % S.hist_cap];
-  int32_t* cnt = &rec->counts[0][0];
-  for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x) cnt[k] = 0;
-}
 
-__global__ void k_rx_scan(Sys S, uint32_t nblk) { rx_scan_body(S, nblk); }
-__global__ void kb_rx_scan(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
-  const Sys& S = T[M[blockIdx.x].sys];
-  if (!S.has_rx) return;
-  rx_scan_body(S, S.n ? (S.n + RX_THREADS - 1) / RX_THREADS : 1u);
-}
-
-__device__ __forceinline__ void rx_apply_body(const Sys& S, const Blk blk, long long step_arg) {
-  const RxParams& R = S.R;
-
-  Ctl* ctl = S.ctl;
-  const unsigned long long step = step_arg >= 0 ? (unsigned long long)step_arg : ctl->step;
-  const SoA B = ctl->set ? S.s1 : S.s0;
-  const uint32_t i = blk.b * blockDim.x + threadIdx.x;
-  const uint32_t T = i < S.n ? S.fin[i] : NONE;
-  const bool has = T != NONE;
-  // rank of this pair among the block's pairs (ballot + warp prefix)
-  __shared__ uint32_t wcount[RX_THREADS / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t bal = __ballot_sync(0xFFFFFFFFu, has);
-  if (lane == 0) wcount[wid] = __popc(bal);
-  __syncthreads();
-  uint32_t before = 0;
-  for (int w = 0; w < wid; ++w) before += wcount[w];
-  const uint32_t rank = before + __popc(bal & ((1u << lane) - 1u));
-  if (!has) return;
-  const unsigned long long pos = ctl->rx_base + S.blk_off[blk.b] + rank;
-  const uint32_t ta = B.type[i], tt = B.type[T];
-  const uint32_t capA = R.maxval[ta] < S.cap ? R.maxval[ta] : S.cap;
-  const uint32_t capT = R.maxval[tt] < S.cap ? R.maxval[tt] : S.cap;
-  const uint32_t na = B.nadj[i], nt = B.nadj[T];
-  if (na >= capA || nt >= capT || pos >= S.bond_cap) {
-    set_status(ctl, PRX_ECAPACITY);
-    return;
-  }
-  const uint32_t sbit = R.style << 31;
-  B.adj[(size_t)i * S.cap + na] = T | sbit;
-  B.nadj[i] = (uint8_t)(na + 1);
-  B.adj[(size_t)T * S.cap + nt] = i | sbit;
-  B.nadj[T] = (uint8_t)(nt + 1);
-  B.state[i] = (int8_t)(B.state[i] + R.dA);
-  B.state[T] = (int8_t)(B.state[T] + R.dT);
-  BondRec rec;
-  rec.a = B.id[i];
-  rec.t = B.id[T];
-  rec.step = (int64_t)step;
-  rec.style = R.style;
-  rec.reserved = 0u;
-  S.bonds[pos] = rec;
-}
-
-__global__ void __launch_bounds__(RX_THREADS) k_rx_apply(Sys S, long long step_arg) {
-  rx_apply_body(S, Blk{blockIdx.x, gridDim.x}, step_arg);
-}
-__global__ void __launch_bounds__(RX_THREADS)
-    kb_rx_apply(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
-  const BlkMap m = M[blockIdx.x];
-  const Sys& S = T[m.sys];
-  if (!S.has_rx) return;  // this member has no reaction scheme
-  rx_apply_body(S, Blk{m.b, m.nb}, -1LL);
-}
 
 // Populations per (type, state) into history record hist_count % hist_cap
 // (integer atomics: the counts do not depend on their order).
@@ -647,7 +595,7 @@ inline unsigned blocks_rx(uint32_t n) { return n ? (n + RX_THREADS - 1) / RX_THR
 
 }  // namespace
 
-int rx_kernel_count(int rule) { return rule == PRX_SELECT_NEAREST ? 7 : 6; }
+int rx_kernel_count(int rule) { return rule == PRX_SELECT_NEAREST ? 5 : 4; }
 
 void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
                void (*hook)(void*, const char*, int), void* ctx) {
@@ -670,16 +618,10 @@ void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
     else k_rx_find_T<false><<<g, RX_THREADS, 0, st>>>(S);
     H("rx_find_T", 1);
   }
-  H("rx_select_T", 0);
-  if (S.nl16) k_rx_select_T<true><<<g, RX_THREADS, 0, st>>>(S, step_arg);
-  else k_rx_select_T<false><<<g, RX_THREADS, 0, st>>>(S, step_arg);
-  H("rx_select_T", 1);
-  H("rx_scan", 0);
-  k_rx_scan<<<1, 1024, 0, st>>>(S, g);
-  H("rx_scan", 1);
-  H("rx_apply", 0);
-  k_rx_apply<<<g, RX_THREADS, 0, st>>>(S, step_arg);
-  H("rx_apply", 1);
+  H("rx_select_apply", 0);
+  if (S.nl16) k_rx_select_apply<true><<<gf, RX_THREADS, 0, st>>>(S, step_arg);
+  else k_rx_select_apply<false><<<gf, RX_THREADS, 0, st>>>(S, step_arg);
+  H("rx_select_apply", 1);
   H("obs_hist", 0);
   k_obs_hist<<<gf, RX_THREADS, 0, st>>>(S, step_arg, 1);
   H("obs_hist", 1);
@@ -703,16 +645,14 @@ void launch_observables(const Sys& S, cudaStream_t st, int nblocks) {
   k_obs_final<<<1, RX_THREADS, 0, st>>>(S, (uint32_t)nblocks);
 }
 
-int batch_rx_kernel_count() { return 8; }
+int batch_rx_kernel_count() { return 6; }
 
 void launch_batch_rx(const BatchLaunch& L, cudaStream_t st) {
   kb_rx_begin<<<L.n_one, 32, 0, st>>>(L.T, L.one);
   kb_rx_compact<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
   kb_rx_find<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
   kb_rx_find_T<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
-  kb_rx_select_T<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
-  kb_rx_scan<<<L.n_one, 1024, 0, st>>>(L.T, L.one);
-  kb_rx_apply<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
+  kb_rx_select_apply<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
   kb_obs_hist<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
 }
 
