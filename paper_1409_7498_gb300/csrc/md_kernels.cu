@@ -174,6 +174,11 @@ __device__ __forceinline__ uint32_t nl_get(const Sys& S, int k, uint32_t i) {
   return nl_raw<NL16>(S, k, i);
 }
 
+// Fetch the line holding *a into L2 (no register result).
+__device__ __forceinline__ void prefetch_l2(const void* a) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 // Physical minimum-image displacement x_j - x_i: exact in fixed point,
 // converted with one rounding, scaled by L / 2^32.
 __device__ __forceinline__ void disp(const Sys& S, uint4 pj, uint4 pi, float& dx, float& dy,
@@ -253,10 +258,11 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
 #pragma unroll
     for (int u = 0; u < 4; ++u) rn[u] = nl_raw<NL16>(S, u, i);
     const uint4 pi = __ldg(P + i);
-    const uint32_t nb = __ldg(B.nadj + i);
-    uint32_t arow[4];  // first four adjacency entries prefetched; more are rare
-#pragma unroll
-    for (int b = 0; b < 4; ++b) arow[b] = b < (int)S.cap ? __ldg(B.adj + (size_t)i * S.cap + b) : 0u;
+    // the bond count and adjacency row are read after the list loop; a
+    // prefetch into L2 now hides their DRAM latency without holding
+    // registers across the loop
+    prefetch_l2(B.nadj + i);
+    prefetch_l2(B.adj + (size_t)i * S.cap);
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
     // software pipeline over the list, four entries per stage: the next
     // stage's list entries (when this list has one) load while this stage's
@@ -292,9 +298,9 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
       fz *= S.scale[0];
     }
     bool ok = true;
+    const uint32_t nb = __ldg(B.nadj + i);
     for (int b = 0; b < (int)nb; ++b) {
-      const uint32_t ent = b == 0 ? arow[0] : b == 1 ? arow[1] : b == 2 ? arow[2] : b == 3 ? arow[3]
-                                                 : __ldg(B.adj + (size_t)i * S.cap + b);
+      const uint32_t ent = __ldg(B.adj + (size_t)i * S.cap + b);
       const uint4 pj = __ldg(P + (ent & SLOT_MASK));
       float dx, dy, dz;
       disp(S, pj, pi, dx, dy, dz);
@@ -722,10 +728,24 @@ __device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk, 
   const uint32_t s = blk.b * blockDim.x + threadIdx.x;
   if (s >= S.n) return;
   const uint32_t o = S.tmp[s];
+  // every load first: a store into set B could alias a later load from set A
+  // as far as the compiler knows, and would hold that load back
+  double x = __ldg(A.x + o), y = __ldg(A.y + o), z = __ldg(A.z + o);
+  const double vx = __ldg(A.vx + o), vy = __ldg(A.vy + o), vz = __ldg(A.vz + o);
+  const uint32_t pid = __ldg(A.id + o);
+  const uint8_t ty = __ldg(A.type + o);
+  const int8_t st = __ldg(A.state + o);
+  const uint32_t nb = __ldg(A.nadj + o);
+  const uint32_t key = __ldg(S.key + o);
+  uint32_t e[4];  // partners renamed to their new slots (the first four at once)
+#pragma unroll
+  for (int b = 0; b < 4; ++b) e[b] = b < (int)nb ? __ldg(A.adj + (size_t)o * S.cap + b) : 0u;
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+    if (b < (int)nb) e[b] = __ldg(S.new_of_old + (e[b] & SLOT_MASK)) | (e[b] & ~SLOT_MASK);
   // positions re-enter the box here (a checkpoint restore keeps them as
   // saved, so that the continued run wraps them at the same step as the
   // original run)
-  double x = A.x[o], y = A.y[o], z = A.z[o];
   if (wrap) {
     x = wrap_into_box(x, S.L[0]);
     y = wrap_into_box(y, S.L[1]);
@@ -734,24 +754,25 @@ __device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk, 
   B.x[s] = x;
   B.y[s] = y;
   B.z[s] = z;
-  B.vx[s] = A.vx[o];
-  B.vy[s] = A.vy[o];
-  B.vz[s] = A.vz[o];
-  const uint32_t pid = A.id[o];
+  B.vx[s] = vx;
+  B.vy[s] = vy;
+  B.vz[s] = vz;
   B.id[s] = pid;
-  B.type[s] = A.type[o];
-  B.state[s] = A.state[o];
-  const uint32_t nb = A.nadj[o];
+  B.type[s] = ty;
+  B.state[s] = st;
   B.nadj[s] = (uint8_t)nb;
-  for (uint32_t b = 0; b < nb; ++b) {  // partners renamed to their new slots
-    const uint32_t e = A.adj[(size_t)o * S.cap + b];
-    B.adj[(size_t)s * S.cap + b] = S.new_of_old[e & SLOT_MASK] | (e & ~SLOT_MASK);
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+    if (b < (int)nb) B.adj[(size_t)s * S.cap + b] = e[b];
+  for (uint32_t b = 4; b < nb; ++b) {
+    const uint32_t f = A.adj[(size_t)o * S.cap + b];
+    B.adj[(size_t)s * S.cap + b] = S.new_of_old[f & SLOT_MASK] | (f & ~SLOT_MASK);
   }
   const uint32_t X = periodic_fx(x, S.Lfx[0], S.M64[0]);
   const uint32_t Y = periodic_fx(y, S.Lfx[1], S.M64[1]);
   const uint32_t Z = periodic_fx(z, S.Lfx[2], S.M64[2]);
   P[s] = make_uint4(X, Y, Z, coarse_ref(X, Y, Z, S.wshift));
-  S.tmp[s] = S.key[o];
+  S.tmp[s] = key;
 }
 
 __global__ void k_rebin_permute(Sys S, int wrap) {
@@ -999,7 +1020,7 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
         for (int w = 0; w < 9; ++w) {
           const int lo = max((int)(win[w] & 0xFFFFu), c0) - c0;
           const int hi = min((int)(win[w] >> 16), c0 + cn) - c0;
-#pragma unroll 1
+#pragma unroll 2
           for (int k = lo; k < hi; ++k) {
             const float4 q = sX[k];
             const float dx = q.x - fi.x, dy = q.y - fi.y, dz = q.z - fi.z;
