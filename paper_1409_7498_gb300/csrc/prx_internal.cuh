@@ -260,28 +260,6 @@ __device__ __forceinline__ long long fx32(double x) {
   return (b < 0) ? -r : r;
 }
 
-// d 2^-32 correctly rounded to float, |d| < 2^34, without an I2F/F2F
-// instruction: d = hi 2^20 + lo with both halves converted exactly, then one
-// rounding in the fused multiply-add.
-__device__ __forceinline__ float fx_to_float(long long d) {
-  const int hi = (int)(d >> 20);                    // [-2^14, 2^14)
-  const uint32_t lo = (uint32_t)d & 0xFFFFFu;       // [0, 2^20)
-  const float hf = __fsub_rn(__uint_as_float(0x4B000000u | (uint32_t)(hi + 16384)), 8404992.0f);
-  const float lf = small_u2f(lo);
-  return __fmul_rn(__fmaf_rn(hf, 1048576.0f, lf), 0x1.0p-32f);
-}
-
-// A 32-bit integer rounded once to float (round to nearest even), on the
-// integer and FP32 pipes: d = hi 2^12 + lo, both halves exact in float.
-__device__ __forceinline__ float i2f_rn(int d) {
-  const int hi = d >> 12;                       // [-2^19, 2^19)
-  const uint32_t lo = (uint32_t)d & 0xFFFu;     // [0, 2^12)
-  const float hf = __fsub_rn(__uint_as_float(0x4B000000u | (uint32_t)(hi + 524288)), 8912896.0f);
-  return __fmaf_rn(hf, 4096.0f, small_u2f(lo));
-}
-// 2^-29 fixed point to float, one rounding.
-__device__ __forceinline__ float fx29_to_float(int d) { return __fmul_rn(i2f_rn(d), 0x1.0p-29f); }
-
 // Periodic fixed point of a coordinate: floor(x / L 2^32) mod 2^32, from
 // the binary64 fields and one 64x64 high multiply (integer pipe only).
 // Valid for -L < x < 2^29.
@@ -297,19 +275,9 @@ __device__ __forceinline__ uint32_t coarse_ref(uint32_t X, uint32_t Y, uint32_t 
   return ((X >> sh[0]) & 1023u) | (((Y >> sh[1]) & 1023u) << 10) | (((Z >> sh[2]) & 1023u) << 20);
 }
 
-__device__ __forceinline__ uint32_t pack_cell(int cx, int cy, int cz) {
-  return (uint32_t)cx | ((uint32_t)cy << 9) | ((uint32_t)cz << 18);
-}
-__device__ __forceinline__ void unpack_cell(uint32_t w, int& cx, int& cy, int& cz) {
-  cx = (int)(w & 511u);
-  cy = (int)((w >> 9) & 511u);
-  cz = (int)((w >> 18) & 511u);
-}
 __device__ __forceinline__ int wrap_cell(int q, int n) { return q < 0 ? q + n : (q >= n ? q - n : q); }
 
 __device__ __forceinline__ void set_status(Ctl* ctl, int code) { atomicCAS(&ctl->status, 0, code); }
-
-__device__ __forceinline__ const SoA& cur_soa(const Sys& S, int set) { return set ? S.s1 : S.s0; }
 
 // Minimum image of one FP64 separation component by compare-and-shift.
 __device__ __forceinline__ double min_image(double d, double L, double half) {
