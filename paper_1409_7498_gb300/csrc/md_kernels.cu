@@ -237,6 +237,80 @@ __device__ __forceinline__ void integrate32(const Sys& S, Ctl* ctl, const SoA& B
 // ---------------------------------------------------------------------------
 // FP32 step kernel: one thread per slot, WCA over the Verlet list.
 // ---------------------------------------------------------------------------
+// The step of slot i: forces over its list and bonds, then the integration
+// (or, FORCES_ONLY, the forces written out).
+template <bool NL16, bool FORCES_ONLY, bool CUBIC>
+__device__ __forceinline__ void step_one(const Sys& S, Ctl* ctl, const SoA& B,
+                                         const uint4* __restrict__ P, uint4* __restrict__ Pn,
+                                         uint32_t i, unsigned long long step) {
+  // every load that does not depend on another goes out first
+  const int cnt = __ldg(S.nn + i);
+  uint32_t rn[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) rn[u] = nl_raw<NL16>(S, u, i);
+  const uint4 pi = __ldg(P + i);
+  // the bond count and adjacency row are read after the list loop; a
+  // prefetch into L2 now hides their DRAM latency without holding
+  // registers across the loop
+  prefetch_l2(B.nadj + i);
+  prefetch_l2(B.adj + (size_t)i * S.cap);
+  float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+  // software pipeline over the list, four entries per stage: the next
+  // stage's list entries (when this list has one) load while this stage's
+  // four gathers complete.
+  // The build pads every list to whole stages with the slot itself (r = 0,
+  // skipped).  In a cubic box displacements stay in position units and the
+  // neighbour force is scaled once at the end.
+  for (int k = 0; k < cnt; k += 4) {
+    uint4 pj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pj[u] = __ldg(P + rn[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) rn[u] = k + 4 < cnt ? nl_raw<NL16>(S, k + 4 + u, i) : 0u;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if constexpr (CUBIC) {
+        const float ux = __int2float_rn(pdiff(pj[u].x, pi.x));
+        const float uy = __int2float_rn(pdiff(pj[u].y, pi.y));
+        const float uz = __int2float_rn(pdiff(pj[u].z, pi.z));
+        const float r2u = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
+        if (r2u > 0.f && r2u < S.rc2u) wca32(S, ux, uy, uz, r2u * S.s2f, fx, fy, fz, e);
+      } else {
+        float dx, dy, dz;
+        disp(S, pj[u], pi, dx, dy, dz);
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        if (r2 > 0.f && r2 < S.rc2f) wca32(S, dx, dy, dz, r2, fx, fy, fz, e);
+      }
+    }
+  }
+  if constexpr (CUBIC) {
+    fx *= S.scale[0];
+    fy *= S.scale[0];
+    fz *= S.scale[0];
+  }
+  bool ok = true;
+  const uint32_t nb = __ldg(B.nadj + i);
+  for (int b = 0; b < (int)nb; ++b) {
+    const uint32_t ent = __ldg(B.adj + (size_t)i * S.cap + b);
+    const uint4 pj = __ldg(P + (ent & SLOT_MASK));
+    float dx, dy, dz;
+    disp(S, pj, pi, dx, dy, dz);
+    ok = bond32(S, ent >> 31, dx, dy, dz, fx, fy, fz, e) && ok;
+  }
+  if (!ok) set_status(ctl, PRX_EOVERSTRETCH);
+  if constexpr (FORCES_ONLY) {
+    S.fout[3 * (size_t)i + 0] = (double)fx;
+    S.fout[3 * (size_t)i + 1] = (double)fy;
+    S.fout[3 * (size_t)i + 2] = (double)fz;
+    S.eout[i] = (double)e;
+  } else {
+    const double xi = B.x[i], yi = B.y[i], zi = B.z[i];
+    const double vx = B.vx[i], vy = B.vy[i], vz = B.vz[i];
+    const uint32_t pid = __ldg(B.id + i);
+    integrate32(S, ctl, B, Pn, i, pid, pi.w, step, fx, fy, fz, xi, yi, zi, vx, vy, vz);
+  }
+}
+
 template <bool NL16, bool FORCES_ONLY, bool CUBIC>
 __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
                                              cudaGraphConditionalHandle cond, int use_cond) {
@@ -251,81 +325,37 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
   const uint4* __restrict__ P = ph ? S.P1 : S.P0;
   uint4* __restrict__ Pn = ph ? S.P0 : S.P1;
   const uint32_t i = blk.b * blockDim.x + threadIdx.x;
-  if (i < S.n) {
-    // every load that does not depend on another goes out first
-    const int cnt = __ldg(S.nn + i);
-    uint32_t rn[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) rn[u] = nl_raw<NL16>(S, u, i);
-    const uint4 pi = __ldg(P + i);
-    // the bond count and adjacency row are read after the list loop; a
-    // prefetch into L2 now hides their DRAM latency without holding
-    // registers across the loop
-    prefetch_l2(B.nadj + i);
-    prefetch_l2(B.adj + (size_t)i * S.cap);
-    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
-    // software pipeline over the list, four entries per stage: the next
-    // stage's list entries (when this list has one) load while this stage's
-    // four gathers complete.
-    // The build pads every list to whole stages with the slot itself (r = 0,
-    // skipped).  In a cubic box displacements stay in position units and the
-    // neighbour force is scaled once at the end.
-    for (int k = 0; k < cnt; k += 4) {
-      uint4 pj[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) pj[u] = __ldg(P + rn[u]);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) rn[u] = k + 4 < cnt ? nl_raw<NL16>(S, k + 4 + u, i) : 0u;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if constexpr (CUBIC) {
-          const float ux = __int2float_rn(pdiff(pj[u].x, pi.x));
-          const float uy = __int2float_rn(pdiff(pj[u].y, pi.y));
-          const float uz = __int2float_rn(pdiff(pj[u].z, pi.z));
-          const float r2u = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
-          if (r2u > 0.f && r2u < S.rc2u) wca32(S, ux, uy, uz, r2u * S.s2f, fx, fy, fz, e);
-        } else {
-          float dx, dy, dz;
-          disp(S, pj[u], pi, dx, dy, dz);
-          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          if (r2 > 0.f && r2 < S.rc2f) wca32(S, dx, dy, dz, r2, fx, fy, fz, e);
-        }
-      }
-    }
-    if constexpr (CUBIC) {
-      fx *= S.scale[0];
-      fy *= S.scale[0];
-      fz *= S.scale[0];
-    }
-    bool ok = true;
-    const uint32_t nb = __ldg(B.nadj + i);
-    for (int b = 0; b < (int)nb; ++b) {
-      const uint32_t ent = __ldg(B.adj + (size_t)i * S.cap + b);
-      const uint4 pj = __ldg(P + (ent & SLOT_MASK));
-      float dx, dy, dz;
-      disp(S, pj, pi, dx, dy, dz);
-      ok = bond32(S, ent >> 31, dx, dy, dz, fx, fy, fz, e) && ok;
-    }
-    if (!ok) set_status(ctl, PRX_EOVERSTRETCH);
-    if constexpr (FORCES_ONLY) {
-      S.fout[3 * (size_t)i + 0] = (double)fx;
-      S.fout[3 * (size_t)i + 1] = (double)fy;
-      S.fout[3 * (size_t)i + 2] = (double)fz;
-      S.eout[i] = (double)e;
-    } else {
-      const double xi = B.x[i], yi = B.y[i], zi = B.z[i];
-      const double vx = B.vx[i], vy = B.vy[i], vz = B.vz[i];
-      const uint32_t pid = __ldg(B.id + i);
-      integrate32(S, ctl, B, Pn, i, pid, pi.w, step, fx, fy, fz, xi, yi, zi, vx, vy, vz);
-    }
-  }
+  if (i < S.n) step_one<NL16, FORCES_ONLY, CUBIC>(S, ctl, B, P, Pn, i, step);
   if constexpr (!FORCES_ONLY) step_epilogue(S, ph, step, cond, use_cond, &warps_left, blk.nb);
 }
 
+// Single system: as many blocks as are resident at once, each warp taking
+// 32-slot chunks strided by the grid's warp count, so that every SM stays
+// fully occupied to the end instead of running a partial last wave.
 template <bool NL16, bool FORCES_ONLY, bool CUBIC>
 __global__ void __launch_bounds__(256, 6)
     k_step_nl(Sys S, cudaGraphConditionalHandle cond, int use_cond) {
-  step_nl_body<NL16, FORCES_ONLY, CUBIC>(S, Blk{blockIdx.x, gridDim.x}, cond, use_cond);
+  __shared__ unsigned int warps_left;
+  if (threadIdx.x == 0) warps_left = blockDim.x >> 5;
+  __syncthreads();
+  Ctl* ctl = S.ctl;
+  const int ph = ctl->phase;
+  const unsigned long long step = ctl->step + 1ull;
+  const uint4* __restrict__ P = ph ? S.P1 : S.P0;
+  uint4* __restrict__ Pn = ph ? S.P0 : S.P1;
+  const uint32_t W = gridDim.x * (blockDim.x >> 5);
+  // one loop per SoA set (a uniform branch), so that the set's array
+  // pointers are read from the kernel parameters where they are used
+  // instead of occupying registers across the loop
+  auto run = [&](const SoA& B) {
+    for (uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c * 32u < S.n; c += W) {
+      const uint32_t i = c * 32u + (threadIdx.x & 31u);
+      if (i < S.n) step_one<NL16, FORCES_ONLY, CUBIC>(S, ctl, B, P, Pn, i, step);
+    }
+  };
+  if (ctl->set) run(S.s1);
+  else run(S.s0);
+  if constexpr (!FORCES_ONLY) step_epilogue(S, ph, step, cond, use_cond, &warps_left, gridDim.x);
 }
 // Members of a batch may differ in list width and box shape: the batch step
 // runs one launch per (list width, cubic) variant present, each over the
@@ -1170,6 +1200,27 @@ void launch_stage_input(const Sys& S, cudaStream_t st, const double* buf, int wh
   if (S.n) k_stage_input<<<blocks_for(S.n, 256), 256, 0, st>>>(S, buf, which);
 }
 
+// Blocks of `threads` threads of kernel `kern` resident on the whole current
+// device at once (cached per device and kernel variant).
+unsigned resident_blocks(int variant, const void* kern, int threads) {
+  static std::mutex mu;
+  static unsigned cache[64][8];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1u;
+  std::lock_guard<std::mutex> lk(mu);
+  unsigned& c = cache[dev][variant & 7];
+  if (!c) {
+    int sms = 0, per = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return 1u;
+    }
+    c = sms * per > 0 ? (unsigned)(sms * per) : 1u;
+  }
+  return c;
+}
+
 void launch_step(const Sys& S, cudaStream_t st, int fp64, int forces_only,
                  cudaGraphConditionalHandle h, int use_cond) {
   if (fp64) {
@@ -1178,10 +1229,13 @@ void launch_step(const Sys& S, cudaStream_t st, int fp64, int forces_only,
     else k_forces64<false><<<g, STEP_THREADS, 0, st>>>(S);
     if (!forces_only) k_integrate64<<<g, STEP_THREADS, 0, st>>>(S, h, use_cond);
   } else {
-    const unsigned g = blocks_for(S.n, 256) > 0 ? blocks_for(S.n, 256) : 1;
+    const unsigned g0 = blocks_for(S.n, 256) > 0 ? blocks_for(S.n, 256) : 1;
     auto K = [&](auto nl16, auto fo, auto cub) {
-      k_step_nl<decltype(nl16)::value, decltype(fo)::value, decltype(cub)::value>
-          <<<g, 256, 0, st>>>(S, h, use_cond);
+      constexpr int v = (decltype(nl16)::value ? 4 : 0) + (decltype(fo)::value ? 2 : 0) +
+                        (decltype(cub)::value ? 1 : 0);
+      auto* kern = k_step_nl<decltype(nl16)::value, decltype(fo)::value, decltype(cub)::value>;
+      const unsigned r = resident_blocks(v, (const void*)kern, 256);
+      kern<<<(g0 < r ? g0 : r), 256, 0, st>>>(S, h, use_cond);
     };
     using T_ = std::true_type;
     using F_ = std::false_type;
