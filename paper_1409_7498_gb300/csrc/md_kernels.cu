@@ -749,14 +749,12 @@ __global__ void kb_rebin_cellsort(const Sys* __restrict__ T, const BlkMap* __res
 // other set (bond partners renamed to their new slots) and writes the
 // fixed-point position with a fresh displacement reference; tmp[s] then
 // receives the cell the sort put the slot in (read by the list build).
-__device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk, bool wrap) {
+__device__ __forceinline__ void rebin_permute_one(const Sys& S, uint32_t s, bool wrap) {
   Ctl* ctl = S.ctl;
   const int set = ctl->set;
   const SoA A = set ? S.s1 : S.s0;
   const SoA B = set ? S.s0 : S.s1;
   uint4* P = ctl->phase ? S.P1 : S.P0;
-  const uint32_t s = blk.b * blockDim.x + threadIdx.x;
-  if (s >= S.n) return;
   const uint32_t o = S.tmp[s];
   // every load first: a store into set B could alias a later load from set A
   // as far as the compiler knows, and would hold that load back
@@ -805,8 +803,18 @@ __device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk, 
   S.tmp[s] = key;
 }
 
+__device__ __forceinline__ void rebin_permute_body(const Sys& S, const Blk blk, bool wrap) {
+  const uint32_t s = blk.b * blockDim.x + threadIdx.x;
+  if (s < S.n) rebin_permute_one(S, s, wrap);
+}
+// Single system: the resident blocks' warps take 32-slot chunks strided by
+// the grid's warp count (no partial last wave, as in k_step_nl).
 __global__ void k_rebin_permute(Sys S, int wrap) {
-  rebin_permute_body(S, Blk{blockIdx.x, gridDim.x}, wrap != 0);
+  const uint32_t W = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c * 32u < S.n; c += W) {
+    const uint32_t i = c * 32u + (threadIdx.x & 31u);
+    if (i < S.n) rebin_permute_one(S, i, wrap != 0);
+  }
 }
 __global__ void kb_rebin_permute(const Sys* __restrict__ T, const BlkMap* __restrict__ M, const uint32_t* __restrict__ C) {
   if (blockIdx.x >= *C) return;
@@ -1201,14 +1209,15 @@ void launch_stage_input(const Sys& S, cudaStream_t st, const double* buf, int wh
 }
 
 // Blocks of `threads` threads of kernel `kern` resident on the whole current
-// device at once (cached per device and kernel variant).
+// device at once (cached per device and kernel id: 0-7 the step kernel's
+// variants).
 unsigned resident_blocks(int variant, const void* kern, int threads) {
   static std::mutex mu;
-  static unsigned cache[64][8];
+  static unsigned cache[64][16];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1u;
   std::lock_guard<std::mutex> lk(mu);
-  unsigned& c = cache[dev][variant & 7];
+  unsigned& c = cache[dev][variant & 15];
   if (!c) {
     int sms = 0, per = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -1333,7 +1342,10 @@ void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, c
   k_rebin_cellsort<<<gc, 256, 0, st>>>(S);
   H("rebin_cellsort", 1);
   H("rebin_permute", 0);
-  k_rebin_permute<<<gp, 256, 0, st>>>(S, mode != 2);
+  {
+    const unsigned r = resident_blocks(8, (const void*)k_rebin_permute, 256);
+    k_rebin_permute<<<(gp < r ? gp : r), 256, 0, st>>>(S, mode != 2);
+  }
   H("rebin_permute", 1);
   const unsigned gt = (unsigned)(S.tiles_y * S.nc[2]);
   const size_t sm = build_tile_smem(S);
