@@ -4,7 +4,7 @@ Both sides start from the same seeded synthetic inputs (synth); the oracle
 never receives anything the GPU produced.  Bars:
   * reaction step: bit-exact bonds, states and Table I counts;
   * forces, FP64 mode: relative 1e-12; FP32 mode: max_i |df_i| / RMS |f| and
-    RMS |df| / RMS |f| both <= 1e-5 (the north-star tolerance);
+    RMS |df| / RMS |f| both <= 1e-5 (the stated force tolerance);
   * FP64-mode trajectories: positions within 1e-9 after hundreds of steps and
     bit-identical bond lists (same random draws, same decisions).
 """

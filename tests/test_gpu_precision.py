@@ -1,5 +1,5 @@
-"""Precision of the FP32-force path against the FP64 oracle (the north-star
-precision statement), per workload family:
+"""Precision of the FP32-force path against the FP64 oracle, per workload
+family:
 
 * energy: without a thermostat (gamma = 0), the total energy
   E = KE(stored velocities) + PE drifts no more on the GPU (FP32 forces, FP64
@@ -8,7 +8,6 @@ precision statement), per workload family:
 * end-to-end distance: chain growth with reactions and the Langevin
   thermostat gives the same mean squared end-to-end distance of the chains
   on both sides (8 seeds each, within 3 standard errors).
-The measured numbers are listed in the design doc.
 """
 import multiprocessing as mp
 import os
