@@ -26,6 +26,8 @@ import numpy as np
 
 TYPE_B = 0
 TYPE_A = 1
+TYPE_E = 2   # chain end unit E of an E-P_n-E chain (Sec. II.B)
+TYPE_P = 3   # repeat unit P of an E-P_n-E chain (does not react)
 DENSITY = 0.85
 BASE_SEED = 14097498
 
@@ -95,6 +97,71 @@ def step_growth(n_B: int, n_A: int, f: int, seed: int, rho: float = DENSITY, kT:
     typ[a_ids] = TYPE_A
     st[a_ids] = f
     return Inputs(L, x, v, typ, st, "step", f, seed)
+
+
+def ep_chains(n_chains: int, n_rep: int, f: int, seed: int, rho: float = DENSITY,
+              kT: float = 1.0, jitter: float = 0.05):
+    """Step growth of Sec. II.B: E-P_n-E chains (n = n_rep repeat units,
+    chain bonds FENE) and crosslinkers X of functionality f in the
+    stoichiometric ratio f n_X = 2 n_chains (two end units per chain).
+
+    Simple cubic lattice with the chain length along x: each x-run of
+    n_rep + 2 consecutive sites is either one chain (bond length = the
+    lattice spacing, 1.06 sigma at rho = 0.85) or n_rep + 2 crosslinkers;
+    which runs hold chains is seeded.  Returns (Inputs, box edges, chain
+    bonds): Inputs.L is the x edge only, the box is the 3-tuple; the bonds
+    are an (m, 2) array (lower id first)."""
+    rng = np.random.default_rng(seed)
+    run = n_rep + 2
+    n_x_runs = int(math.ceil(2 * n_chains / f / run))
+    n_runs = n_chains + n_x_runs
+    # lattice of (run * mx) x my x mz sites with mx * my * mz >= n_runs
+    m = max(1, int(math.ceil((n_runs * run) ** (1.0 / 3.0) / run)))
+    my = mz = max(1, int(math.ceil(math.sqrt(n_runs / m))))
+    while m * my * mz < n_runs:
+        my += 1
+    n = n_runs * run
+    a = (n / rho / (m * run * my * mz)) ** (1.0 / 3.0)
+    dims = (m * run * a, my * a, mz * a)  # box edges (not cubic in general)
+    runs = rng.permutation(m * my * mz)[:n_runs]
+    is_chain = np.zeros(n_runs, bool)
+    is_chain[rng.permutation(n_runs)[:n_chains]] = True
+    x = np.zeros((n, 3))
+    typ = np.full(n, TYPE_A, np.uint8)
+    st = np.full(n, f, np.int8)
+    bonds = []
+    for r in range(n_runs):
+        q = runs[r]
+        ix, iy, iz = q % m, (q // m) % my, q // (m * my)
+        for u in range(run):
+            p = r * run + u
+            x[p] = ((ix * run + u + 0.5) * a, (iy + 0.5) * a, (iz + 0.5) * a)
+        if is_chain[r]:
+            base = r * run
+            typ[base:base + run] = TYPE_P
+            typ[base] = typ[base + run - 1] = TYPE_E
+            st[base:base + run] = 0
+            bonds += [(base + u, base + u + 1) for u in range(run - 1)]
+    x += jitter * a * (rng.random((n, 3)) - 0.5)
+    box = np.array(dims)
+    x = np.where(x >= box, x - box, x)
+    x = np.where(x < 0.0, x + box, x)
+    v = maxwell_velocities(n, kT, 1.0, rng)
+    return (Inputs(dims[0], np.ascontiguousarray(x), v, typ, st, "ep", f, seed),
+            dims, np.array(bonds, np.int64).reshape(-1, 2))
+
+
+def ep_scheme(f: int, k: float, theta: int = 10, r_react: float = 1.1,
+              bond_style: int = 0, selection: int = 0) -> dict:
+    """Sec. II.B: X^s (s in 1..f) + E^0 -> bond, X to s - 1 (delta_A = -1),
+    E to 1 (delta_T = +1).  Valences: X f, E 2 (chain bond + one X), P 2."""
+    mv = [0] * 8
+    mv[TYPE_A] = f
+    mv[TYPE_E] = 2
+    mv[TYPE_P] = 2
+    return dict(mask_A=1 << TYPE_A, mask_T=1 << TYPE_E, a_lo=1, a_hi=f, t_lo=0, t_hi=0, dA=-1,
+                dT=+1, k=k, theta=theta, r_react=r_react, bond_style=bond_style,
+                max_valence=tuple(mv), selection=selection)
 
 
 def step_growth_sites(n_total: int, f: int, seed: int, **kw) -> Inputs:

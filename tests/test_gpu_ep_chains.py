@@ -1,0 +1,113 @@
+"""Step growth on the paper's own system type (Sec. II.B): E-P3-E chains
+joined by f = 4 crosslinkers X that react with the chain end units E, on
+the GPU against the FP64 oracle.
+
+The chains are FENE-bonded from the start and the box is not cubic, so this
+covers what the single-bead step-growth workloads do not: initial bonds in
+the input, bond forces on every particle of a chain, reactions at chain
+ends only, and the general (per-axis) step kernel path.  Both sides start
+from the same seeded synthetic input (synth.ep_chains); nothing flows from
+the GPU to the oracle.  Bars: forces as in test_gpu_parity (FP64 1e-12,
+FP32 1e-5 max and RMS over RMS); FP64-mode runs with reactions: positions
+within 1e-9 and identical bond lists and states.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+import synth
+from helpers import (bonds_of_oracle, canonical, force_errors, gpu, gpu_reaction, oracle_system,
+                     orc_reaction)
+
+pytestmark = pytest.mark.gpu
+
+F = 4
+SEED = 2718
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return gpu()
+
+
+def workload(P):
+    inp, dims, cb = synth.ep_chains(400, 3, F, SEED)
+    bonds = np.zeros(len(cb), P.BOND_DTYPE)
+    bonds["a"], bonds["t"] = cb[:, 0], cb[:, 1]
+    return inp, dims, bonds
+
+
+def min_image_max(a, b, dims):
+    d = a - b
+    for k in range(3):
+        d[:, k] -= dims[k] * np.round(d[:, k] / dims[k])
+    return np.abs(d).max()
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_forces_with_chain_bonds(P, fp64):
+    inp, dims, bonds = workload(P)
+    o = oracle_system(inp.x, inp.v, inp.type, inp.state, F, bonds)
+    f_ref, e_ref = orc.forces(o, orc.MDParams(L=dims, seed=SEED), use_cells=True)
+    desc = P.make_desc(inp.n, dims, adj_cap=F, fp64=fp64, seed=SEED)
+    with P.System(desc, inp.x, inp.v, inp.type, inp.state, bonds=bonds) as g:
+        f, e = g.forces()
+    err = force_errors(f, f_ref)
+    tol = 1e-12 if fp64 else 1e-5
+    assert err["max_over_rms"] < tol, err
+    assert e == pytest.approx(e_ref, rel=tol)
+
+
+def test_fp64_run_with_end_reactions_matches_oracle(P):
+    inp, dims, bonds = workload(P)
+    sch = synth.ep_scheme(F, k=5.0)  # p = k dt Theta = 0.25: many bonds early
+    o = oracle_system(inp.x, inp.v, inp.type, inp.state, F, bonds)
+    md = orc.MDParams(L=dims, seed=SEED)
+    desc = P.make_desc(inp.n, dims, adj_cap=F, fp64=True, seed=SEED)
+    with P.System(desc, inp.x, inp.v, inp.type, inp.state, bonds=bonds) as g:
+        g.set_reaction(gpu_reaction(P, sch))
+        for chunk in range(3):
+            orc.run(o, md, orc_reaction(sch), 100)
+            g.run(100)
+            assert g.step() == o.step
+            assert min_image_max(g.positions(), o.x, dims) < 1e-9
+            assert np.array_equal(canonical(g.bonds()), canonical(bonds_of_oracle(o)))
+            assert (g.states() == o.state).all()
+        b = canonical(g.bonds())
+        st = g.states()
+    # Sec. II.B: only X-E bonds form; each E reacts at most once (state 0 -> 1),
+    # each X at most f times (state f -> f - bonds); the chain bonds stay
+    new = b[b[:, 0] > 0]
+    assert len(new) > 20
+    ty = inp.type
+    assert (ty[new[:, 1]] == synth.TYPE_A).all() and (ty[new[:, 2]] == synth.TYPE_E).all()
+    e_deg = np.bincount(new[:, 2], minlength=inp.n)
+    x_deg = np.bincount(new[:, 1], minlength=inp.n)
+    E = ty == synth.TYPE_E
+    X = ty == synth.TYPE_A
+    assert (e_deg[E] == st[E]).all() and e_deg[E].max() <= 1
+    assert (x_deg[X] == F - st[X]).all()
+    assert (st[ty == synth.TYPE_P] == 0).all()
+    assert len(b) - len(new) == len(bonds)
+
+
+def test_fp32_reaction_steps_bit_exact(P):
+    """Reaction steps from the same state on both sides (FP32 force mode: the
+    reaction's distance test and draws are FP64 / integer on the device)."""
+    inp, dims, bonds = workload(P)
+    sch = synth.ep_scheme(F, k=5.0)
+    o = oracle_system(inp.x, inp.v, inp.type, inp.state, F, bonds)
+    md = orc.MDParams(L=dims, seed=SEED)
+    desc = P.make_desc(inp.n, dims, adj_cap=F, seed=SEED)
+    with P.System(desc, inp.x, inp.v, inp.type, inp.state, bonds=bonds) as g:
+        g.set_reaction(gpu_reaction(P, sch))
+        for step in (10, 20, 30):
+            tr_o = orc.react(o, md, orc_reaction(sch), step=step, use_cells=True)
+            tr_g = g.react_once(step)
+            assert tr_g == tr_o, (step, tr_g, tr_o)
+            assert (g.states() == o.state).all()
+            assert np.array_equal(canonical(g.bonds()), canonical(bonds_of_oracle(o)))
+    assert tr_o["formed"] >= 0 and o.nb > len(bonds)
