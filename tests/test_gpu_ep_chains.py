@@ -111,3 +111,76 @@ def test_fp32_reaction_steps_bit_exact(P):
             assert (g.states() == o.state).all()
             assert np.array_equal(canonical(g.bonds()), canonical(bonds_of_oracle(o)))
     assert tr_o["formed"] >= 0 and o.nb > len(bonds)
+
+
+# --- kinetics: 32 seeds on each side -----------------------------------------
+KIN_SEEDS = 32
+KIN_STEPS = 2000
+KIN_K = 0.5
+
+
+def kin_input(seed):
+    inp, dims, cb = synth.ep_chains(200, 3, F, seed)
+    return inp, dims, cb
+
+
+def kin_curves(bonds, countsX, n_chain_bonds, n_ends, n_X):
+    """conversion of the end units and the crosslinker fractions x_s (s = bonds
+    formed, Eq. step-fraction) from the bond totals and the X populations."""
+    conv = (bonds - n_chain_bonds) / n_ends
+    xs = countsX[..., F::-1] / n_X
+    return np.concatenate([conv[..., None], xs], axis=-1)
+
+
+def kin_oracle_run(seed):
+    inp, dims, cb = kin_input(seed)
+    o = orc.System(inp.x, inp.v, inp.type, inp.state, cap=F)
+    for a, t in cb:
+        o.add_bond(int(a), int(t), 0, 0)
+    obs = orc.run(o, orc.MDParams(L=dims, seed=seed), orc.Reaction(**synth.ep_scheme(F, k=KIN_K)),
+                  KIN_STEPS)
+    bonds = np.array([ob["bonds"] for ob in obs], np.float64)
+    cX = np.array([ob["counts"][synth.TYPE_A][:F + 1] for ob in obs], np.float64)
+    n_X = int((inp.type == synth.TYPE_A).sum())
+    return kin_curves(bonds, cX, len(cb), 2 * 200, n_X)
+
+
+def test_end_reaction_kinetics_32_seeds_match_the_oracle(P):
+    import multiprocessing as mp
+    import os
+    seeds = [SEED + 100 + s for s in range(KIN_SEEDS)]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        pending = pool.map_async(kin_oracle_run, seeds)
+        systems, meta = [], []
+        for seed in seeds:
+            inp, dims, cb = kin_input(seed)
+            bonds = np.zeros(len(cb), P.BOND_DTYPE)
+            bonds["a"], bonds["t"] = cb[:, 0], cb[:, 1]
+            desc = P.make_desc(inp.n, dims, adj_cap=F, seed=seed)
+            g = P.System(desc, inp.x, inp.v, inp.type, inp.state, bonds=bonds)
+            g.set_reaction(gpu_reaction(P, synth.ep_scheme(F, k=KIN_K)))
+            systems.append(g)
+            meta.append((len(cb), int((inp.type == synth.TYPE_A).sum())))
+        with P.Batch() as b:
+            for g in systems:
+                b.add(g)
+            b.run(KIN_STEPS)
+            b.sync()
+        gpu_curves = []
+        for g, (ncb, n_X) in zip(systems, meta):
+            h = g.history()
+            gpu_curves.append(kin_curves(h["bonds"].astype(np.float64),
+                                         h["counts"][:, synth.TYPE_A, :F + 1].astype(np.float64),
+                                         ncb, 2 * 200, n_X))
+            g.close()
+        orc_curves = np.array(pending.get())
+    gpu_curves = np.array(gpu_curves)
+    assert gpu_curves.shape == orc_curves.shape == (KIN_SEEDS, KIN_STEPS // 10, F + 2)
+    idx = np.arange(19, KIN_STEPS // 10, 20)  # ten sample times
+    mg, mo = gpu_curves[:, idx].mean(0), orc_curves[:, idx].mean(0)
+    se = np.sqrt(gpu_curves[:, idx].var(0, ddof=1) / KIN_SEEDS +
+                 orc_curves[:, idx].var(0, ddof=1) / KIN_SEEDS)
+    z = np.abs(mg - mo) / np.maximum(se, 1e-12)
+    # within 2 combined standard errors at (nearly) every point, none beyond 3.5
+    assert (z <= 2.0).mean() >= 0.9 and z.max() <= 3.5, z
+    assert mg[-1, 0] > 0.3  # the runs went far enough to test something
