@@ -490,35 +490,46 @@ __global__ void __launch_bounds__(RX_THREADS)
 __global__ void __launch_bounds__(RX_THREADS) k_obs_sums(Sys S, double mass) {
   Ctl* ctl = S.ctl;
   const SoA B = ctl->set ? S.s1 : S.s0;
-  __shared__ double red[4][RX_THREADS];
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  // grid-strided sums per thread, then a fixed warp tree and the warps in
+  // order: few FP64 additions per slot, the same order on every call
   double ke = 0.0, px = 0.0, py = 0.0, pz = 0.0;
-  if (i < S.n) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) {
     const double vx = B.vx[i], vy = B.vy[i], vz = B.vz[i];
-    ke = 0.5 * mass * (vx * vx + vy * vy + vz * vz);
-    px = mass * vx;
-    py = mass * vy;
-    pz = mass * vz;
+    ke += vx * vx + vy * vy + vz * vz;
+    px += vx;
+    py += vy;
+    pz += vz;
   }
-  red[0][threadIdx.x] = ke;
-  red[1][threadIdx.x] = px;
-  red[2][threadIdx.x] = py;
-  red[3][threadIdx.x] = pz;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ke += __shfl_down_sync(0xFFFFFFFFu, ke, o);
+    px += __shfl_down_sync(0xFFFFFFFFu, px, o);
+    py += __shfl_down_sync(0xFFFFFFFFu, py, o);
+    pz += __shfl_down_sync(0xFFFFFFFFu, pz, o);
+  }
+  __shared__ double red[4][RX_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = ke;
+    red[1][wid] = px;
+    red[2][wid] = py;
+    red[3][wid] = pz;
+  }
   __syncthreads();
-  for (int w = RX_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
-    __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+    S.red[4 * (size_t)blockIdx.x + threadIdx.x] = (threadIdx.x == 0 ? 0.5 * mass : mass) * t;
   }
-  if (threadIdx.x < 4) S.red[4 * (size_t)blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// The per-block sums reduced to one value each, in a fixed order (thread t
-// adds blocks t, t + 256, ...; then a fixed tree): red[4 nblk .. 4 nblk + 3].
-__global__ void __launch_bounds__(RX_THREADS) k_obs_final(Sys S, uint32_t nblk) {
+// The nsum per-block sums reduced to one value each, in a fixed order (thread
+// t adds blocks t, t + 256, ...; then a fixed tree), written to
+// red[4 nblk .. 4 nblk + 3].
+__global__ void __launch_bounds__(RX_THREADS) k_obs_final(Sys S, uint32_t nsum, uint32_t nblk) {
   __shared__ double part[4][RX_THREADS];
   double a[4] = {0.0, 0.0, 0.0, 0.0};
-  for (uint32_t b = threadIdx.x; b < nblk; b += blockDim.x)
+  for (uint32_t b = threadIdx.x; b < nsum; b += blockDim.x)
     for (int q = 0; q < 4; ++q) a[q] += S.red[4 * (size_t)b + q];
   for (int q = 0; q < 4; ++q) part[q][threadIdx.x] = a[q];
   __syncthreads();
@@ -641,8 +652,10 @@ void launch_pair_hist(const Sys& S, cudaStream_t st, const PairClass& a, const P
 void launch_observables(const Sys& S, cudaStream_t st, int nblocks) {
   cudaMemsetAsync(&S.hist[S.hist_cap], 0, sizeof(HistRec), st);
   k_obs_hist<<<nblocks, RX_THREADS, 0, st>>>(S, -1, 0);
-  k_obs_sums<<<nblocks, RX_THREADS, 0, st>>>(S, S.mass);
-  k_obs_final<<<1, RX_THREADS, 0, st>>>(S, (uint32_t)nblocks);
+  // the sums on at most 8 blocks per SM, strided over the slots
+  const unsigned nsum = nblocks < 1216 ? (unsigned)nblocks : 1216u;
+  k_obs_sums<<<nsum, RX_THREADS, 0, st>>>(S, S.mass);
+  k_obs_final<<<1, RX_THREADS, 0, st>>>(S, nsum, (uint32_t)nblocks);
 }
 
 int batch_rx_kernel_count() { return 6; }
