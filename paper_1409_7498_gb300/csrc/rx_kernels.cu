@@ -445,33 +445,19 @@ __device__ __forceinline__ void obs_hist_body(const Sys& S, const Blk blk, long 
   __shared__ int32_t h[PRX_MAX_TYPES * PRX_MAX_STATES];
   for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x) h[k] = 0;
   __syncthreads();
-  // Block-strided over the slots, four consecutive slots per thread (one
-  // 4-byte load of the types and one of the states); within a warp, lanes
-  // with the same (type, state) bin are counted by one shared atomic of
-  // their leader.
+  // Block-strided over the slots; within a warp, lanes with the same
+  // (type, state) bin are counted by one shared atomic of their leader.
   const int lane = threadIdx.x & 31;
-  for (uint32_t base = blk.b * blockDim.x * 4u; base < S.n; base += blk.nb * blockDim.x * 4u) {
-    const uint32_t i0 = base + 4u * threadIdx.x;
-    uint32_t tw = 0xFFFFFFFFu, sw = 0u;  // absent slots: type 255, outside the bins
-    if (i0 + 3u < S.n) {
-      tw = *reinterpret_cast<const uint32_t*>(B.type + i0);
-      sw = *reinterpret_cast<const uint32_t*>(B.state + i0);
-    } else {
-      for (uint32_t q = 0; q < 4u; ++q)
-        if (i0 + q < S.n) {
-          tw = (tw & ~(0xFFu << (8 * q))) | ((uint32_t)B.type[i0 + q] << (8 * q));
-          sw |= (uint32_t)(uint8_t)B.state[i0 + q] << (8 * q);
-        }
+  for (uint32_t base = blk.b * blockDim.x; base < S.n; base += blk.nb * blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    int key = -1;
+    if (i < S.n) {
+      const uint32_t t = B.type[i];
+      const int s = B.state[i];
+      if (t < PRX_MAX_TYPES && s >= 0 && s < PRX_MAX_STATES) key = (int)t * PRX_MAX_STATES + s;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t t = (tw >> (8 * q)) & 0xFFu;
-      const int s = (int)(int8_t)((sw >> (8 * q)) & 0xFFu);
-      const int key = (t < PRX_MAX_TYPES && s >= 0 && s < PRX_MAX_STATES)
-                          ? (int)t * PRX_MAX_STATES + s : -1;
-      const unsigned grp = __match_any_sync(0xFFFFFFFFu, key);
-      if (key >= 0 && lane == __ffs(grp) - 1) atomicAdd(&h[key], __popc(grp));
-    }
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, key);
+    if (key >= 0 && lane == __ffs(grp) - 1) atomicAdd(&h[key], __popc(grp));
   }
   __syncthreads();
   const unsigned long long slot = record ? ctl->hist_count % S.hist_cap : S.hist_cap;
