@@ -268,8 +268,10 @@ int prx_profile_end(prx_system* sys, prx_kernel_time* out, uint32_t cap, uint32_
 /* Largest system prx_react_noalloc accepts. */
 #define PRX_NOALLOC_MAX_N 16384
 
-/* One reaction step (the same rule, draws and tie-breaking as
- * prx_react_once) on device arrays the caller owns, allocating nothing.
+/* One reaction step (the same rules, draws and tie-breaking as
+ * prx_react_once: rx->selection picks Table I's random rule or the
+ * nearest-partner rule of Sec. IV.A) on device arrays the caller owns,
+ * allocating nothing.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory themselves, e.g. code that must stay within
  * a memory budget fixed by a host framework, or that runs inside an
@@ -285,12 +287,21 @@ int prx_profile_end(prx_system* sys, prx_kernel_time* out, uint32_t cap, uint32_
  * Scratch memory: one static device array sized for PRX_NOALLOC_MAX_N
  * particles, held by every GPU that loads the library until the process
  * exits; n above that limit returns PRX_ECAPACITY.  The first call on a
- * device looks up the array's device address with that device current
- * (make that first call before any stream capture).  Every call shares the
- * array: calls whose work overlaps on the GPU race, so serialise them.  The
- * call is queued on cuda_stream (NULL: the legacy default stream) and waits
- * for it before returning the status (PRX_ECAPACITY when a valence or
- * bonds_cap limit was hit). */
+ * device looks up the array's device address with that device current.
+ * Every call shares the array: calls whose work overlaps on the GPU race, so
+ * serialise them.  The call is queued on cuda_stream (NULL: the legacy
+ * default stream), copies its counters into host memory and waits for the
+ * stream before returning, so it must not be called while that stream is
+ * being captured into a CUDA graph.
+ *
+ * Errors: PRX_EINVAL for a bad descriptor (as prx_set_reaction, including an
+ * unknown selection rule) or a missing pointer.  PRX_ECAPACITY when a pair
+ * would exceed a particle's valence (min(max_valence[type], adj_cap): that
+ * pair forms no bond and takes no place in the output) or more bonds formed
+ * than bonds_cap (the first bonds_cap, in ascending id of A, are applied and
+ * written; the rest are not applied); every other pair is still applied and
+ * written, and the trace counts every surviving pair, as prx_react_once
+ * does. */
 int prx_react_noalloc(const prx_reaction_desc* rx, const double* box, double dt, uint64_t seed,
                       uint64_t step, uint32_t n, const double* d_pos, const uint8_t* d_type,
                       int8_t* d_state, uint32_t adj_cap, uint8_t* d_nadj, uint32_t* d_adj,

@@ -9,9 +9,12 @@
 // library until the process exits.
 //
 // The candidate search is all-pairs (at most PRX_NOALLOC_MAX_N particles), so
-// no cell list or neighbour list is needed.  The rule is the same as that of
-// prx_react_once: same keyed Philox draws, same FP64 distance test, same
-// tie-breaking, so the two agree bit for bit on the same state.
+// no cell list or neighbour list is needed.  Both selection rules of
+// prx_react_once are implemented with its keyed Philox draws, its FP64
+// distance test and its tie-breaking, so the two agree bit for bit on the
+// same state: Table I's random rule (one T per A, then one A per T, each the
+// smallest selection key) and the LAMMPS nearest-partner rule of Sec. IV.A
+// (mutual nearest A-T pairs, then the acceptance draw).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -23,8 +26,9 @@ namespace {
 using namespace prx;
 
 struct NaScratch {
-  uint32_t win[PRX_NOALLOC_MAX_N];  // chosen T of each A (Table I step 5)
-  uint32_t fin[PRX_NOALLOC_MAX_N];  // surviving pairs (step 7)
+  uint32_t win[PRX_NOALLOC_MAX_N];  // random rule: chosen T of each A (Table I step 5);
+                                    // nearest rule: nearest partner of each A and T
+  uint32_t fin[PRX_NOALLOC_MAX_N];  // surviving pairs (step 7), by A
   unsigned long long trace[4];
   unsigned int nbonds;
   int status;
@@ -60,26 +64,67 @@ __device__ __forceinline__ unsigned long long na_key64(uint4 w) {
   return ((unsigned long long)w.x << 32) | w.y;
 }
 
-// Steps 1-5, one thread per particle id, all pairs.
+// Exact FP64 test of Table I step 1 for the pair (i, j): the minimum-image
+// separation x_j - x_i, r^2 = fma(dz, dz, fma(dy, dy, dx dx)), strict
+// r^2 < r_react^2.  Returns r^2, or a negative value when out of range.
+__device__ __forceinline__ double na_r2(const NaArgs& a, uint32_t i, uint32_t j, double xi,
+                                        double yi, double zi) {
+  const double dx = min_image(__dsub_rn(a.pos[3 * (size_t)j], xi), a.L[0], a.halfL[0]);
+  const double dy = min_image(__dsub_rn(a.pos[3 * (size_t)j + 1], yi), a.L[1], a.halfL[1]);
+  const double dz = min_image(__dsub_rn(a.pos[3 * (size_t)j + 2], zi), a.L[2], a.halfL[2]);
+  const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+  return r2 < a.R.rr2 ? r2 : -1.0;
+}
+
+__device__ __forceinline__ bool na_bonded(const NaArgs& a, uint32_t i, uint32_t j) {
+  const uint32_t nb = a.nadj[i];
+  bool bonded = false;
+  for (uint32_t b = 0; b < nb; ++b) bonded |= (a.adj[(size_t)i * a.cap + b] & SLOT_MASK) == j;
+  return bonded;
+}
+
+// LAMMPS rule (Sec. IV.A): the eligible partner of the other kind (a T when
+// want_T, else an A) within r_react of particle i, not bonded to it, of
+// smallest exact r^2, ties to the smaller id; in_range counts the pairs in
+// range.
+__device__ __forceinline__ uint32_t na_nearest(const NaArgs& a, uint32_t i, bool want_T,
+                                               unsigned long long& in_range) {
+  const double xi = a.pos[3 * (size_t)i], yi = a.pos[3 * (size_t)i + 1], zi = a.pos[3 * (size_t)i + 2];
+  uint32_t best = NONE;
+  double best_r2 = 0.0;
+  for (uint32_t j = 0; j < a.n; ++j) {
+    if (j == i) continue;
+    const bool ok = want_T ? na_window(a.R.mask_T, a.R.t_lo, a.R.t_hi, a.type[j], a.state[j])
+                           : na_window(a.R.mask_A, a.R.a_lo, a.R.a_hi, a.type[j], a.state[j]);
+    if (!ok) continue;
+    const double r2 = na_r2(a, i, j, xi, yi, zi);
+    if (r2 < 0.0 || na_bonded(a, i, j)) continue;
+    ++in_range;
+    // j ascends, so a tie keeps the earlier (smaller) id
+    if (best == NONE || r2 < best_r2) {
+      best = j;
+      best_r2 = r2;
+    }
+  }
+  return best;
+}
+
+// Steps 1-5, one thread per particle id, all pairs (random rule); for the
+// nearest rule each eligible A records its nearest eligible T.
 __global__ void k_na_find(NaArgs a) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   uint32_t best = NONE;
   unsigned long long cand = 0, ret = 0;
-  if (na_window(a.R.mask_A, a.R.a_lo, a.R.a_hi, a.type[i], a.state[i])) {
+  const bool isA = na_window(a.R.mask_A, a.R.a_lo, a.R.a_hi, a.type[i], a.state[i]);
+  if (isA && a.R.rule == PRX_SELECT_NEAREST) {
+    best = na_nearest(a, i, true, cand);
+  } else if (isA) {
     const double xi = a.pos[3 * (size_t)i], yi = a.pos[3 * (size_t)i + 1], zi = a.pos[3 * (size_t)i + 2];
-    const uint32_t nb = a.nadj[i];
     unsigned long long bestkey = 0ull;
     for (uint32_t j = 0; j < a.n; ++j) {
       if (j == i || !na_window(a.R.mask_T, a.R.t_lo, a.R.t_hi, a.type[j], a.state[j])) continue;
-      const double dx = min_image(__dsub_rn(a.pos[3 * (size_t)j], xi), a.L[0], a.halfL[0]);
-      const double dy = min_image(__dsub_rn(a.pos[3 * (size_t)j + 1], yi), a.L[1], a.halfL[1]);
-      const double dz = min_image(__dsub_rn(a.pos[3 * (size_t)j + 2], zi), a.L[2], a.halfL[2]);
-      const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
-      if (!(r2 < a.R.rr2)) continue;
-      bool bonded = false;
-      for (uint32_t b = 0; b < nb; ++b) bonded |= (a.adj[(size_t)i * a.cap + b] & SLOT_MASK) == j;
-      if (bonded) continue;
+      if (na_r2(a, i, j, xi, yi, zi) < 0.0 || na_bonded(a, i, j)) continue;
       ++cand;
       const uint4 wa = keyed_draw(a.seed, a.step, i, j, TAG_ACCEPT);
       if (!u53_below(wa.x, wa.y, a.R.p53)) continue;
@@ -96,14 +141,35 @@ __global__ void k_na_find(NaArgs a) {
   if (ret) atomicAdd(&a.sc->trace[1], ret);
 }
 
-// Steps 6-7: an A keeps its T only if its key Philox(step, id_T, id_A) is the
-// smallest among the A's that chose the same T.
+// Nearest rule: each eligible T records its nearest eligible A.  A and T
+// are disjoint sets, so the two kinds share win[].
+__global__ void k_na_find_T(NaArgs a) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n || !na_window(a.R.mask_T, a.R.t_lo, a.R.t_hi, a.type[i], a.state[i])) return;
+  unsigned long long unused = 0;
+  a.sc->win[i] = na_nearest(a, i, false, unused);
+}
+
+// Steps 6-7 (random rule): an A keeps its T only if its key
+// Philox(step, id_T, id_A) is the smallest among the A's that chose the same
+// T.  Nearest rule: an A and the T it picked react when the T picked it too
+// and u < k dt Theta, drawn with the pair's smaller id first.
 __global__ void k_na_select(NaArgs a) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const uint32_t T = a.sc->win[i];
   uint32_t fin = NONE;
-  if (T != NONE) {
+  const bool isA = na_window(a.R.mask_A, a.R.a_lo, a.R.a_hi, a.type[i], a.state[i]);
+  if (T != NONE && isA && a.R.rule == PRX_SELECT_NEAREST) {
+    if (a.sc->win[T] == i) {
+      atomicAdd(&a.sc->trace[1], 1ull);  // mutual pairs
+      const uint4 w = keyed_draw(a.seed, a.step, min(i, T), max(i, T), TAG_NEAREST);
+      if (u53_below(w.x, w.y, a.R.p53)) {
+        atomicAdd(&a.sc->trace[2], 1ull);  // accepted pairs
+        fin = T;
+      }
+    }
+  } else if (T != NONE && isA) {
     atomicAdd(&a.sc->trace[2], 1ull);
     const unsigned long long mine = na_key64(keyed_draw(a.seed, a.step, T, i, TAG_SEL_T));
     bool keep = true;
@@ -118,17 +184,33 @@ __global__ void k_na_select(NaArgs a) {
 }
 
 // Step 9 in one block: bonds appended in ascending id of A (a running count
-// over the ids, no atomics), adjacency rows and states updated.
+// over the ids, no atomics), adjacency rows and states updated.  A pair that
+// would exceed a particle's valence forms no bond and takes no place in the
+// bond list (status PRX_ECAPACITY); the surviving pairs are all counted in
+// the trace, as prx_react_once counts them.  Each A and each T is in at most
+// one pair, so the valence reads see the rows as they were before this step.
 __global__ void k_na_apply(NaArgs a) {
   __shared__ uint32_t wtot[32];
-  __shared__ uint32_t carry;
-  if (threadIdx.x == 0) carry = 0u;
+  __shared__ uint32_t carry, surv;
+  if (threadIdx.x == 0) carry = surv = 0u;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (uint32_t base = 0; base < a.n; base += blockDim.x) {
     const uint32_t i = base + threadIdx.x;
     const uint32_t T = i < a.n ? a.sc->fin[i] : NONE;
-    const bool has = T != NONE;
+    bool has = false;
+    uint32_t na = 0, nt = 0;
+    if (T != NONE) {
+      const uint32_t ta = a.type[i], tt = a.type[T];
+      const uint32_t capA = a.R.maxval[ta] < a.cap ? a.R.maxval[ta] : a.cap;
+      const uint32_t capT = a.R.maxval[tt] < a.cap ? a.R.maxval[tt] : a.cap;
+      na = a.nadj[i];
+      nt = a.nadj[T];
+      has = na < capA && nt < capT;
+      if (!has) atomicCAS(&a.sc->status, 0, PRX_ECAPACITY);
+    }
+    const uint32_t sbal = __ballot_sync(0xFFFFFFFFu, T != NONE);
+    if (lane == 0 && sbal) atomicAdd(&surv, __popc(sbal));
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, has);
     if (lane == 0) wtot[wid] = __popc(bal);
     __syncthreads();
@@ -136,11 +218,7 @@ __global__ void k_na_apply(NaArgs a) {
     for (int w = 0; w < wid; ++w) before += wtot[w];
     const uint32_t pos = before + __popc(bal & ((1u << lane) - 1u));
     if (has) {
-      const uint32_t ta = a.type[i], tt = a.type[T];
-      const uint32_t capA = a.R.maxval[ta] < a.cap ? a.R.maxval[ta] : a.cap;
-      const uint32_t capT = a.R.maxval[tt] < a.cap ? a.R.maxval[tt] : a.cap;
-      const uint32_t na = a.nadj[i], nt = a.nadj[T];
-      if (na >= capA || nt >= capT || pos >= a.bonds_cap) {
+      if (pos >= a.bonds_cap) {
         atomicCAS(&a.sc->status, 0, PRX_ECAPACITY);
       } else {
         const uint32_t sbit = a.R.style << 31;
@@ -170,7 +248,7 @@ __global__ void k_na_apply(NaArgs a) {
   if (threadIdx.x == 0) {
     const uint32_t formed = carry < a.bonds_cap ? carry : a.bonds_cap;
     a.sc->nbonds = formed;
-    a.sc->trace[3] = carry;
+    a.sc->trace[3] = surv;
     *a.nbonds_out = formed;
   }
 }
@@ -211,6 +289,7 @@ extern "C" int prx_react_noalloc(const prx_reaction_desc* rx, const double* box,
   if (rx->a_lo > rx->a_hi || rx->t_lo > rx->t_hi || rx->theta < 1 || !(rx->k >= 0.0) ||
       !(rx->r_react > 0.0) || (rx->bond_style != PRX_BOND_FENE && rx->bond_style != PRX_BOND_MIRROR_LJ) ||
       ((rx->type_mask_A | rx->type_mask_T) >> PRX_MAX_TYPES) ||
+      (rx->selection != PRX_SELECT_RANDOM && rx->selection != PRX_SELECT_NEAREST) ||
       ((rx->type_mask_A & rx->type_mask_T) && !(rx->a_hi < rx->t_lo || rx->t_hi < rx->a_lo)))
     return PRX_EINVAL;
   for (int k = 0; k < 3; ++k)
@@ -250,6 +329,7 @@ extern "C" int prx_react_noalloc(const prx_reaction_desc* rx, const double* box,
   a.R.rr2 = rx->r_react * rx->r_react;
   a.R.rr2_pre = 0.f;
   a.R.style = (uint32_t)rx->bond_style;
+  a.R.rule = rx->selection;
   for (int t = 0; t < PRX_MAX_TYPES; ++t) a.R.maxval[t] = rx->max_valence[t];
   a.sc = sc;
 
@@ -259,6 +339,7 @@ extern "C" int prx_react_noalloc(const prx_reaction_desc* rx, const double* box,
     return PRX_ECUDA;
   const unsigned g = n ? (n + 255u) / 256u : 1u;
   k_na_find<<<g, 256, 0, st>>>(a);
+  if (a.R.rule == PRX_SELECT_NEAREST) k_na_find_T<<<g, 256, 0, st>>>(a);
   k_na_select<<<g, 256, 0, st>>>(a);
   k_na_apply<<<1, 1024, 0, st>>>(a);
   if (cudaGetLastError() != cudaSuccess) return PRX_ECUDA;

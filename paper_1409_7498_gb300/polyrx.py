@@ -345,9 +345,11 @@ PRX_NOALLOC_MAX_N = 16384
 
 
 def prx_react_noalloc(rx, box, dt, seed, step, n, d_pos, d_type, d_state, adj_cap, d_nadj, d_adj,
-                      d_bonds_out, bonds_cap, d_nbonds_out, stream=None) -> dict:
+                      d_bonds_out, bonds_cap, d_nbonds_out, stream=None, check=True):
     """Reaction step on caller-owned device buffers (integer device
-    addresses), allocating nothing; see prx_react_noalloc in polyrx.h."""
+    addresses), allocating nothing; see prx_react_noalloc in polyrx.h.
+    Returns the trace counts; with check=False, (status, trace) instead of
+    raising on a non-zero status (the outputs are written either way)."""
     b = (C.c_double * 3)(*([float(box)] * 3 if np.isscalar(box) else [float(v) for v in box]))
     t = prx_rx_trace()
     rc = lib().prx_react_noalloc(C.byref(rx), b, float(dt), int(seed) & 0xFFFFFFFFFFFFFFFF,
@@ -356,10 +358,13 @@ def prx_react_noalloc(rx, box, dt, seed, step, n, d_pos, d_type, d_state, adj_ca
                                  C.c_void_p(d_adj), C.c_void_p(d_bonds_out), int(bonds_cap),
                                  C.c_void_p(d_nbonds_out), C.c_void_p(stream) if stream else None,
                                  C.byref(t))
+    tr = dict(candidates=t.candidates, retained=t.retained, a_winners=t.a_winners,
+              formed=t.formed)
+    if not check:
+        return rc, tr
     if rc != PRX_OK:
         raise PolyrxError(rc, lib().prx_status_string(rc).decode())
-    return dict(candidates=t.candidates, retained=t.retained, a_winners=t.a_winners,
-                formed=t.formed)
+    return tr
 
 
 def prx_pair_histogram(h, a, b, r_max: float, nbins: int):
