@@ -1,29 +1,40 @@
 """Benchmark: particle-steps/s of the reactive MD hot path on GB300.
 
-Workload (default): 1,048,576-bead step growth (difunctional B monomers and
-A crosslinkers of functionality 4 at a 4:1 B:A site ratio, density 0.85,
-WCA + FENE + Langevin, dt = 0.005, reaction every Theta = 10 steps with
-r_react = 1.1 and k = 0.1), FP32 forces with FP64 integration.
+Headline workload: 1,048,576-bead step growth (difunctional B monomers and A
+crosslinkers of functionality 4 at a 4:1 B:A site ratio, density 0.85, WCA +
+FENE + Langevin, dt = 0.005, reaction every Theta = 10 steps with
+r_react = 1.1 and k = 0.1), FP32 forces with FP64 integration.  The start is
+the workload's recipe: seeded uniform placement, a capped-force WCA warm-up
+(2,000 steps with the pair force capped at 100, then 1,000 uncapped steps, no
+reactions, untimed).  The timed region is the whole reaction run: K bench
+steps of one reaction interval each (K = 2,000 by default: the 20,000 MD
+steps of the workload), every step of the hot path included.
 
 One bench step = one reaction interval: Theta MD steps (fused force +
-integrate kernel, conditional cell-list rebuilds) followed by the reaction
-step and its observables record, i.e. every step of the hot path.  The metric
-counts particles x MD steps.  Inputs are synthetic (seeded lattice placement,
-Maxwell velocities); the L2 cache is flushed between timed bench steps.
+integrate kernel, conditional neighbour-list rebuilds) followed by the
+reaction step and its populations record.  The metric counts particles x MD
+steps.  The L2 cache is flushed between timed bench steps.
 
-Multi-GPU (torchrun): every rank advances its own independent replica (own
-seed); there is no data-path collective ("scaling": "weak").
+The same JSON line carries the other workloads: the 1,250-bead FP64 step
+growth and the 33,096-bead chain growth at k = 0.01, 0.1 and 1 (each a full
+run, with its roofline and the oracle timed beside it), the batched ensemble
+(256 replicas) against one job at a time, and the serving stream (Poisson
+arrivals at 20 jobs/s, unscaled step counts) against serving the same trace
+one job at a time.
+
+Multi-GPU (torchrun): every rank advances its own independent replica of the
+headline workload (own seed) and its share of the ensemble's replicas; there
+is no data-path collective ("scaling": "weak").
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
-import math
 import os
 import subprocess
-import tempfile
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -38,18 +49,25 @@ N_BEADS = 1_048_576
 FUNC = 4
 K_RATE = 0.1
 THETA = 10
+MD_STEPS = 20_000
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SKINS = (0.3, 0.35, 0.4, 0.45, 0.5)  # autotuner candidates
+# warm-up of the uniform placement (App. A protocol): capped WCA, then uncapped
+F_CAP, CAP_STEPS, FREE_STEPS = 100.0, 2000, 1000
+WARM_SEED_OFFSET = 1_000_003  # the warm-up's thermostat draws differ from the run's
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=MD_STEPS // THETA,
+                    help="timed bench steps (reaction intervals of Theta MD steps)")
+    ap.add_argument("--warmup", type=int, default=10,
+                    help="untimed bench steps of MD on the warmed liquid before the timed run")
     ap.add_argument("--impl", default="polyrx", choices=["polyrx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
+    ap.add_argument("--cpu-budget", type=float, default=8.0,
+                    help="seconds of oracle work per CPU timing")
     ap.add_argument("--direct", action="store_true",
                     help="launch kernels one by one instead of CUDA graphs (for ncu launch lists)")
     ap.add_argument("--no-ensemble", action="store_true",
@@ -57,10 +75,13 @@ def parse():
     ap.add_argument("--ensemble-steps", type=int, default=20,
                     help="timed reaction intervals of the ensemble measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 1,250-bead and 33,096-bead workload lines")
     ap.add_argument("--skin", type=float, default=0.0,
                     help="Verlet skin to use (default: the library's autotuner picks it)")
     ap.add_argument("--serving-arrivals", type=int, default=64)
-    ap.add_argument("--serving-step-scale", type=float, default=0.1)
+    ap.add_argument("--serving-step-scale", type=float, default=1.0)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     return ap.parse_args()
 
 
@@ -71,12 +92,29 @@ def dist_env():
     return rank, world, local
 
 
-def inputs(rank: int):
-    return synth.step_growth_sites(N_BEADS, FUNC, synth.BASE_SEED + rank)
+def inputs(rank: int, placement: str = "uniform"):
+    return synth.step_growth_sites(N_BEADS, FUNC, synth.BASE_SEED + rank, placement=placement)
 
 
 def scheme():
     return synth.step_growth_scheme(FUNC, k=K_RATE, theta=THETA)
+
+
+def warmed_liquid(P, inp, adj_cap: int, seed: int, fp64: bool = False, stream=None):
+    """The workloads' start: the seeded uniform placement `inp` relaxed by
+    CAP_STEPS Langevin steps with the WCA pair force capped at F_CAP, then
+    FREE_STEPS uncapped steps, no reactions (App. A protocol), run by the
+    library on the GPU.  Returns host positions and half-step velocities by
+    particle id.  Untimed preparation of the input."""
+    ws = seed + WARM_SEED_OFFSET
+    d1 = P.make_desc(inp.n, inp.L, adj_cap=adj_cap, seed=ws, force_cap=F_CAP)
+    with P.System(d1, inp.x, inp.v, inp.type, inp.state, stream=stream) as g:
+        g.run(CAP_STEPS)
+        x, v = g.positions(), g.velocities()
+    d2 = P.make_desc(inp.n, inp.L, adj_cap=adj_cap, seed=ws + 1, fp64=fp64)
+    with P.System(d2, x, v, inp.type, inp.state, stream=stream) as g:
+        g.run(FREE_STEPS)
+        return g.positions(), g.velocities()
 
 
 class Clocks:
@@ -144,33 +182,179 @@ def algorithmic_bytes_per_particle_step(mean_bonds_per_bead: float) -> float:
     return 96.0 + 4.0 * mean_bonds_per_bead
 
 
-def cpu_baseline(budget_s: float) -> dict:
-    """The oracle as it stands, single-threaded on this host, on a bounded
-    sample of the same workload: MD steps (with the reaction every Theta
-    steps) of the full 1M-bead system until the budget is spent."""
+def peak_hbm():
+    if os.path.exists(PEAKS):
+        return json.load(open(PEAKS))["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs (burst copy)"
+    return 6800.0, "fallback"
+
+
+def roofline_of(P, g, n: int, intervals: int = 10) -> dict:
+    """Roofline of the step kernel (the dominant kernel): per-kernel CUDA-event
+    times on the system's stream over `intervals` further reaction intervals
+    (kernels launched one by one), algorithmic bytes from the bond count."""
+    P.prx_profile_begin(g.h)
+    g.run(intervals * THETA)
+    prof = P.prx_profile_end(g.h)
+    top = max(prof, key=lambda r: r["total_ms"])
+    step_rec = next(r for r in prof if r["name"] == "step")
+    nb = g.observables()["bonds"]
+    bpp = algorithmic_bytes_per_particle_step(2.0 * nb / max(n, 1))
+    avg_ms = step_rec["total_ms"] / step_rec["launches"]
+    achieved = n * bpp / (avg_ms * 1e-3) / 1e9
+    peak, src = peak_hbm()
+    return {"bound": "hbm", "kernel": "step", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "algorithmic_bytes_per_particle_step": bpp, "avg_launch_ms": avg_ms,
+            "peak_source": src, "top_kernel": top["name"],
+            "kernel_ms": {r["name"]: round(r["total_ms"], 4) for r in prof},
+            "kernel_launches": {r["name"]: r["launches"] for r in prof}}
+
+
+def step_kernel_traffic():
+    """DRAM bytes of one step-kernel launch from an ncu capture, valid only
+    while the step kernel's sources are unchanged since the capture."""
+    tr_path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if not os.path.exists(tr_path):
+        return None
+    tr = json.load(open(tr_path))
+    h = hashlib.sha256()
+    for rel in tr.get("digest_of", []):
+        # "path" (the whole file) or "path::until::text" (the file up to the
+        # first occurrence of text: the step kernel's part of it)
+        path, _, until = rel.partition("::until::")
+        with open(os.path.join(ROOT, path), "rb") as f:
+            src = f.read()
+        if until:
+            cut = src.find(until.encode())
+            src = src[:cut] if cut >= 0 else b""
+        h.update(src)
+    if tr.get("kernel_source_digest") == h.hexdigest():
+        return tr.get("bytes_per_launch")
+    return None
+
+
+# ---------------------------------------------------------------------------
+# The oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_timing(inp, sch, cap: int, seed: int, budget_s: float, max_steps: int,
+                  threads: int | None = None) -> dict:
+    """The oracle as it stands, on a bounded sample of a workload: MD steps
+    (with the reaction every Theta steps) from the given state until the
+    budget is spent or max_steps are done.  threads=None: orc_run on one
+    thread; else the OpenMP driver (same trajectory) on `threads` threads
+    (0: all)."""
     import oracle as orc
-    inp = inputs(0)
-    sch = scheme()
-    o = orc.System(inp.x, inp.v, inp.type, inp.state, cap=FUNC)
-    md = orc.MDParams(L=(inp.L,) * 3, seed=synth.BASE_SEED)
+    o = orc.System(inp.x, inp.v, inp.type, inp.state, cap=cap)
+    md = orc.MDParams(L=(inp.L,) * 3, seed=seed)
     rx = orc.Reaction(**sch)
+    cores = 1
     t0 = time.perf_counter()
     steps = 0
-    while True:
-        orc.run(o, md, rx, 1)
+    while steps < max_steps:
+        if threads is None:
+            orc.run(o, md, rx, 1)
+        else:
+            cores = orc.run_omp(o, md, rx, 1, threads)
         steps += 1
-        el = time.perf_counter() - t0
-        if el > budget_s or steps >= 10 * THETA:
+        if time.perf_counter() - t0 > budget_s:
             break
-    return {"value": inp.n * steps / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} MD steps of the {inp.n}-bead step-growth workload "
-                      f"(reaction every {THETA} steps), FP64, one thread, {el:.1f} s"}
+    el = time.perf_counter() - t0
+    return {"value": inp.n * steps / el, "unit": "particle-steps/s", "cores": cores,
+            "kind": "oracle", "steps": steps, "seconds": el}
 
 
+def cpu_baselines(inp, sch, cap, seed, budget_s, max_steps, what: str) -> dict:
+    """Single-thread and all-core timings of the oracle on one workload."""
+    one = oracle_timing(inp, sch, cap, seed, budget_s, max_steps)
+    out = {"value": one["value"], "unit": one["unit"], "cores": 1, "kind": "oracle",
+           "nproc": os.cpu_count(),
+           "sample": f"{one['steps']} MD steps of {what} (reaction every {THETA} steps), FP64, "
+                     f"one thread, {one['seconds']:.1f} s"}
+    try:
+        import oracle as orc
+        if orc.omp_lib() is not None:
+            allc = oracle_timing(inp, sch, cap, seed, budget_s, max_steps, threads=0)
+            out["all_cores"] = {"value": allc["value"], "cores": allc["cores"],
+                                "sample": f"{allc['steps']} MD steps, OpenMP over the per-particle "
+                                          f"force and integration loops, {allc['seconds']:.1f} s"}
+    except Exception as e:  # the single-thread number stands alone
+        out["all_cores"] = {"unavailable": str(e)}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Smaller workloads: 1,250-bead FP64 step growth, 33,096-bead chain growth
+# ---------------------------------------------------------------------------
+def small_config(P, torch, name: str, inp, sch: dict, cap: int, fp64: bool, md_steps: int,
+                 seed: int, args, stream) -> dict:
+    """One full run of a small workload from its warmed liquid: the whole
+    run timed as one region with CUDA events (the state fits in L2; the L2
+    is flushed once before it), its step kernel's roofline over ten further
+    intervals, and the oracle timed on the same start."""
+    xw, vw = warmed_liquid(P, inp, cap, seed, fp64=fp64, stream=stream.cuda_stream)
+    desc = P.make_desc(inp.n, inp.L, adj_cap=cap, seed=seed, fp64=fp64)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=stream.device)
+    with P.System(desc, xw, vw, inp.type, inp.state, stream=stream.cuda_stream) as g:
+        g.set_reaction(P.make_reaction(**sch))
+        g.run(0)  # graphs captured before the timed region
+        st0 = g.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            e0.record(stream)
+            g.run(md_steps)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        g.sync()
+        ms = e0.elapsed_time(e1)
+        st1 = g.stats()
+        obs = g.observables()
+        roof = roofline_of(P, g, inp.n)
+    del flush
+    line = {"workload": name, "metric": "particle-steps/s",
+            "value": inp.n * md_steps / (ms * 1e-3), "unit": "particle-steps/s",
+            "md_steps": md_steps, "ms": ms, "beads": inp.n, "k": sch["k"],
+            "dtype": "f64" if fp64 else "f32 forces / f64 integration",
+            "bonds_end": int(obs["bonds"]), "gpu_launches": int(st1["kernel_launches"]
+                                                               - st0["kernel_launches"]),
+            "rebins": int(st1["rebins"] - st0["rebins"]), "roofline": roof,
+            "l2": "flushed once before the timed run (the whole state fits in L2)"}
+    if not args.no_cpu_baseline:
+        class _W:
+            pass
+        w = _W()
+        w.x, w.v, w.type, w.state, w.L, w.n = xw, vw, inp.type, inp.state, inp.L, inp.n
+        line["cpu_baseline"] = cpu_baselines(w, sch, cap, seed, args.cpu_budget, md_steps,
+                                             f"the {name} workload from the same warmed start")
+    return line
+
+
+def configs_1_2(P, torch, args, stream) -> dict:
+    W1 = synth.WORKLOADS["step_growth_1250_fp64"]
+    W2 = synth.WORKLOADS["chain_growth_33096"]
+    out = {}
+    seed = synth.BASE_SEED + 101
+    inp = synth.step_growth(W1["n_B"], W1["n_A"], W1["f"], seed, placement="uniform")
+    out["step_growth_1250_fp64"] = small_config(
+        P, torch, "step_growth_1250_fp64", inp, synth.step_growth_scheme(W1["f"], k=W1["k"]),
+        W1["f"], True, W1["steps"], seed, args, stream)
+    for k in W2["k"]:
+        seed = synth.BASE_SEED + 202
+        inp = synth.chain_growth(W2["n_M"], W2["n_init"], seed, placement="uniform")
+        nm = f"chain_growth_33096_k{k:g}"
+        out[nm] = small_config(P, torch, nm, inp, synth.chain_growth_scheme(k), 2, False,
+                               W2["steps"], seed, args, stream)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Batched ensemble and serving stream
+# ---------------------------------------------------------------------------
 ENSEMBLE = synth.WORKLOADS["ensemble_256"]
 
 
-def ensemble(P, torch, steps: int, warmup: int = 3) -> dict:
+def ensemble(P, torch, steps: int, rank: int = 0, world: int = 1, dist=None,
+             warmup: int = 3) -> dict:
     """Batched ensemble (256 replicas, sizes log-uniform in 1,024-65,536
     beads, step or chain growth, k log-uniform in [0.01, 1], own seeds)
     advanced together by one prx_batch, against the same replicas run one at
@@ -179,10 +363,12 @@ def ensemble(P, torch, steps: int, warmup: int = 3) -> dict:
     from the same state; wall clock around each leg.  A sample of replicas is
     then re-run alone from the initial inputs for the same total number of
     steps and compared bit for bit with the replicas that went through the
-    batch (same accuracy: identical results)."""
+    batch (same accuracy: identical results).  With several ranks, rank r
+    takes replicas r, r + world, ... and the value is all ranks' replica-steps
+    over the slowest rank's time."""
     W = ENSEMBLE
     specs = synth.ensemble_specs(W["replicas"], W["n_lo"], W["n_hi"], W["k_lo"], W["k_hi"],
-                                 synth.BASE_SEED)
+                                 synth.BASE_SEED)[rank::world]
     reps = []
     for sp in specs:
         inp, sch, cap = synth.replica(sp)
@@ -202,6 +388,8 @@ def ensemble(P, torch, steps: int, warmup: int = 3) -> dict:
     st0 = b.stats()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     ev0.record(stream)
     b.run(md_steps)
@@ -237,10 +425,16 @@ def ensemble(P, torch, steps: int, warmup: int = 3) -> dict:
                                                  np.sort(g.bonds(), order=["step", "a", "t"])))
     for _, g in reps:
         g.close()
-    rs_batch = nrep * md_steps / t_batch
-    rs_plain = nrep * md_steps / t_plain
-    return {"workload": "ensemble_256", "replicas": nrep, "beads_total": beads,
-            "md_steps_per_replica": md_steps, "unit": "replica-steps/s",
+    tb, tp = t_batch, t_plain
+    if dist is not None:
+        tb = max_over_ranks(t_batch, dist, world)
+        tp = max_over_ranks(t_plain, dist, world)
+    n_all = W["replicas"] if world > 1 else nrep
+    rs_batch = n_all * md_steps / tb
+    rs_plain = n_all * md_steps / tp
+    return {"workload": "ensemble_256", "replicas": n_all, "replicas_this_rank": nrep,
+            "beads_this_rank": beads, "md_steps_per_replica": md_steps,
+            "unit": "replica-steps/s",
             "batched": {"value": rs_batch, "particle_steps_per_s": beads * md_steps / t_batch,
                         "device_ms": ms_batch, "wall_s": t_batch,
                         "kernel_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
@@ -253,24 +447,34 @@ def ensemble(P, torch, steps: int, warmup: int = 3) -> dict:
             "l2": "not flushed: the ensemble state (~1 GB) exceeds L2"}
 
 
+def max_over_ranks(v: float, dist, world: int) -> float:
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 SERVING = synth.WORKLOADS["serving_stream"]
 
 
-def serving(P, torch, arrivals: int, step_scale: float) -> dict:
+def serving(P, torch, arrivals: int, step_scale: float, rank: int = 0, world: int = 1) -> dict:
     """Serving stream: Poisson arrivals (20 jobs/s) of step- or chain-growth
-    jobs of 2,048-262,144 beads (log-uniform), replayed in real time through
-    the continuous-batching server (admission by device memory, one shared
-    batch), then the same trace one job at a time (FIFO, each job created,
-    run alone and read back before the next).  Latency = arrival to result
-    read-back.  The step counts are the workload's (5,000-50,000,
-    log-uniform) times `step_scale`, and the arrival count is bounded, so
-    that both legs finish in seconds.  Two jobs are re-run alone afterwards
-    and compared bit for bit with their served results."""
+    jobs of 2,048-262,144 beads (log-uniform) and 5,000-50,000 steps
+    (log-uniform), replayed in real time through the continuous-batching
+    server (admission by device memory through prx_batch_admit, one shared
+    batch), then the same trace one job at a time (FIFO, each job created, run
+    alone and read back before the next).  Latency = arrival to result
+    read-back.  Only the arrival count is bounded; with step_scale = 1 the
+    offered load is the workload's (about 2e10 particle-steps/s, above one
+    GPU's capacity, so jobs queue and overlap).  Two jobs are re-run alone
+    afterwards and compared bit for bit with their served results.  With
+    several ranks, rank r serves arrivals r, r + world, ..."""
     from paper_1409_7498_gb300.serve import Job, PolyrxBackend, Server, serve_serial, serve_trace
     W = SERVING
     lo, hi = max(10, int(W["steps_lo"] * step_scale)), max(10, int(W["steps_hi"] * step_scale))
     specs = synth.serving_trace(arrivals, W["rate"], W["n_lo"], W["n_hi"], lo, hi, W["k_lo"],
-                                W["k_hi"], synth.BASE_SEED + 5)
+                                W["k_hi"], synth.BASE_SEED + 5)[rank::world]
 
     def jobs():
         out = []
@@ -285,13 +489,14 @@ def serving(P, torch, arrivals: int, step_scale: float) -> dict:
 
     free, _ = torch.cuda.mem_get_info()
     budget = int(min(0.5 * free, 64 << 30))
-    be = PolyrxBackend(P)
-    srv = Server(be, budget, round_steps=100, theta=THETA)
+    be = PolyrxBackend(P, mem_budget=budget)
+    srv = Server(be, budget, round_steps=200, theta=THETA)
     jb = jobs()
     res_b = serve_trace(srv, jb)
     be.shutdown()
     res_b.update(rounds=srv.rounds, max_resident_jobs=srv.max_members,
-                 peak_admitted_bytes=srv.peak_in_use, budget_bytes=budget)
+                 mean_resident_jobs=srv.mean_members(), peak_admitted_bytes=srv.peak_in_use,
+                 budget_bytes=budget)
     be2 = PolyrxBackend(P)
     res_s = serve_serial(be2, jobs())
     be2.shutdown()
@@ -307,58 +512,87 @@ def serving(P, torch, arrivals: int, step_scale: float) -> dict:
                 np.sort(g.bonds(), order=["step", "a", "t"]),
                 np.sort(j.result["bonds"], order=["step", "a", "t"])))
     beads = [sp["n"] for sp in specs]
-    offered = W["rate"] * float(np.mean(beads)) * float(np.mean([sp["nsteps"] for sp in specs]))
-    return {"workload": "serving_stream", "arrivals": arrivals, "rate_per_s": W["rate"],
+    offered = W["rate"] / world * float(np.mean(beads)) * float(
+        np.mean([sp["nsteps"] for sp in specs]))
+    return {"workload": "serving_stream", "arrivals": len(specs), "rate_per_s": W["rate"],
             "beads": [W["n_lo"], W["n_hi"]], "steps": [lo, hi],
-            "scaled": f"steps x{step_scale} and {arrivals} of {W['arrivals']} arrivals, "
-                      "so that both legs run in seconds",
+            "bounded": f"{arrivals} of {W['arrivals']} arrivals"
+                       + ("" if step_scale == 1.0 else f", steps x{step_scale}"),
             "offered_particle_steps_per_s": offered,
             "batched": res_b, "serial": res_s,
+            "p50_speedup": res_s["p50_latency_s"] / res_b["p50_latency_s"],
             "p99_speedup": res_s["p99_latency_s"] / res_b["p99_latency_s"],
             "throughput_ratio": res_b["replica_steps_per_s"] / res_s["replica_steps_per_s"],
             "identical": identical}
 
 
+# ---------------------------------------------------------------------------
+# Reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def headline_config(steps: int) -> dict:
+    return {"workload": WORKLOAD, "beads": N_BEADS, "f": FUNC, "k": K_RATE, "theta": THETA,
+            "md_steps_per_bench_step": THETA, "md_steps_timed": steps * THETA,
+            "start": f"uniform placement, {CAP_STEPS} steps with the WCA force capped at "
+                     f"{F_CAP:g}, {FREE_STEPS} uncapped steps (untimed)",
+            "l2": "flushed between bench steps (256 MB write)"}
+
+
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 oracle, timed on this host's cores; each bench
+    """Reference arm: the FP64 oracle, timed on all of this host's cores
+    (the OpenMP driver of its per-particle loops, the same trajectory as the
+    single-threaded oracle; one thread when OpenMP is missing); each bench
     step is one MD step of the same 1M-bead workload (the reaction every
-    Theta steps)."""
+    Theta steps).  The oracle's start is the workload's lattice placement:
+    the capped warm-up of a million beads is GPU work this arm does not run."""
     if rank != 0:
         return
     import oracle as orc
-    inp = inputs(0)
+    inp = inputs(0, placement="lattice")
     sch = scheme()
     o = orc.System(inp.x, inp.v, inp.type, inp.state, cap=FUNC)
     md = orc.MDParams(L=(inp.L,) * 3, seed=synth.BASE_SEED)
     rx = orc.Reaction(**sch)
-    for _ in range(args.warmup):
-        orc.run(o, md, rx, 1)
+    omp = orc.omp_lib() is not None
+
+    def one():
+        return orc.run_omp(o, md, rx, 1, 0) if omp else (orc.run(o, md, rx, 1) or 1)
+
+    for _ in range(min(args.warmup, 3)):
+        one()
     t0 = time.perf_counter()
     done = 0
-    budget = 150.0
+    cores = 1
+    budget = 120.0
     for _ in range(args.steps):
-        orc.run(o, md, rx, 1)
+        cores = one()
         done += 1
         if time.perf_counter() - t0 > budget:
             break
     el = time.perf_counter() - t0
     v = inp.n * done / el
+    how = f"OpenMP over {cores} threads" if omp else "one thread"
     line = {"impl": "reference", "metric": "particle-steps/s", "value": v,
             "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": done, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / max(done, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "beads": inp.n, "f": FUNC, "k": K_RATE,
-                       "theta": THETA, "sample": "one MD step per bench step"},
-            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{done} MD steps of the {inp.n}-bead workload, one thread"},
+            "config": headline_config(args.steps),
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": cores,
+                             "kind": "oracle", "nproc": os.cpu_count(),
+                             "sample": f"{done} MD steps of the {inp.n}-bead workload from its "
+                                       f"lattice placement, {how}"},
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.gpus != world:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world}; launch one rank per GPU "
+              f"with torchrun (--nproc-per-node {args.gpus})", file=sys.stderr)
+        sys.exit(2)
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
@@ -366,6 +600,7 @@ def main():
     from paper_1409_7498_gb300 import build as gbuild
     from paper_1409_7498_gb300 import polyrx as P
 
+    dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
@@ -378,22 +613,26 @@ def main():
     gbuild.build()
     stream = torch.cuda.Stream(device=dev)
 
+    seed = synth.BASE_SEED + rank
     inp = inputs(rank)
     sch = scheme()
+    xw, vw = warmed_liquid(P, inp, FUNC, seed, stream=stream.cuda_stream)
     # the library's autotuner picks the Verlet skin for this workload (timed
-    # on temporary copies of the system, outside the timed region)
+    # on temporary copies of the warmed system, outside the timed region)
     if args.skin > 0:
         skin, skin_ms = args.skin, {}
     else:
         skin, skin_ms = P.prx_autotune_skin(
-            P.make_desc(inp.n, inp.L, adj_cap=FUNC, seed=synth.BASE_SEED + rank), inp.x, inp.v,
-            inp.type, inp.state, P.make_reaction(**sch), steps=100, skins=SKINS)
-    desc = P.make_desc(inp.n, inp.L, adj_cap=FUNC, seed=synth.BASE_SEED + rank, skin=skin)
-    g = P.System(desc, inp.x, inp.v, inp.type, inp.state, stream=stream.cuda_stream)
-    g.set_reaction(P.make_reaction(**sch))
-
-    # warm-up (also melts the lattice)
+            P.make_desc(inp.n, inp.L, adj_cap=FUNC, seed=seed), xw, vw, inp.type, inp.state,
+            P.make_reaction(**sch), steps=100, skins=SKINS)
+    desc = P.make_desc(inp.n, inp.L, adj_cap=FUNC, seed=seed, skin=skin)
+    g = P.System(desc, xw, vw, inp.type, inp.state, stream=stream.cuda_stream)
+    # untimed warm-up bench steps: MD on the warmed liquid; then the reaction
+    # scheme is set and its graphs are captured, so the timed region is the
+    # whole reaction run
     g.run(args.warmup * THETA)
+    g.set_reaction(P.make_reaction(**sch))
+    g.run(0)
     g.sync()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -420,49 +659,27 @@ def main():
     clocks = clk.stop()
     g.sync()
     st1 = g.stats()
+    obs_end = g.observables()
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    ms_max, value = aggregate_throughput(ms, inp.n * THETA * args.steps, world,
-                                         dist if world > 1 else None, dev)
+    ms_max, value = aggregate_throughput(ms, inp.n * THETA * args.steps, world, dist, dev)
     launches = int(st1["kernel_launches"] - st0["kernel_launches"])
     rebins = int(st1["rebins"] - st0["rebins"])
-
-    # roofline of the dominant kernel: per-kernel CUDA-event times on the same
-    # stream over a further stretch of the same run (kernels launched one by one)
-    P.prx_profile_begin(g.h)
-    g.run(10 * THETA)
-    prof = P.prx_profile_end(g.h)
-    top = max(prof, key=lambda r: r["total_ms"])
-    step_rec = next(r for r in prof if r["name"] == "step")
-    nb = g.observables()["bonds"]
-    bpp = algorithmic_bytes_per_particle_step(2.0 * nb / inp.n)
-    avg_ms = step_rec["total_ms"] / step_rec["launches"]
-    achieved = inp.n * bpp / (avg_ms * 1e-3) / 1e9
-    peak = json.load(open(PEAKS))["hbm_gbs"] if os.path.exists(PEAKS) else 6800.0
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-    if os.path.exists(tr_path):
-        # DRAM bytes of one step-kernel launch from an ncu capture, valid only
-        # while the step kernel's sources are unchanged since the capture
-        tr = json.load(open(tr_path))
-        h = hashlib.sha256()
-        for rel in tr.get("digest_of", []):
-            # "path" (the whole file) or "path::until::text" (the file up to
-            # the first occurrence of text: the step kernel's part of it)
-            path, _, until = rel.partition("::until::")
-            with open(os.path.join(ROOT, path), "rb") as f:
-                src = f.read()
-            if until:
-                cut = src.find(until.encode())
-                src = src[:cut] if cut >= 0 else b""
-            h.update(src)
-        if tr.get("kernel_source_digest") == h.hexdigest():
-            traffic = tr.get("bytes_per_launch")
+    n_A = int((inp.type == synth.TYPE_A).sum())
+    run_info = {"skin": skin, "autotune_ms_per_step": {str(k): round(v, 4)
+                                                      for k, v in skin_ms.items()},
+                "cells": list(st1["cells"]), "rebins_in_timed_region": rebins, "wall_s": wall,
+                "bonds_end": int(obs_end["bonds"]),
+                "conversion_end": obs_end["bonds"] / (FUNC * n_A),
+                "bonds_per_bead_end": 2.0 * obs_end["bonds"] / inp.n}
+    roof = roofline_of(P, g, inp.n)
+    roof["traffic"] = step_kernel_traffic()
+    del flush
 
     # end to end through the C ABI with host buffers
     e2e = None
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         pin = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-               for k, a in (("x", inp.x), ("v", inp.v), ("t", inp.type), ("s", inp.state))}
+               for k, a in (("x", xw), ("v", vw), ("t", inp.type), ("s", inp.state))}
         h2d = sum(a.nbytes for a in pin.values())
         torch.cuda.synchronize()
         e0 = time.perf_counter()
@@ -470,6 +687,7 @@ def main():
         ge.set_reaction(P.make_reaction(**sch))
         d2h = 0
         ke = max(args.steps, 1)  # the same number of steps as the device-timed region
+        ob = None
         for q in range(ke):
             ge.run(THETA)
             # the step's result (populations, bonds, energy) copied into a
@@ -486,48 +704,44 @@ def main():
         e_el = time.perf_counter() - e0
         e2e = {"value": inp.n * THETA * ke / e_el, "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(h2d / ke), "d2h_bytes_per_step": int(d2h / ke),
-               "steps": ke, "includes": "create (upload + binning), runs, per-step observables "
-                                        "read-back (pipelined, one step behind), final states "
-                                        "and bonds, destroy"}
+               "steps": ke, "includes": "create from the warmed host state (upload + binning), "
+                                        "runs, per-step observables read-back (pipelined, one "
+                                        "step behind), final states and bonds, destroy"}
         del ob
+    g.close()
 
     ens = None
-    if world == 1 and not args.no_ensemble:
-        ens = ensemble(P, torch, args.ensemble_steps)
+    if not args.no_ensemble:
+        ens = ensemble(P, torch, args.ensemble_steps, rank, world, dist)
     srv = None
     if world == 1 and not args.no_serving:
         srv = serving(P, torch, args.serving_arrivals, args.serving_step_scale)
+    cfgs = None
+    if world == 1 and not args.no_configs:
+        cfgs = configs_1_2(P, torch, args, stream)
 
     if world > 1:
         dist.barrier()
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(args.cpu_budget)
+            class _W:
+                pass
+            w = _W()
+            w.x, w.v, w.type, w.state, w.L, w.n = xw, vw, inp.type, inp.state, inp.L, inp.n
+            cpu = cpu_baselines(w, sch, FUNC, seed, args.cpu_budget, 10 * THETA,
+                                f"the {inp.n}-bead workload from the same warmed start")
         line = {
             "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 forces / f64 integration", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "beads": inp.n, "f": FUNC, "k": K_RATE,
-                       "theta": THETA, "md_steps_per_bench_step": THETA, "box": inp.L,
-                       "cells": list(st1["cells"]), "parallelism": f"replicas x{world}",
-                       "l2": "flushed between bench steps (256 MB write)",
-                       "rebins_in_timed_region": rebins, "wall_s": wall, "skin": skin,
-                       "autotune_ms_per_step": {str(k): round(v, 4) for k, v in skin_ms.items()}},
-            "clocks": clocks, "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "kernel": "step", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                         "algorithmic_bytes_per_particle_step": bpp,
-                         "avg_launch_ms": avg_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs"
-                         if os.path.exists(PEAKS) else "fallback",
-                         "top_kernel": top["name"],
-                         "kernel_ms": {r["name"]: round(r["total_ms"], 4) for r in prof},
-                         "kernel_launches": {r["name"]: r["launches"] for r in prof}},
-            "e2e": e2e, "cpu_baseline": cpu, "ensemble": ens, "serving": srv,
+            "config": dict(headline_config(args.steps), parallelism=f"replicas x{world}"),
+            "run": run_info, "clocks": clocks, "gpu_launches": launches, "roofline": roof,
+            "e2e": e2e, "cpu_baseline": cpu, "configs": cfgs, "ensemble": ens,
+            "serving": srv,
         }
         print(json.dumps(line), flush=True)
-    g.close()
     if world > 1:
         dist.destroy_process_group()
 

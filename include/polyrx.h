@@ -172,9 +172,11 @@ int prx_create(const prx_system_desc* desc, const double* pos, const double* vel
 /* Frees every device and host resource of the system (NULL is a no-op). */
 void prx_destroy(prx_system* sys);
 
-/* Device bytes prx_create would allocate for this descriptor, before any
- * reaction history. */
-int prx_estimate_bytes(const prx_system_desc* desc, uint64_t* bytes);
+/* Device bytes a system of this descriptor holds once created (prx_create)
+ * and given the reaction scheme rx (NULL: none; a reaction cutoff above the
+ * WCA cutoff widens the Verlet lists).  The admission unit of a batch's
+ * memory budget (prx_batch_admit).  PRX_EINVAL for a NULL desc or bytes. */
+int prx_estimate_bytes(const prx_system_desc* desc, const prx_reaction_desc* rx, uint64_t* bytes);
 
 /* Sets (or, with rx == NULL, clears) the reaction scheme.  PRX_EINVAL when
  * the state windows of a type in both masks overlap, theta == 0, k < 0,
@@ -350,17 +352,27 @@ typedef struct {
   uint64_t reactions;       /* reaction steps run */
   uint64_t kernel_launches; /* kernels launched by the batch */
   uint64_t graph_launches;  /* CUDA graph replays */
+  uint32_t max_slots;       /* as given to prx_batch_create (0: no limit) */
+  uint32_t slots_used;      /* admitted systems not yet reported by prx_batch_poll */
+  uint64_t mem_budget;      /* as given to prx_batch_create (0: no limit) */
+  uint64_t bytes_admitted;  /* prx_estimate_bytes summed over the members and the
+                               admitted systems not yet reported */
+  uint64_t epochs;          /* prx_batch_step_epoch calls that ran steps */
 } prx_batch_stats;
 
 /* Creates an empty batch whose work is queued on cuda_stream (NULL: a
- * library-owned stream). */
-int prx_batch_create(void* cuda_stream, prx_batch** out);
+ * library-owned stream).  max_slots bounds the systems held at once and
+ * mem_budget the device bytes they hold together (prx_estimate_bytes of
+ * each); 0 means no limit.  Admission beyond either is PRX_ENOMEM. */
+int prx_batch_create(uint32_t max_slots, uint64_t mem_budget, void* cuda_stream, prx_batch** out);
 
 /* Waits for the batch, returns every member to standalone use (on its own
  * stream, state kept) and frees the batch.  NULL is a no-op. */
 void prx_batch_destroy(prx_batch* b);
 
-/* Adds a system.  PRX_EINVAL when the system is in a batch already, uses
+/* Adds a system with no step target (advanced by prx_batch_run).  PRX_ENOMEM
+ * when it would exceed the batch's slots or memory budget; PRX_EINVAL when
+ * the system is in a batch already, uses
  * PRX_FORCE_FP64 (batches run FP32 forces only), is being profiled, or has
  * a reaction scheme whose Theta differs from that of the batch's reacting
  * members or whose step is at another point of the Theta cycle.  The
@@ -370,12 +382,53 @@ void prx_batch_destroy(prx_batch* b);
  * work and wait for the batch's stream. */
 int prx_batch_add(prx_batch* b, prx_system* sys);
 
-/* Waits for the batch and removes a member (PRX_EINVAL if it is not one). */
+/* Waits for the batch and removes a member (PRX_EINVAL if it is not one);
+ * its slot and budget are freed. */
 int prx_batch_remove(prx_batch* b, prx_system* sys);
 
 /* Queues nsteps steps of every member (reactions every Theta steps as in
- * prx_run) on the batch's stream and returns without waiting. */
+ * prx_run) on the batch's stream and returns without waiting.  PRX_EINVAL
+ * while a member admitted with a step target (prx_batch_admit) is in the
+ * batch: such batches advance by prx_batch_step_epoch. */
 int prx_batch_run(prx_batch* b, uint64_t nsteps);
+
+/* ---- serving: admission by slots and device memory, epochs, completion ----
+ * The request loop of a server that keeps many jobs resident on one GPU:
+ * jobs arrive as systems created by the caller, are admitted while a slot
+ * and memory are free, advance together epoch by epoch, and are reported
+ * when their steps are done so that the caller reads their results and the
+ * slot takes the next job.  The paper runs one system at a time; this is the
+ * library's continuous batching of many. */
+
+/* Admits sys as a member that is to run exactly nsteps more steps (its result
+ * is then the same as that of prx_run(sys, nsteps) alone, bit for bit).
+ * *slot receives its slot number (0..max_slots-1; a running number when
+ * max_slots is 0).  PRX_ENOMEM when no slot is free or when its
+ * prx_estimate_bytes plus bytes_admitted exceeds the budget: the system is
+ * then not admitted and stays usable alone.  PRX_EINVAL as prx_batch_add.
+ * Queued work of the system is ordered before the batch's (no host wait). */
+int prx_batch_admit(prx_batch* b, prx_system* sys, uint64_t nsteps, int32_t* slot);
+
+/* Queues one epoch on the batch's stream:
+ *  - admitted members with fewer steps left than one chunk (Theta steps;
+ *    10 when no member reacts) leave the batch and run their last steps
+ *    alone on their own streams, after the batch's queued work;
+ *  - the others advance together by E steps, E = min(max_steps, the fewest
+ *    steps left of an admitted member), rounded down to whole chunks;
+ *  - admitted members whose steps are then done leave the batch.
+ * *steps_run (may be NULL) receives E.  It returns without waiting while at
+ * most two earlier epochs are still running on the device; otherwise it
+ * first waits for the oldest (flow control).  A member's status (e.g. FENE
+ * overstretch) surfaces in its own read-backs. */
+int prx_batch_step_epoch(prx_batch* b, uint64_t max_steps, uint64_t* steps_run);
+
+/* Reports, without waiting, admitted systems whose steps are all done and
+ * whose device work has finished: up to cap slot numbers into done_slots,
+ * their count into *n_done (0 when none).  A reported system has left the
+ * batch, its slot and budget are free again, and it is back in standalone
+ * use: read its results with the prx_get_* calls, then destroy it or keep
+ * using it. */
+int prx_batch_poll(prx_batch* b, int32_t* done_slots, int32_t cap, int32_t* n_done);
 
 /* Waits for the batch; returns the first non-zero member status (its index
  * in *failed when failed != NULL, else -1 there). */

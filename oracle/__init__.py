@@ -5,7 +5,9 @@ CPU-baseline leg of ``bench.py`` are the only users of this package; the CUDA
 library and its Python binding never import it, and it never imports them.
 
 The arithmetic lives in ``oracle.c`` (compiled with ``-ffp-contract=off``);
-this module only builds it, loads it and marshals numpy arrays.  The rate
+this module only builds it, loads it and marshals numpy arrays.
+``timing_omp.c`` includes ``oracle.c`` unchanged and adds an OpenMP driver
+of the per-particle loops, used only to time the oracle on all host cores.  The rate
 equations of Secs. II.A and II.B live in ``rate_equations.py``.
 
 Citations name the paper's sections, equations and tables.
@@ -42,6 +44,31 @@ def build(force: bool = False) -> str:
     )
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+_OMP_SRC = os.path.join(_HERE, "timing_omp.c")
+_OMP_LIB_PATH = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def build_omp(force: bool = False):
+    """Compile timing_omp.c (oracle.c unchanged plus an OpenMP driver of the
+    per-particle loops) into liboracle_omp.so; returns its path, or None when
+    the host compiler has no OpenMP."""
+    srcs = [_SRC, _OMP_SRC, os.path.join(_HERE, "oracle.h")]
+    if not force and os.path.exists(_OMP_LIB_PATH) and os.path.getmtime(_OMP_LIB_PATH) >= max(
+        os.path.getmtime(p) for p in srcs
+    ):
+        return _OMP_LIB_PATH
+    tmp = _OMP_LIB_PATH + f".tmp{os.getpid()}"
+    try:
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+             "-fopenmp", "-I", _HERE, "-o", tmp, _OMP_SRC, "-lm"],
+            stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+    except (OSError, subprocess.CalledProcessError):
+        return None
+    os.replace(tmp, _OMP_LIB_PATH)
+    return _OMP_LIB_PATH
 
 
 class _MD(C.Structure):
@@ -317,6 +344,39 @@ def run(sys: System, md: MDParams, rx: Reaction | None, nsteps: int, use_cells: 
     sys._sync_back(cs)
     _check(rc, "run")
     return [_obs_dict(obs[i]) for i in range(nrx)]
+
+
+_omp = None
+
+
+def omp_lib():
+    """The OpenMP timing driver, or None when it cannot be built here."""
+    global _omp
+    if _omp is None:
+        path = build_omp()
+        if path is None:
+            return None
+        _omp = C.CDLL(path)
+        _omp.orc_run_omp.argtypes = [C.POINTER(_SYS), C.POINTER(_MD), C.POINTER(_RX), C.c_int64,
+                                     C.c_int]
+        _omp.orc_omp_max_threads.restype = C.c_int
+    return _omp
+
+
+def run_omp(sys: System, md: MDParams, rx: Reaction | None, nsteps: int, threads: int = 0) -> int:
+    """The MD steps and reactions of run(), with the per-particle force and
+    integration loops on `threads` host threads (0: all); the same trajectory
+    bit for bit.  Returns the thread count used."""
+    L = omp_lib()
+    if L is None:
+        raise OracleError(EINVAL, "run_omp (no OpenMP compiler)")
+    cs = sys._c()
+    rxc = C.byref(rx._c()) if rx else None
+    used = threads if threads > 0 else L.orc_omp_max_threads()
+    rc = L.orc_run_omp(C.byref(cs), C.byref(md._c()), rxc, int(nsteps), int(threads))
+    sys._sync_back(cs)
+    _check(rc, "run_omp")
+    return used
 
 
 def pair_histogram(sys: System, md: MDParams, a: tuple, b: tuple, r_max: float, nbins: int):

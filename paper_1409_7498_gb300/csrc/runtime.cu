@@ -69,6 +69,9 @@ struct prx_system {
   std::string err;
   prx_batch* batch = nullptr;      // batch this system belongs to, if any
   cudaStream_t solo_stream = nullptr;  // the system's own stream while in a batch
+  prx_batch* slot_batch = nullptr; // batch holding this system's admission slot
+  int32_t slot = -1;               // its slot there (admitted until polled)
+  cudaEvent_t join_ev = nullptr;   // orders the system's queued work before a batch's
 };
 
 // A batch: systems advanced together, one launch per kernel for all members.
@@ -80,7 +83,6 @@ struct prx_batch {
   uint64_t theta = 0;  // reaction interval shared by the reacting members (0: none)
   uint64_t phase = 0;  // steps run mod theta
   uint64_t steps = 0, kernel_steps = 0, graph_launches = 0, rx_runs = 0;
-  uint64_t rebuilds_seen = 0;  // device rebuild counter at the last table reset
   // device tables (valid while `valid`)
   BatchCtl* bctl = nullptr;
   BatchCtl* bctl_host = nullptr;
@@ -96,6 +98,30 @@ struct prx_batch {
   cudaGraphExec_t g_step = nullptr, g_chunk = nullptr, g_react = nullptr;
   bool valid = false;
   std::string err;
+  // admission (prx_batch_admit / step_epoch / poll)
+  uint32_t max_slots = 0;     // 0: no limit
+  uint64_t mem_budget = 0;    // 0: no limit
+  uint64_t bytes_in_use = 0;  // estimates of the members and the unreported admitted systems
+  uint64_t epochs = 0;
+  struct Slot {
+    prx_system* sys = nullptr;  // nullptr: free
+    uint64_t left = 0;          // steps still to run (targeted members)
+    uint64_t bytes = 0;
+    bool targeted = false;      // admitted with a step target
+    bool finishing = false;     // left the batch; done when `done` has completed
+    cudaEvent_t done = nullptr;
+  };
+  std::vector<Slot> slots;
+  std::vector<cudaEvent_t> inflight;  // ends of the epochs still queued (oldest first)
+  std::vector<cudaEvent_t> ev_pool;   // spare epoch events
+  // pinned staging of the member table and block maps (a ring, so that an
+  // upload still queued is never overwritten)
+  struct Stage {
+    char* host = nullptr;
+    size_t cap = 0;
+    cudaEvent_t used = nullptr;  // recorded after the copies from this buffer
+  } stage[4];
+  int stage_next = 0;
 };
 
 namespace {
@@ -761,13 +787,17 @@ void batch_destroy_graphs(prx_batch* b) {
 // batch member; every kernel family gets a block map listing, per block,
 // the member and the block's index within that member's own grid (the grid
 // the member would be launched with alone).
+//
+// Everything is ordered on the batch's stream, with no host wait: the tables
+// are uploaded by copies queued behind the work already queued (pageable
+// sources are staged by the copy call itself), grown tables are allocated and
+// the old ones freed in stream order, and graph executables still running
+// are released by CUDA when they complete.  The batch control block needs no
+// reset: its member counter and rebuild flag return to zero at the end of
+// every batch step, and its rebuild count is cumulative.
 int batch_prepare(prx_batch* b) {
   if (b->valid) return PRX_OK;
-  CKB(cudaStreamSynchronize(b->stream));
   batch_destroy_graphs(b);
-  CKB(cudaMemcpy(b->bctl_host, b->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost));
-  b->rebuilds_seen += b->bctl_host->rebuilds;
-  CKB(cudaMemset(b->bctl, 0, sizeof(BatchCtl)));
   std::vector<Sys> table;
   b->any_rx = false;
   for (prx_system* m : b->members) {
@@ -811,21 +841,22 @@ int batch_prepare(prx_batch* b) {
   }
   const size_t nmaps = part.size() + cell.size() + tile.size() + one.size() + build.size();
   if (b->n_active > b->T_cap) {
-    if (b->T) cudaFree(b->T);
+    if (b->T) CKB(cudaFreeAsync(b->T, b->stream));
     b->T = nullptr;
     b->T_cap = 0;
-    CKB(cudaMalloc(&b->T, sizeof(Sys) * b->n_active));
-    b->T_cap = b->n_active;
+    const size_t cap = std::max<size_t>(b->n_active, 2 * b->members.size());
+    CKB(cudaMallocAsync((void**)&b->T, sizeof(Sys) * cap, b->stream));
+    b->T_cap = cap;
   }
   if (2 * nmaps > b->maps_cap) {
-    if (b->maps) cudaFree(b->maps);
+    if (b->maps) CKB(cudaFreeAsync(b->maps, b->stream));
     b->maps = nullptr;
     b->maps_cap = 0;
-    CKB(cudaMalloc(&b->maps, sizeof(BlkMap) * 2 * nmaps));
-    b->maps_cap = 2 * nmaps;
+    CKB(cudaMallocAsync((void**)&b->maps, sizeof(BlkMap) * 4 * nmaps, b->stream));
+    b->maps_cap = 4 * nmaps;
   }
-  if (!b->act_n) CKB(cudaMalloc(&b->act_n, sizeof(uint32_t) * 8));
-  CKB(cudaMemset(b->act_n, 0, sizeof(uint32_t) * 8));
+  if (!b->act_n) CKB(cudaMallocAsync((void**)&b->act_n, sizeof(uint32_t) * 8, b->stream));
+  CKB(cudaMemsetAsync(b->act_n, 0, sizeof(uint32_t) * 8, b->stream));
   std::vector<BlkMap> all;
   all.reserve(nmaps);
   BatchLaunch& L = b->L;
@@ -848,8 +879,26 @@ int batch_prepare(prx_batch* b) {
     L.step_off[v] = step_off[v];
     L.step_n[v] = step_n[v];
   }
-  CKB(cudaMemcpy(b->T, table.data(), sizeof(Sys) * table.size(), cudaMemcpyHostToDevice));
-  CKB(cudaMemcpy(b->maps, all.data(), sizeof(BlkMap) * all.size(), cudaMemcpyHostToDevice));
+  {
+    const size_t tb = sizeof(Sys) * table.size(), mb = sizeof(BlkMap) * all.size();
+    prx_batch::Stage& sg = b->stage[b->stage_next];
+    b->stage_next = (b->stage_next + 1) % 4;
+    if (sg.used) CKB(cudaEventSynchronize(sg.used));  // normally long complete
+    else CKB(cudaEventCreateWithFlags(&sg.used, cudaEventDisableTiming));
+    if (sg.cap < tb + mb) {
+      if (sg.host) CKB(cudaFreeHost(sg.host));
+      sg.host = nullptr;
+      sg.cap = 0;
+      const size_t cap = 2 * (tb + mb) + 4096;
+      CKB(cudaMallocHost((void**)&sg.host, cap));
+      sg.cap = cap;
+    }
+    memcpy(sg.host, table.data(), tb);
+    memcpy(sg.host + tb, all.data(), mb);
+    CKB(cudaMemcpyAsync(b->T, sg.host, tb, cudaMemcpyHostToDevice, b->stream));
+    CKB(cudaMemcpyAsync(b->maps, sg.host + tb, mb, cudaMemcpyHostToDevice, b->stream));
+    CKB(cudaEventRecord(sg.used, b->stream));
+  }
   if (configure_batch_build_kernel(build_smem))
     return bfail(b, PRX_ECUDA, "list-build shared memory of " + std::to_string(build_smem) + " bytes refused");
   const int chunk = b->any_rx ? (int)b->theta : kNoRxChunk;
@@ -862,6 +911,40 @@ int batch_prepare(prx_batch* b) {
   b->valid = true;
   return PRX_OK;
 }
+
+// Device bytes of a system of descriptor d whose list cutoff includes
+// r_react (0: the WCA cutoff alone).
+uint64_t estimate_bytes(const prx_system_desc& d, double r_react) {
+  // mirrors the allocations of prx_create and of the cell grid / Verlet
+  // list set up for the larger of the WCA and reaction cutoffs
+  const prx_system_desc* desc = &d;
+  const uint64_t n = desc->n, cap = desc->adj_cap ? desc->adj_cap : 1;
+  const double rc = std::max(std::pow(2.0, 1.0 / 6.0) * desc->wca_sigma, r_react);
+  double skin = desc->skin < 0.0 ? kDefaultSkin : desc->skin;
+  const double Lmin = std::min(desc->box[0], std::min(desc->box[1], desc->box[2]));
+  if (Lmin / (rc + skin) < 3.0) skin = std::max(0.02, Lmin / 3.0 - rc);
+  const double rv = rc + skin;
+  uint64_t ncell = 1;
+  int nc[3];
+  for (int k = 0; k < 3; ++k) {
+    nc[k] = std::max(3, std::min(1023, (int)std::floor(desc->box[k] / rv)));
+    ncell *= (uint64_t)nc[k];
+  }
+  const double V = desc->box[0] * desc->box[1] * desc->box[2];
+  const double mean_nb = (double)n / V * 4.0 / 3.0 * M_PI * rv * rv * rv;
+  const uint64_t list_cap =
+      (uint64_t)((std::max(32, std::min(252, (int)std::ceil(2.5 * mean_nb + 16.0))) + 3) & ~3);
+  const uint64_t nl_bytes = n <= 65535 ? 2 : 4;  // as setup_grid
+  const uint64_t per_set = n * (6 * 8 + 4 + 3 + 4 * cap);
+  const uint64_t nblk = std::max<uint64_t>(n / RX_THREADS + 1, ncell / SCAN_TILE + 1) + 1;
+  const uint64_t allocs = 40;  // separate cudaMalloc calls, each rounded up
+  return 2 * per_set + n * (2 * 16 + 4 * 4) + (n * cap / 2 + 1) * sizeof(prx_bond) +
+           (kHistCap + 1ull) * sizeof(prx_history_record) + sizeof(Ctl) + 32 * (n / RX_THREADS + 2) +
+           32 * n + ncell * 12 + 8 * nblk + list_cap * n * nl_bytes + n + allocs * 4096;
+}
+
+
+void free_slot(prx_batch* b, prx_system* sys);  // (defined with the batch entry points)
 
 // Calls that would change a batch member on its own are refused.
 int refuse_member(prx_system* sys) {
@@ -893,33 +976,9 @@ const char* prx_status_string(int st) {
 // With sys == NULL: the message of the last failed prx_create / prx_load on this thread.
 const char* prx_last_error(const prx_system* sys) { return sys ? sys->err.c_str() : g_create_error.c_str(); }
 
-int prx_estimate_bytes(const prx_system_desc* desc, uint64_t* bytes) {
+int prx_estimate_bytes(const prx_system_desc* desc, const prx_reaction_desc* rx, uint64_t* bytes) {
   if (!desc || !bytes) return PRX_EINVAL;
-  // mirrors the allocations of prx_create and of the cell grid / Verlet
-  // list set up for the WCA cutoff (a larger reaction cutoff grows the list)
-  const uint64_t n = desc->n, cap = desc->adj_cap ? desc->adj_cap : 1;
-  const double rc = std::pow(2.0, 1.0 / 6.0) * desc->wca_sigma;
-  double skin = desc->skin < 0.0 ? kDefaultSkin : desc->skin;
-  const double Lmin = std::min(desc->box[0], std::min(desc->box[1], desc->box[2]));
-  if (Lmin / (rc + skin) < 3.0) skin = std::max(0.02, Lmin / 3.0 - rc);
-  const double rv = rc + skin;
-  uint64_t ncell = 1;
-  int nc[3];
-  for (int k = 0; k < 3; ++k) {
-    nc[k] = std::max(3, std::min(1023, (int)std::floor(desc->box[k] / rv)));
-    ncell *= (uint64_t)nc[k];
-  }
-  const double V = desc->box[0] * desc->box[1] * desc->box[2];
-  const double mean_nb = (double)n / V * 4.0 / 3.0 * M_PI * rv * rv * rv;
-  const uint64_t list_cap =
-      (uint64_t)((std::max(32, std::min(252, (int)std::ceil(2.5 * mean_nb + 16.0))) + 3) & ~3);
-  const uint64_t nl_bytes = n <= 65535 ? 2 : 4;  // as setup_grid
-  const uint64_t per_set = n * (6 * 8 + 4 + 3 + 4 * cap);
-  const uint64_t nblk = std::max<uint64_t>(n / RX_THREADS + 1, ncell / SCAN_TILE + 1) + 1;
-  const uint64_t allocs = 40;  // separate cudaMalloc calls, each rounded up
-  *bytes = 2 * per_set + n * (2 * 16 + 4 * 4) + (n * cap / 2 + 1) * sizeof(prx_bond) +
-           (kHistCap + 1ull) * sizeof(prx_history_record) + sizeof(Ctl) + 32 * (n / RX_THREADS + 2) +
-           32 * n + ncell * 12 + 8 * nblk + list_cap * n * nl_bytes + n + allocs * 4096;
+  *bytes = estimate_bytes(*desc, rx ? rx->r_react : 0.0);
   return PRX_OK;
 }
 
@@ -934,6 +993,8 @@ void prx_destroy(prx_system* sys) {
   if (!sys) return;
   if (sys->batch) prx_batch_remove(sys->batch, sys);
   if (sys->stream) cudaStreamSynchronize(sys->stream);
+  if (sys->slot_batch) free_slot(sys->slot_batch, sys);  // admitted, finished, not yet polled
+  if (sys->join_ev) cudaEventDestroy(sys->join_ev);
   destroy_graphs(sys);
   for (auto& e : sys->prof) {
     cudaEventDestroy(e.a);
@@ -1558,11 +1619,13 @@ int prx_autotune_skin(const prx_system_desc* desc, const double* pos, const doub
 
 // ---- batched ensemble ---------------------------------------------------------
 
-int prx_batch_create(void* cuda_stream, prx_batch** out) {
+int prx_batch_create(uint32_t max_slots, uint64_t mem_budget, void* cuda_stream, prx_batch** out) {
   if (!out) return PRX_EINVAL;
   *out = nullptr;
   prx_batch* b = new (std::nothrow) prx_batch();
   if (!b) return PRX_ENOMEM;
+  b->max_slots = max_slots;
+  b->mem_budget = mem_budget;
   bool ok = true;
   if (cuda_stream) {
     b->stream = (cudaStream_t)cuda_stream;
@@ -1591,6 +1654,19 @@ void prx_batch_destroy(prx_batch* b) {
     m->stream = m->solo_stream;
     m->batch = nullptr;
   }
+  for (prx_batch::Slot& sl : b->slots) {
+    if (sl.sys) {
+      sl.sys->slot = -1;
+      sl.sys->slot_batch = nullptr;
+    }
+    if (sl.done) cudaEventDestroy(sl.done);
+  }
+  for (cudaEvent_t e : b->inflight) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
+  for (prx_batch::Stage& sg : b->stage) {
+    if (sg.host) cudaFreeHost(sg.host);
+    if (sg.used) cudaEventDestroy(sg.used);
+  }
   batch_destroy_graphs(b);
   if (b->T) cudaFree(b->T);
   if (b->maps) cudaFree(b->maps);
@@ -1602,9 +1678,13 @@ void prx_batch_destroy(prx_batch* b) {
   delete b;
 }
 
-int prx_batch_add(prx_batch* b, prx_system* sys) {
-  if (!b || !sys) return PRX_EINVAL;
-  if (sys->batch) return bfail(b, PRX_EINVAL, "system is already a member of a batch");
+}  // extern "C"
+
+namespace {
+
+// The conditions prx_batch_add and prx_batch_admit share.
+int check_member(prx_batch* b, prx_system* sys) {
+  if (sys->batch || sys->slot_batch) return bfail(b, PRX_EINVAL, "system is already a member of a batch");
   if (sys->d.force_precision != PRX_FORCE_FP32)
     return bfail(b, PRX_EINVAL, "batches run PRX_FORCE_FP32 systems only");
   if (sys->profiling) return bfail(b, PRX_EINVAL, "system is being profiled");
@@ -1615,8 +1695,10 @@ int prx_batch_add(prx_batch* b, prx_system* sys) {
     if (b->theta && sys->host_step % th != b->phase)
       return bfail(b, PRX_EINVAL, "system is at another point of the reaction cycle");
   }
-  if (cudaStreamSynchronize(sys->stream) != cudaSuccess)
-    return bfail(b, PRX_ECUDA, "synchronising the system's stream failed");
+  return PRX_OK;
+}
+
+void join(prx_batch* b, prx_system* sys) {
   if (sys->has_rx && !b->theta) {
     b->theta = sys->rxd.theta;
     b->phase = sys->host_step % b->theta;
@@ -1626,13 +1708,16 @@ int prx_batch_add(prx_batch* b, prx_system* sys) {
   sys->batch = b;
   b->members.push_back(sys);
   b->valid = false;
-  return PRX_OK;
 }
 
-int prx_batch_remove(prx_batch* b, prx_system* sys) {
-  if (!b || !sys || sys->batch != b) return PRX_EINVAL;
-  if (cudaStreamSynchronize(b->stream) != cudaSuccess)
-    return bfail(b, PRX_ECUDA, "synchronising the batch stream failed");
+// Takes a member out of the batch without waiting: its own stream waits for
+// the work queued on the batch's stream so far, and further calls on the
+// system go to its own stream.
+int leave(prx_batch* b, prx_system* sys) {
+  if (!sys->join_ev && cudaEventCreateWithFlags(&sys->join_ev, cudaEventDisableTiming) != cudaSuccess)
+    return bfail(b, PRX_ECUDA, "event creation failed");
+  CKB(cudaEventRecord(sys->join_ev, b->stream));
+  CKB(cudaStreamWaitEvent(sys->solo_stream, sys->join_ev, 0));
   b->members.erase(std::find(b->members.begin(), b->members.end(), sys));
   sys->stream = sys->solo_stream;
   sys->batch = nullptr;
@@ -1643,8 +1728,47 @@ int prx_batch_remove(prx_batch* b, prx_system* sys) {
   return PRX_OK;
 }
 
-int prx_batch_run(prx_batch* b, uint64_t nsteps) {
-  if (!b) return PRX_EINVAL;
+// Releases an admission slot (after poll, removal or destruction).
+void free_slot(prx_batch* b, prx_system* sys) {
+  if (sys->slot < 0 || sys->slot_batch != b) return;
+  prx_batch::Slot& sl = b->slots[(size_t)sys->slot];
+  b->bytes_in_use -= sl.bytes;
+  if (sl.done) cudaEventDestroy(sl.done);
+  sl = prx_batch::Slot{};
+  sys->slot = -1;
+  sys->slot_batch = nullptr;
+}
+
+// Takes a slot for sys (PRX_ENOMEM when none is free or the budget is spent).
+int take_slot(prx_batch* b, prx_system* sys, uint64_t bytes, bool targeted, uint64_t nsteps) {
+  if (b->mem_budget && b->bytes_in_use + bytes > b->mem_budget)
+    return bfail(b, PRX_ENOMEM, "memory budget: " + std::to_string(b->bytes_in_use) + " + " +
+                                    std::to_string(bytes) + " > " + std::to_string(b->mem_budget) + " bytes");
+  size_t q = 0;
+  while (q < b->slots.size() && b->slots[q].sys) ++q;
+  if (b->max_slots && q >= b->max_slots) return bfail(b, PRX_ENOMEM, "no free slot");
+  if (q == b->slots.size()) b->slots.emplace_back();
+  prx_batch::Slot& sl = b->slots[q];
+  if (cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
+    return bfail(b, PRX_ECUDA, "event creation failed");
+  sl.sys = sys;
+  sl.bytes = bytes;
+  sl.targeted = targeted;
+  sl.left = nsteps;
+  b->bytes_in_use += bytes;
+  sys->slot = (int32_t)q;
+  sys->slot_batch = b;
+  return PRX_OK;
+}
+
+bool has_targets(const prx_batch* b) {
+  for (const prx_batch::Slot& sl : b->slots)
+    if (sl.sys && sl.targeted && !sl.finishing) return true;
+  return false;
+}
+
+// Queues nsteps steps of every member (graph replays on the batch stream).
+int batch_launch(prx_batch* b, uint64_t nsteps) {
   int rc = batch_prepare(b);
   if (rc) return rc;
   const uint64_t total = nsteps;
@@ -1675,6 +1799,142 @@ int prx_batch_run(prx_batch* b, uint64_t nsteps) {
   if (b->theta) b->phase = (b->phase + total) % b->theta;
   if (b->n_active) b->kernel_steps += total * (uint64_t)b->n_step_variants;
   for (prx_system* m : b->members) m->host_step += total;
+  return PRX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int prx_batch_add(prx_batch* b, prx_system* sys) {
+  if (!b || !sys) return PRX_EINVAL;
+  int rc = check_member(b, sys);
+  if (rc) return rc;
+  if (cudaStreamSynchronize(sys->stream) != cudaSuccess)
+    return bfail(b, PRX_ECUDA, "synchronising the system's stream failed");
+  if (b->max_slots || b->mem_budget) {
+    if ((rc = take_slot(b, sys, estimate_bytes(sys->d, sys->has_rx ? sys->rxd.r_react : 0.0), false, 0)))
+      return rc;
+  }
+  join(b, sys);
+  return PRX_OK;
+}
+
+int prx_batch_admit(prx_batch* b, prx_system* sys, uint64_t nsteps, int32_t* slot) {
+  if (!b || !sys || !slot) return PRX_EINVAL;
+  *slot = -1;
+  int rc = check_member(b, sys);
+  if (rc) return rc;
+  if ((rc = take_slot(b, sys, estimate_bytes(sys->d, sys->has_rx ? sys->rxd.r_react : 0.0), true, nsteps)))
+    return rc;
+  // the system's queued work (creation, earlier runs) comes before the batch's
+  if (!sys->join_ev && cudaEventCreateWithFlags(&sys->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    free_slot(b, sys);
+    return bfail(b, PRX_ECUDA, "event creation failed");
+  }
+  if (cudaEventRecord(sys->join_ev, sys->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(b->stream, sys->join_ev, 0) != cudaSuccess) {
+    free_slot(b, sys);
+    return bfail(b, PRX_ECUDA, "ordering the system before the batch failed");
+  }
+  *slot = sys->slot;
+  join(b, sys);
+  return PRX_OK;
+}
+
+int prx_batch_remove(prx_batch* b, prx_system* sys) {
+  if (!b || !sys || sys->batch != b) return PRX_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return bfail(b, PRX_ECUDA, "synchronising the batch stream failed");
+  b->members.erase(std::find(b->members.begin(), b->members.end(), sys));
+  sys->stream = sys->solo_stream;
+  sys->batch = nullptr;
+  b->valid = false;
+  free_slot(b, sys);
+  bool rx = false;
+  for (prx_system* m : b->members) rx = rx || m->has_rx;
+  if (!rx) b->theta = 0, b->phase = 0;
+  return PRX_OK;
+}
+
+int prx_batch_run(prx_batch* b, uint64_t nsteps) {
+  if (!b) return PRX_EINVAL;
+  if (has_targets(b))
+    return bfail(b, PRX_EINVAL, "members admitted with step targets advance by prx_batch_step_epoch");
+  return batch_launch(b, nsteps);
+}
+
+int prx_batch_step_epoch(prx_batch* b, uint64_t max_steps, uint64_t* steps_run) {
+  if (steps_run) *steps_run = 0;
+  if (!b) return PRX_EINVAL;
+  int rc;
+  // flow control: at most two earlier epochs queued on the device
+  while (!b->inflight.empty()) {
+    cudaError_t q = cudaEventQuery(b->inflight.front());
+    if (q == cudaErrorNotReady) {
+      if (b->inflight.size() < 2) break;
+      q = cudaEventSynchronize(b->inflight.front());
+    }
+    if (q != cudaSuccess) return bfail(b, PRX_ECUDA, std::string("epoch wait: ") + cudaGetErrorString(q));
+    b->ev_pool.push_back(b->inflight.front());
+    b->inflight.erase(b->inflight.begin());
+  }
+  const uint64_t chunk = b->theta ? b->theta : (uint64_t)kNoRxChunk;
+  // 1. members with less than a chunk left finish alone, after the batch's queued work
+  for (prx_batch::Slot& sl : b->slots) {
+    if (!sl.sys || !sl.targeted || sl.finishing || sl.left >= chunk) continue;
+    prx_system* m = sl.sys;
+    if ((rc = leave(b, m))) return rc;
+    if (sl.left && (rc = prx_run(m, sl.left))) return bfail(b, rc, "running a member's last steps: " + m->err);
+    sl.left = 0;
+    sl.finishing = true;
+    CKB(cudaEventRecord(sl.done, m->stream));
+  }
+  // 2. the epoch
+  uint64_t E = max_steps;
+  for (const prx_batch::Slot& sl : b->slots)
+    if (sl.sys && sl.targeted && !sl.finishing) E = std::min(E, sl.left);
+  const uint64_t ch = b->theta ? b->theta : (uint64_t)kNoRxChunk;
+  if (E >= ch) E -= E % ch;
+  if (b->members.empty()) E = 0;
+  if (E) {
+    if ((rc = batch_launch(b, E))) return rc;
+    b->epochs++;
+    for (prx_batch::Slot& sl : b->slots)
+      if (sl.sys && sl.targeted && !sl.finishing) sl.left -= E;
+    cudaEvent_t ev = nullptr;
+    if (!b->ev_pool.empty()) {
+      ev = b->ev_pool.back();
+      b->ev_pool.pop_back();
+    } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      return bfail(b, PRX_ECUDA, "event creation failed");
+    }
+    CKB(cudaEventRecord(ev, b->stream));
+    b->inflight.push_back(ev);
+  }
+  // 3. members whose steps are done leave; they complete with this epoch
+  for (prx_batch::Slot& sl : b->slots) {
+    if (!sl.sys || !sl.targeted || sl.finishing || sl.left) continue;
+    if ((rc = leave(b, sl.sys))) return rc;
+    sl.finishing = true;
+    CKB(cudaEventRecord(sl.done, sl.sys->stream));
+  }
+  if (steps_run) *steps_run = E;
+  return PRX_OK;
+}
+
+int prx_batch_poll(prx_batch* b, int32_t* done_slots, int32_t cap, int32_t* n_done) {
+  if (!b || !n_done || cap < 0 || (cap && !done_slots)) return PRX_EINVAL;
+  *n_done = 0;
+  for (size_t q = 0; q < b->slots.size() && *n_done < cap; ++q) {
+    prx_batch::Slot& sl = b->slots[q];
+    if (!sl.sys || !sl.finishing) continue;
+    const cudaError_t e = cudaEventQuery(sl.done);
+    if (e == cudaErrorNotReady) continue;
+    if (e != cudaSuccess) return bfail(b, PRX_ECUDA, std::string("poll: ") + cudaGetErrorString(e));
+    done_slots[(*n_done)++] = (int32_t)q;
+    free_slot(b, sl.sys);
+  }
   return PRX_OK;
 }
 
@@ -1709,11 +1969,16 @@ int prx_batch_stats_get(prx_batch* b, prx_batch_stats* out) {
     if (m->S.n) out->active++;
   }
   out->steps = b->steps;
-  out->rebuilds = b->rebuilds_seen + b->bctl_host->rebuilds;
+  out->rebuilds = b->bctl_host->rebuilds;
   out->reactions = b->rx_runs;
   out->kernel_launches = b->kernel_steps + out->rebuilds * (uint64_t)batch_rebuild_kernel_count() +
                          b->rx_runs * (uint64_t)batch_rx_kernel_count();
   out->graph_launches = b->graph_launches;
+  out->max_slots = b->max_slots;
+  out->mem_budget = b->mem_budget;
+  out->bytes_admitted = b->bytes_in_use;
+  for (const prx_batch::Slot& sl : b->slots) out->slots_used += sl.sys ? 1u : 0u;
+  out->epochs = b->epochs;
   return PRX_OK;
 }
 

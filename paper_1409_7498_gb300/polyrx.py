@@ -80,7 +80,10 @@ class prx_stats(C.Structure):
 class prx_batch_stats(C.Structure):
     _fields_ = [("members", C.c_uint32), ("active", C.c_uint32), ("particles", C.c_uint64),
                 ("steps", C.c_uint64), ("rebuilds", C.c_uint64), ("reactions", C.c_uint64),
-                ("kernel_launches", C.c_uint64), ("graph_launches", C.c_uint64)]
+                ("kernel_launches", C.c_uint64), ("graph_launches", C.c_uint64),
+                ("max_slots", C.c_uint32), ("slots_used", C.c_uint32),
+                ("mem_budget", C.c_uint64), ("bytes_admitted", C.c_uint64),
+                ("epochs", C.c_uint64)]
 
 
 class prx_class(C.Structure):
@@ -106,7 +109,7 @@ def lib():
     sig = {
         "prx_create": ([P(prx_system_desc), VP, VP, VP, VP, VP, U64, VP, P(VP)], I),
         "prx_destroy": ([VP], None),
-        "prx_estimate_bytes": ([P(prx_system_desc), P(U64)], I),
+        "prx_estimate_bytes": ([P(prx_system_desc), P(prx_reaction_desc), P(U64)], I),
         "prx_set_reaction": ([VP, P(prx_reaction_desc)], I),
         "prx_run": ([VP, U64], I),
         "prx_sync": ([VP], I),
@@ -135,7 +138,10 @@ def lib():
         "prx_autotune_skin": ([P(prx_system_desc), VP, VP, VP, VP, P(prx_reaction_desc),
                                C.c_uint32, P(C.c_double), C.c_uint32, P(C.c_double),
                                P(C.c_double)], I),
-        "prx_batch_create": ([VP, P(VP)], I),
+        "prx_batch_create": ([C.c_uint32, U64, VP, P(VP)], I),
+        "prx_batch_admit": ([VP, VP, U64, P(C.c_int32)], I),
+        "prx_batch_step_epoch": ([VP, U64, P(U64)], I),
+        "prx_batch_poll": ([VP, P(C.c_int32), C.c_int32, P(C.c_int32)], I),
         "prx_batch_destroy": ([VP], None),
         "prx_batch_add": ([VP, VP], I),
         "prx_batch_remove": ([VP, VP], I),
@@ -208,9 +214,10 @@ def prx_destroy(h):
     lib().prx_destroy(h)
 
 
-def prx_estimate_bytes(desc: prx_system_desc) -> int:
+def prx_estimate_bytes(desc: prx_system_desc, rx: prx_reaction_desc | None = None) -> int:
     b = C.c_uint64()
-    _check(lib().prx_estimate_bytes(C.byref(desc), C.byref(b)))
+    _check(lib().prx_estimate_bytes(C.byref(desc), C.byref(rx) if rx is not None else None,
+                                    C.byref(b)))
     return b.value
 
 
@@ -402,10 +409,34 @@ def _bcheck(rc: int, b=None):
         raise PolyrxError(rc, (msg or b"").decode() or lib().prx_status_string(rc).decode())
 
 
-def prx_batch_create(stream=None):
+def prx_batch_create(max_slots: int = 0, mem_budget: int = 0, stream=None):
     h = C.c_void_p()
-    _bcheck(lib().prx_batch_create(C.c_void_p(stream) if stream else None, C.byref(h)))
+    _bcheck(lib().prx_batch_create(int(max_slots), int(mem_budget),
+                                   C.c_void_p(stream) if stream else None, C.byref(h)))
     return h.value
+
+
+def prx_batch_admit(b, h, nsteps: int):
+    """The system's slot, or None when the batch refused it (PRX_ENOMEM)."""
+    slot = C.c_int32(-1)
+    rc = lib().prx_batch_admit(b, h, int(nsteps), C.byref(slot))
+    if rc == PRX_ENOMEM:
+        return None
+    _bcheck(rc, b)
+    return slot.value
+
+
+def prx_batch_step_epoch(b, max_steps: int) -> int:
+    run = C.c_uint64()
+    _bcheck(lib().prx_batch_step_epoch(b, int(max_steps), C.byref(run)), b)
+    return run.value
+
+
+def prx_batch_poll(b, cap: int = 256) -> list:
+    out = (C.c_int32 * max(1, cap))()
+    n = C.c_int32()
+    _bcheck(lib().prx_batch_poll(b, out, int(cap), C.byref(n)), b)
+    return [out[i] for i in range(n.value)]
 
 
 def prx_batch_destroy(b):
@@ -445,13 +476,33 @@ class Batch:
     """Owning handle over one prx_batch.  Members are System objects; the
     batch keeps them alive while they are members."""
 
-    def __init__(self, stream=None):
-        self.h = prx_batch_create(stream)
+    def __init__(self, stream=None, max_slots: int = 0, mem_budget: int = 0):
+        self.h = prx_batch_create(max_slots, mem_budget, stream)
         self.members = []
+        self.admitted = {}  # slot -> System, until poll reports it
 
     def add(self, system):
         prx_batch_add(self.h, system.h)
         self.members.append(system)
+
+    def admit(self, system, nsteps: int):
+        """Admits `system` for exactly nsteps more steps; returns its slot, or
+        None when no slot or memory is free."""
+        slot = prx_batch_admit(self.h, system.h, nsteps)
+        if slot is not None:
+            self.admitted[slot] = system
+        return slot
+
+    def step_epoch(self, max_steps: int) -> int:
+        return prx_batch_step_epoch(self.h, max_steps)
+
+    def poll(self) -> list:
+        """Slots of the admitted systems that finished since the last poll
+        (they are back in standalone use)."""
+        slots = prx_batch_poll(self.h)
+        for q in slots:
+            self.admitted.pop(q, None)
+        return slots
 
     def remove(self, system):
         prx_batch_remove(self.h, system.h)
@@ -471,6 +522,7 @@ class Batch:
             prx_batch_destroy(self.h)
             self.h = None
             self.members = []
+            self.admitted = {}
 
     def __del__(self):
         try:

@@ -4,21 +4,27 @@ share one GPU through one prx_batch (continuous batching).
 Each job is a system (positions, velocities, types, states, a reaction
 scheme, a seed) and a number of MD steps.  The loop:
 
-  * admits queued jobs in arrival order while their device-memory estimate
-    (prx_estimate_bytes) fits the budget; an admitted job's system is created
-    (uploaded and binned) while the batch is busy on the GPU;
-  * runs the batch in rounds of whole reaction intervals, so that every
-    member stays at the start of its reaction cycle between rounds and new
-    jobs can join at any round;
-  * a job with fewer steps left than one interval leaves the batch and runs
-    its last steps alone (the same kernels on the same data: a job's result
-    does not depend on which other jobs shared the GPU with it);
-  * a finished job's bonds and states are read back, its memory freed, and
-    its latency (arrival to result) recorded.
+  * admits queued jobs while a slot and device memory are free
+    (prx_estimate_bytes against the batch's budget; prx_batch_admit refuses
+    with PRX_ENOMEM otherwise).  Jobs are taken in arrival order, but a job
+    that does not fit lets later jobs that fit go ahead (backfilling) until it
+    has waited `patience` seconds; then it holds the queue until it fits.  An
+    admitted job's system is created (uploaded and binned) while the batch is
+    busy on the GPU;
+  * queues epochs of the batch (prx_batch_step_epoch: whole reaction
+    intervals, never past a job's step count; a job with less than an
+    interval left finishes alone on its own stream), with no host wait while
+    at most two epochs are queued;
+  * retires the jobs that prx_batch_poll reports finished: their bonds and
+    states are read back, their memory freed, and their latency (arrival to
+    result) recorded.
 
-All simulation work runs in the library's CUDA kernels; this module only
-schedules.  The backend interface is small so that the scheduling logic can
-be tested without a GPU.
+A job's result does not depend on which other jobs shared the GPU with it
+(the batch runs each member's own kernels on its own data).  All simulation
+work runs in the library's CUDA kernels and the admission, epoch and
+completion bookkeeping in its C runtime; this module only decides which job
+to admit next.  The backend interface is small so that the scheduling logic
+can be tested without a GPU.
 """
 from __future__ import annotations
 
@@ -43,8 +49,8 @@ class Job:
     admitted: Optional[float] = None
     finished: Optional[float] = None
     result: Any = None
-    steps_done: int = 0
     handle: Any = None
+    slot: int = -1
 
     @property
     def latency(self) -> Optional[float]:
@@ -52,15 +58,23 @@ class Job:
 
 
 class PolyrxBackend:
-    """Backend on the polyrx C ABI (prx_create / prx_batch_*)."""
+    """Backend on the polyrx C ABI: prx_create, prx_batch_admit,
+    prx_batch_step_epoch, prx_batch_poll."""
 
-    def __init__(self, P, stream=None, positions: bool = False):
+    def __init__(self, P, stream=None, positions: bool = False, mem_budget: int = 0,
+                 max_slots: int = 0):
         self.P = P
-        self.batch = P.Batch(stream=stream)
+        self.batch = P.Batch(stream=stream, max_slots=max_slots, mem_budget=mem_budget)
         self.positions = positions
 
     def estimate(self, job: Job) -> int:
-        return self.P.prx_estimate_bytes(job.system["desc"])
+        return self.P.prx_estimate_bytes(job.system["desc"], job.system.get("reaction"))
+
+    def fits(self, nbytes: int) -> bool:
+        st = self.batch.stats()
+        if st["max_slots"] and st["slots_used"] >= st["max_slots"]:
+            return False
+        return not st["mem_budget"] or st["bytes_admitted"] + nbytes <= st["mem_budget"]
 
     def create(self, job: Job):
         s = job.system
@@ -69,23 +83,21 @@ class PolyrxBackend:
             g.set_reaction(s["reaction"])
         return g
 
-    def add(self, h):
-        self.batch.add(h)
+    def admit(self, h, nsteps: int):
+        """The job's slot, or None when the batch refused it (no slot or memory)."""
+        return self.batch.admit(h, nsteps)
 
-    def remove(self, h):
-        self.batch.remove(h)
+    def epoch(self, max_steps: int) -> int:
+        return self.batch.step_epoch(max_steps)
 
-    def run(self, nsteps: int):
-        self.batch.run(nsteps)
-
-    def sync(self):
-        self.batch.sync()
+    def poll(self) -> list:
+        return self.batch.poll()
 
     def run_alone(self, h, nsteps: int):
         h.run(nsteps)
 
     def finish(self, h):
-        """Reads the job's result back (synchronises its stream)."""
+        """Reads the job's result back (synchronises its own stream)."""
         out = dict(bonds=h.bonds(), states=h.states(), step=h.step())
         if self.positions:
             out["positions"] = h.positions()
@@ -101,14 +113,18 @@ class PolyrxBackend:
 class Server:
     """Continuous-batching scheduler.
 
-    mem_budget : device bytes the admitted jobs may occupy together
-    round_steps: MD steps per batch round (a multiple of theta)
+    mem_budget : device bytes the admitted jobs may occupy together (the
+                 backend's batch enforces it; the server only uses it to
+                 refuse jobs that could never fit)
+    round_steps: most MD steps per epoch (a multiple of theta)
     theta      : the reaction interval shared by the jobs
+    patience   : seconds a job that does not fit lets later jobs go ahead
     clock      : time source (seconds)
     """
 
     def __init__(self, backend, mem_budget: int, round_steps: int = 200, theta: int = 10,
-                 clock: Callable[[], float] = time.perf_counter):
+                 clock: Callable[[], float] = time.perf_counter, patience: float = 0.5,
+                 idle_wait: Callable[[], None] = lambda: time.sleep(2e-4)):
         if round_steps % theta:
             raise ValueError("round_steps must be a multiple of theta")
         self.be = backend
@@ -116,13 +132,16 @@ class Server:
         self.round_steps = round_steps
         self.theta = theta
         self.clock = clock
+        self.patience = patience
+        self.idle_wait = idle_wait
         self.queue: deque = deque()
-        self.running: list = []
+        self.by_slot: dict = {}
         self.done: list = []
         self.in_use = 0
         self.peak_in_use = 0
         self.rounds = 0
         self.max_members = 0
+        self._resident_sum = 0
         self.feed: Optional[Callable[[], None]] = None  # submits jobs that arrived meanwhile
 
     def submit(self, job: Job):
@@ -132,72 +151,62 @@ class Server:
         self.queue.append(job)
 
     def _admit(self):
-        """Creates systems for queued jobs in arrival order while they fit."""
-        admitted = []
-        while self.queue and self.in_use + self.queue[0].est_bytes <= self.budget:
-            job = self.queue.popleft()
-            job.handle = self.be.create(job)
-            job.admitted = self.clock()
+        """Creates and admits queued jobs that fit, in arrival order with
+        backfilling past a job that does not fit (until it ran out of
+        patience)."""
+        now = self.clock()
+        for job in list(self.queue):
+            if not self.be.fits(job.est_bytes):
+                if now - job.arrival > self.patience:
+                    break  # this job holds the queue until it fits
+                continue
+            h = self.be.create(job)
+            slot = self.be.admit(h, job.nsteps)
+            if slot is None:  # refused after all: try again later
+                self.be.close(h)
+                continue
+            self.queue.remove(job)
+            job.handle, job.slot, job.admitted = h, slot, self.clock()
+            self.by_slot[slot] = job
             self.in_use += job.est_bytes
             self.peak_in_use = max(self.peak_in_use, self.in_use)
-            admitted.append(job)
-        return admitted
+            self.max_members = max(self.max_members, len(self.by_slot))
 
     def _retire(self, job: Job):
         job.result = self.be.finish(job.handle)
+        job.finished = self.clock()
         self.be.close(job.handle)
         job.handle = None
-        job.finished = self.clock()
         self.in_use -= job.est_bytes
         self.done.append(job)
 
     def step(self) -> bool:
-        """One round: admit, launch a round of the batch, then (while the GPU
-        works) admit more, wait, and retire finished jobs.  Returns False when
-        there is nothing to run."""
+        """One round: admit, queue an epoch, admit jobs that arrived
+        meanwhile (their creation overlaps the epoch on the GPU), retire the
+        finished ones.  Returns False when there is nothing to run."""
         if self.feed:
             self.feed()
-        for job in self._admit():
-            self._join(job)
-        if not self.running:
+        self._admit()
+        if not self.by_slot:
             return False
-        left = min(j.nsteps - j.steps_done for j in self.running)
-        k = min(self.round_steps, (left // self.theta) * self.theta)
-        if k > 0:
-            self.be.run(k)
-            for j in self.running:
-                j.steps_done += k
+        k = self.be.epoch(self.round_steps)
         self.rounds += 1
+        self._resident_sum += len(self.by_slot)
         if self.feed:
             self.feed()
-        late = self._admit()  # overlaps the round on the GPU (uploads, binning)
-        self.be.sync()
-        for j in list(self.running):
-            rem = j.nsteps - j.steps_done
-            if rem < self.theta:
-                self.be.remove(j.handle)
-                self.running.remove(j)
-                if rem:
-                    self.be.run_alone(j.handle, rem)
-                    j.steps_done += rem
-                self._retire(j)
-        for job in late:
-            self._join(job)
+        self._admit()
+        finished = self.be.poll()
+        for slot in finished:
+            self._retire(self.by_slot.pop(slot))
+        if k == 0 and not finished:
+            self.idle_wait()  # only jobs finishing alone are left: let them run
         return True
 
-    def _join(self, job: Job):
-        if job.nsteps < self.theta:  # too short to share a round: run alone
-            if job.nsteps:
-                self.be.run_alone(job.handle, job.nsteps)
-                job.steps_done = job.nsteps
-            self._retire(job)
-            return
-        self.be.add(job.handle)
-        self.running.append(job)
-        self.max_members = max(self.max_members, len(self.running))
+    def mean_members(self) -> float:
+        return self._resident_sum / self.rounds if self.rounds else 0.0
 
     def idle(self) -> bool:
-        return not self.queue and not self.running
+        return not self.queue and not self.by_slot
 
 
 def serve_trace(server: Server, jobs: list, clock: Callable[[], float] = time.perf_counter,
@@ -240,10 +249,9 @@ def serve_serial(backend, jobs: list, clock: Callable[[], float] = time.perf_cou
         h = backend.create(j)
         j.admitted = clock()
         backend.run_alone(h, j.nsteps)
-        j.steps_done = j.nsteps
         j.result = backend.finish(h)
-        backend.close(h)
         j.finished = clock()
+        backend.close(h)
         done.append(j)
     wall = clock() - t0
     return summarize(done, wall)

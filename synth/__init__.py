@@ -11,6 +11,9 @@ Recipe (stated once here, used everywhere):
     about 1.03-1.05 sigma at rho = 0.85), each displaced by a uniform jitter
     of +-jitter/2 lattice spacings, so no two particles start closer than
     about 0.95 sigma and no capped warm-up is needed;
+    or (placement="uniform", the benchmark workloads' recipe) uniformly at
+    random in the box, which needs the capped-force WCA warm-up before
+    production (the warm-up runs in the library; this module only places);
   * velocities: Maxwell-Boltzmann at kT with the centre-of-mass velocity
     removed;
   * types: 0 = B (difunctional monomer / chain monomer M), 1 = A
@@ -82,14 +85,22 @@ def maxwell_velocities(n: int, kT: float, mass: float, rng: np.random.Generator)
     return np.ascontiguousarray(v)
 
 
+def _place(n: int, L: float, rng: np.random.Generator, jitter: float, placement: str):
+    if placement == "uniform":
+        return uniform_positions(n, L, rng)
+    if placement != "lattice":
+        raise ValueError(f"unknown placement {placement!r}")
+    return lattice_positions(n, L, rng, jitter)
+
+
 def step_growth(n_B: int, n_A: int, f: int, seed: int, rho: float = DENSITY, kT: float = 1.0,
-                jitter: float = 0.05) -> Inputs:
+                jitter: float = 0.05, placement: str = "lattice") -> Inputs:
     """Difunctional B monomers (state 0) and A crosslinkers of functionality
     f (state f)."""
     rng = np.random.default_rng(seed)
     n = n_B + n_A
     L = box_edge(n, rho)
-    x = lattice_positions(n, L, rng, jitter)
+    x = _place(n, L, rng, jitter, placement)
     v = maxwell_velocities(n, kT, 1.0, rng)
     typ = np.full(n, TYPE_B, np.uint8)
     st = np.zeros(n, np.int8)
@@ -172,12 +183,12 @@ def step_growth_sites(n_total: int, f: int, seed: int, **kw) -> Inputs:
 
 
 def chain_growth(n_M: int, n_init: int, seed: int, rho: float = DENSITY, kT: float = 1.0,
-                 jitter: float = 0.05) -> Inputs:
+                 jitter: float = 0.05, placement: str = "lattice") -> Inputs:
     """Monomers M (type B, state 0) and initiators (type A, state 2 = P*)."""
     rng = np.random.default_rng(seed)
     n = n_M + n_init
     L = box_edge(n, rho)
-    x = lattice_positions(n, L, rng, jitter)
+    x = _place(n, L, rng, jitter, placement)
     v = maxwell_velocities(n, kT, 1.0, rng)
     typ = np.full(n, TYPE_B, np.uint8)
     st = np.zeros(n, np.int8)

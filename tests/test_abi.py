@@ -63,6 +63,10 @@ def test_status_strings_and_estimate(P):
     d = P.make_desc(1_048_576, 107.249, adj_cap=4)
     est = P.prx_estimate_bytes(d)
     assert 150e6 < est < 600e6  # roughly 250 B per bead at 1M beads
+    # a reaction cutoff beyond the WCA cutoff widens the Verlet lists
+    wide = P.make_reaction(2, 1, 1, 4, 0, 1, -1, 1, 0.1, r_react=1.6)
+    narrow = P.make_reaction(2, 1, 1, 4, 0, 1, -1, 1, 0.1, r_react=1.1)
+    assert P.prx_estimate_bytes(d, narrow) == est < P.prx_estimate_bytes(d, wide)
 
 
 def test_library_has_no_cpu_fallback_path():
