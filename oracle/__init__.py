@@ -99,6 +99,7 @@ class _SYS(C.Structure):
         ("nadj", C.c_void_p), ("adj", C.c_void_p), ("adj_style", C.c_void_p),
         ("nb", C.c_int64), ("nb_cap", C.c_int64), ("bond_a", C.c_void_p), ("bond_t", C.c_void_p),
         ("bond_step", C.c_void_p), ("bond_style", C.c_void_p), ("step", C.c_int64),
+        ("bond_rx", C.c_void_p),
     ]
 
 
@@ -135,6 +136,10 @@ def lib():
         _lib.orc_pair_histogram.argtypes = [P(_SYS), P(_MD), P(_CLASS), P(_CLASS), C.c_double,
                                             C.c_int32, P(C.c_int64), P(C.c_int64),
                                             P(C.c_int64)]
+        _lib.orc_check_reactions.argtypes = [P(_RX), C.c_int]
+        _lib.orc_react_set.argtypes = [P(_SYS), P(_MD), P(_RX), C.c_int, C.c_int, C.c_int64,
+                                       P(_TRACE), P(C.c_int64)]
+        _lib.orc_run_set.argtypes = [P(_SYS), P(_MD), P(_RX), C.c_int, C.c_int64, C.c_int]
     return _lib
 
 
@@ -228,6 +233,7 @@ class System:
         self.bond_t = np.zeros(self.bond_capacity, np.uint32)
         self.bond_step = np.zeros(self.bond_capacity, np.int64)
         self.bond_style = np.zeros(self.bond_capacity, np.uint8)
+        self.bond_rx = np.zeros(self.bond_capacity, np.uint8)
 
     @property
     def n(self) -> int:
@@ -254,12 +260,24 @@ class System:
             b = b[np.lexsort((b[:, 2], b[:, 1], b[:, 0]))]
         return b
 
+    def bond_reactions(self) -> np.ndarray:
+        """Bonds as rows (step, a, t, reaction) in canonical order; reaction is
+        the index in the scheme of react_set that formed the bond (0 for
+        initial bonds and for the single-reaction step)."""
+        b = np.stack([self.bond_step[: self.nb], self.bond_a[: self.nb].astype(np.int64),
+                      self.bond_t[: self.nb].astype(np.int64),
+                      self.bond_rx[: self.nb].astype(np.int64)], axis=1)
+        if len(b):
+            b = b[np.lexsort((b[:, 2], b[:, 1], b[:, 0]))]
+        return b
+
     def _c(self) -> _SYS:
         def p(a):
             return a.ctypes.data_as(C.c_void_p)
         return _SYS(self.n, self.cap, 0, p(self.x), p(self.v), p(self.type), p(self.state),
                     p(self.nadj), p(self.adj), p(self.adj_style), self.nb, self.bond_capacity,
-                    p(self.bond_a), p(self.bond_t), p(self.bond_step), p(self.bond_style), self.step)
+                    p(self.bond_a), p(self.bond_t), p(self.bond_step), p(self.bond_style), self.step,
+                    p(self.bond_rx))
 
     def _sync_back(self, cs: _SYS):
         self.nb = int(cs.nb)
@@ -317,6 +335,41 @@ def react(sys: System, md: MDParams, rx: Reaction, step: int, use_cells: bool = 
     _check(rc, "react")
     return dict(candidates=tr.candidates, retained=tr.retained, a_winners=tr.a_winners,
                 formed=tr.formed)
+
+
+def _rx_array(rxs):
+    arr = (_RX * max(1, len(rxs)))()
+    for q, r in enumerate(rxs):
+        arr[q] = r._c()
+    return arr
+
+
+def check_reactions(rxs) -> int:
+    """Status of a set of concurrent reactions (0 when valid)."""
+    return lib().orc_check_reactions(_rx_array(rxs), len(rxs))
+
+
+def react_set(sys: System, md: MDParams, rxs, step: int, use_cells: bool = False):
+    """Reaction step with several concurrent reactions (see orc_react_set).
+    Returns (trace counts, final pairs per reaction)."""
+    cs = sys._c()
+    tr = _TRACE()
+    per = (C.c_int64 * max(1, len(rxs)))()
+    rc = lib().orc_react_set(C.byref(cs), C.byref(md._c()), _rx_array(rxs), len(rxs),
+                             int(use_cells), int(step), C.byref(tr), per)
+    sys._sync_back(cs)
+    _check(rc, "react_set")
+    return (dict(candidates=tr.candidates, retained=tr.retained, a_winners=tr.a_winners,
+                 formed=tr.formed), [int(per[q]) for q in range(len(rxs))])
+
+
+def run_set(sys: System, md: MDParams, rxs, nsteps: int, use_cells: bool = True):
+    """nsteps MD steps with the concurrent reactions every Theta steps."""
+    cs = sys._c()
+    rc = lib().orc_run_set(C.byref(cs), C.byref(md._c()), _rx_array(rxs), len(rxs), int(nsteps),
+                           int(use_cells))
+    sys._sync_back(cs)
+    _check(rc, "run_set")
 
 
 def _obs_dict(o: _OBS) -> dict:

@@ -739,3 +739,254 @@ int orc_pair_histogram(const orc_system* s, const orc_md_params* md, const orc_c
   free(e2);
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------
+ * Several concurrent reactions.  The paper names this extension (Secs. III.B
+ * and VII: reactions with different intrinsic rates, following the reactive
+ * multiparticle collision scheme of Rohlf et al.) without giving the
+ * algorithm.  Reading used here:
+ *   - the reactions share Theta and the structure of Table I.  A particle may
+ *     be an A of several reactions or a T of several, never an A of one and
+ *     a T of another (checked), so a reaction step still forms at most one
+ *     bond per particle (Sec. III.A);
+ *   - the pair (A, T) is a candidate of reaction r when A is in r's A
+ *     window, T in r's T window, r^2 < r_react,r^2 and the two are not
+ *     bonded.  Its candidate reactions c_1 < ... < c_m (in the scheme's
+ *     order) share one acceptance draw u, as the reaction channels of one
+ *     collision do in that scheme: the pair is retained for reaction c_j, the
+ *     first j with u < P_j, where P_j = p_c1 + ... + p_cj is summed in that
+ *     order and p_r = k_r dt Theta (Eqs. 3-4 per reaction); with
+ *     u >= P_m it is not retained.  The pair thus reacts with probability
+ *     min(1, p_c1 + ... + p_cm), and with reaction r with probability p_r
+ *     over that sum when the sum is at most 1; one reaction reduces to
+ *     u < p exactly;
+ *   - steps 3-9 of Table I run on the pooled retained pairs with the same
+ *     keyed choices (the keys do not depend on the reaction); the bond of a
+ *     final pair takes the increments, bond style and valence limit of its
+ *     reaction.
+ * ---------------------------------------------------------------------- */
+int orc_check_reactions(const orc_rx_params* rx, int nrx) {
+  if (!rx || nrx < 1 || nrx > ORC_MAX_REACTIONS) return ORC_EINVAL;
+  for (int r = 0; r < nrx; ++r) {
+    int rc = orc_check_reaction(&rx[r]);
+    if (rc) return rc;
+    if (rx[r].theta != rx[0].theta) return ORC_EINVAL;
+    if (nrx > 1 && rx[r].selection != ORC_SELECT_RANDOM) return ORC_EINVAL;
+  }
+  /* no (type, state) is an A of one reaction and a T of another */
+  for (int r = 0; r < nrx; ++r)
+    for (int q = 0; q < nrx; ++q)
+      if ((rx[r].mask_A & rx[q].mask_T) && !(rx[r].a_hi < rx[q].t_lo || rx[q].t_hi < rx[r].a_lo))
+        return ORC_EINVAL;
+  return ORC_OK;
+}
+
+typedef struct {
+  uint32_t a, t;
+  int32_t rx;
+} rpair_t;
+
+static int rcmp_by_a(const void* p, const void* q) {
+  const rpair_t* x = (const rpair_t*)p;
+  const rpair_t* y = (const rpair_t*)q;
+  if (x->a != y->a) return x->a < y->a ? -1 : 1;
+  if (x->t != y->t) return x->t < y->t ? -1 : 1;
+  return 0;
+}
+static int rcmp_by_t(const void* p, const void* q) {
+  const rpair_t* x = (const rpair_t*)p;
+  const rpair_t* y = (const rpair_t*)q;
+  if (x->t != y->t) return x->t < y->t ? -1 : 1;
+  if (x->a != y->a) return x->a < y->a ? -1 : 1;
+  return 0;
+}
+
+typedef struct {
+  const orc_system* s;
+  const orc_md_params* md;
+  const orc_rx_params* rx;
+  int nrx;
+  int64_t step;
+  rpair_t* list;
+  int64_t nlist, caplist;
+  int64_t candidates;
+  int oom;
+} rfind_ctx;
+
+/* Steps 1 and 2 for one pair (i, j): its candidate reactions, then one
+ * draw against their cumulative acceptance probabilities. */
+static void rfind_visit(int64_t i, int64_t j, void* vctx) {
+  rfind_ctx* c = (rfind_ctx*)vctx;
+  const orc_system* s = c->s;
+  double d[3];
+  separation(s->x, i, j, c->md->L, d);
+  const double r2 = dist2_fixed(d);
+  int cand[ORC_MAX_REACTIONS];
+  int m = 0;
+  for (int r = 0; r < c->nrx; ++r) {
+    const orc_rx_params* x = &c->rx[r];
+    if (!eligible_A(s, x, i) || !eligible_T(s, x, j)) continue;
+    if (!(r2 < x->r_react * x->r_react)) continue;
+    cand[m++] = r;
+  }
+  if (m == 0 || bonded(s, i, j)) return;
+  c->candidates++;
+  uint32_t w[4];
+  draw(c->md->seed, c->step, (uint32_t)i, (uint32_t)j, ORC_TAG_ACCEPT, w);
+  const double u = orc_u53(w[0], w[1]);
+  double P = 0.0;
+  int chosen = -1;
+  for (int q = 0; q < m && chosen < 0; ++q) {
+    const orc_rx_params* x = &c->rx[cand[q]];
+    P = P + x->k * c->md->dt * (double)x->theta;
+    if (u < P) chosen = cand[q];
+  }
+  if (chosen < 0) return;
+  if (c->nlist == c->caplist) {
+    int64_t nc = c->caplist ? 2 * c->caplist : 1024;
+    rpair_t* nl = (rpair_t*)realloc(c->list, sizeof(rpair_t) * (size_t)nc);
+    if (!nl) {
+      c->oom = 1;
+      return;
+    }
+    c->list = nl;
+    c->caplist = nc;
+  }
+  c->list[c->nlist].a = (uint32_t)i;
+  c->list[c->nlist].t = (uint32_t)j;
+  c->list[c->nlist].rx = chosen;
+  c->nlist++;
+}
+
+int orc_react_set(orc_system* s, const orc_md_params* md, const orc_rx_params* rx, int nrx,
+                  int use_cells, int64_t step, orc_rx_trace* trace, int64_t* formed_per_rx) {
+  if (!s || !md) return ORC_EINVAL;
+  int rc = orc_check_reactions(rx, nrx);
+  if (rc) return rc;
+  rfind_ctx c;
+  memset(&c, 0, sizeof(c));
+  c.s = s;
+  c.md = md;
+  c.rx = rx;
+  c.nrx = nrx;
+  c.step = step;
+  double rmax = 0.0;
+  for (int r = 0; r < nrx; ++r) rmax = rx[r].r_react > rmax ? rx[r].r_react : rmax;
+
+  /* Steps 1-2 for every particle that is an A of some reaction. */
+  cells_t cl;
+  int have = 0;
+  if (use_cells) {
+    have = cells_build(s, md->L, rmax, &cl);
+    if (have < 0) return ORC_ENOMEM;
+  }
+  for (int64_t i = 0; i < s->n; ++i) {
+    int isA = 0;
+    for (int r = 0; r < nrx; ++r) isA |= eligible_A(s, &rx[r], i);
+    if (isA) for_each_neighbor(s, have ? &cl : NULL, md->L, i, rfind_visit, &c);
+  }
+  if (have) cells_free(&cl);
+  if (c.oom) {
+    free(c.list);
+    return ORC_ENOMEM;
+  }
+
+  /* Steps 3 and 5: L_A by id_A, one T per A (smallest key, ties to the
+   * smaller id_T). */
+  qsort(c.list, (size_t)c.nlist, sizeof(rpair_t), rcmp_by_a);
+  int64_t nwin = 0;
+  for (int64_t q = 0; q < c.nlist;) {
+    int64_t e = q, best = -1;
+    uint64_t bestkey = 0;
+    while (e < c.nlist && c.list[e].a == c.list[q].a) {
+      uint32_t w[4];
+      draw(md->seed, step, c.list[e].a, c.list[e].t, ORC_TAG_SEL_A, w);
+      uint64_t key = ((uint64_t)w[0] << 32) | w[1];
+      if (best < 0 || key < bestkey || (key == bestkey && c.list[e].t < c.list[best].t)) {
+        best = e;
+        bestkey = key;
+      }
+      ++e;
+    }
+    c.list[nwin++] = c.list[best];
+    q = e;
+  }
+
+  /* Steps 6-7: L_T by id_T, one A per T (smallest key, ties to the
+   * smaller id_A). */
+  qsort(c.list, (size_t)nwin, sizeof(rpair_t), rcmp_by_t);
+  int64_t nfin = 0;
+  for (int64_t q = 0; q < nwin;) {
+    int64_t e = q, best = -1;
+    uint64_t bestkey = 0;
+    while (e < nwin && c.list[e].t == c.list[q].t) {
+      uint32_t w[4];
+      draw(md->seed, step, c.list[e].t, c.list[e].a, ORC_TAG_SEL_T, w);
+      uint64_t key = ((uint64_t)w[0] << 32) | w[1];
+      if (best < 0 || key < bestkey || (key == bestkey && c.list[e].a < c.list[best].a)) {
+        best = e;
+        bestkey = key;
+      }
+      ++e;
+    }
+    c.list[nfin++] = c.list[best];
+    q = e;
+  }
+  qsort(c.list, (size_t)nfin, sizeof(rpair_t), rcmp_by_a);
+
+  /* Step 9, in ascending id of A, each bond with its reaction's increments,
+   * style and valence limits. */
+  int status = ORC_OK;
+  if (formed_per_rx)
+    for (int r = 0; r < nrx; ++r) formed_per_rx[r] = 0;
+  for (int64_t q = 0; q < nfin; ++q) {
+    const uint32_t a = c.list[q].a, t = c.list[q].t;
+    const orc_rx_params* x = &rx[c.list[q].rx];
+    if (formed_per_rx) formed_per_rx[c.list[q].rx]++;
+    int capA = s->cap < x->max_valence[s->type[a] & 7] ? s->cap : x->max_valence[s->type[a] & 7];
+    int capT = s->cap < x->max_valence[s->type[t] & 7] ? s->cap : x->max_valence[s->type[t] & 7];
+    if (s->nadj[a] >= capA || s->nadj[t] >= capT || s->nb >= s->nb_cap) {
+      status = ORC_ECAPACITY;
+      continue;
+    }
+    s->adj[(int64_t)s->cap * a + s->nadj[a]] = t;
+    s->adj_style[(int64_t)s->cap * a + s->nadj[a]] = (uint8_t)x->bond_style;
+    s->nadj[a]++;
+    s->adj[(int64_t)s->cap * t + s->nadj[t]] = a;
+    s->adj_style[(int64_t)s->cap * t + s->nadj[t]] = (uint8_t)x->bond_style;
+    s->nadj[t]++;
+    s->bond_a[s->nb] = a;
+    s->bond_t[s->nb] = t;
+    s->bond_step[s->nb] = step;
+    s->bond_style[s->nb] = (uint8_t)x->bond_style;
+    if (s->bond_rx) s->bond_rx[s->nb] = (uint8_t)c.list[q].rx;
+    s->nb++;
+    s->state[a] = (int8_t)(s->state[a] + x->dA);
+    s->state[t] = (int8_t)(s->state[t] + x->dT);
+  }
+  if (trace) {
+    trace->candidates = c.candidates;
+    trace->retained = c.nlist;
+    trace->a_winners = nwin;
+    trace->formed = nfin;
+  }
+  free(c.list);
+  return status;
+}
+
+/* nsteps MD steps with the reaction set applied after every step s with
+ * s % Theta == 0 (as orc_run). */
+int orc_run_set(orc_system* s, const orc_md_params* md, const orc_rx_params* rx, int nrx,
+                int64_t nsteps, int use_cells) {
+  int rc = orc_check_reactions(rx, nrx);
+  if (rc) return rc;
+  for (int64_t q = 0; q < nsteps; ++q) {
+    rc = orc_step(s, md, use_cells, NULL);
+    if (rc) return rc;
+    if (s->step % rx[0].theta == 0) {
+      rc = orc_react_set(s, md, rx, nrx, use_cells, s->step, NULL, NULL);
+      if (rc) return rc;
+    }
+  }
+  return ORC_OK;
+}

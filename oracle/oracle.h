@@ -85,6 +85,7 @@ typedef struct {
   int64_t* bond_step; /* [nb_cap] step the bond formed (0: initial) */
   uint8_t* bond_style;/* [nb_cap] */
   int64_t step;       /* completed MD steps */
+  uint8_t* bond_rx;   /* [nb_cap] reaction that formed the bond (orc_react_set; may be NULL) */
 } orc_system;
 
 typedef struct {
@@ -131,5 +132,16 @@ int orc_pair_histogram(const orc_system* s, const orc_md_params* md, const orc_c
                        int64_t* n_a, int64_t* n_b);
 int orc_run(orc_system* s, const orc_md_params* md, const orc_rx_params* rx,
             int64_t nsteps, int use_cells, orc_obs* obs_per_reaction, int64_t obs_cap);
+
+/* Several concurrent reactions (the extension named in Secs. III.B and VII;
+ * see orc_react_set in oracle.c for the reading).  At most ORC_MAX_REACTIONS
+ * reactions sharing Theta; formed_per_rx (may be NULL) receives, per
+ * reaction, the final pairs of that reaction. */
+#define ORC_MAX_REACTIONS 4
+int orc_check_reactions(const orc_rx_params* rx, int nrx);
+int orc_react_set(orc_system* s, const orc_md_params* md, const orc_rx_params* rx, int nrx,
+                  int use_cells, int64_t step, orc_rx_trace* trace, int64_t* formed_per_rx);
+int orc_run_set(orc_system* s, const orc_md_params* md, const orc_rx_params* rx, int nrx,
+                int64_t nsteps, int use_cells);
 
 #endif
