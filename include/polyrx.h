@@ -63,6 +63,7 @@ extern "C" {
 #define PRX_MAX_TYPES 8
 #define PRX_MAX_STATES 16     /* states tracked by the observables: 0..15 */
 #define PRX_MAX_ADJ 8         /* largest adjacency capacity per particle */
+#define PRX_MAX_REACTIONS 4   /* concurrent reactions of one scheme */
 
 typedef struct prx_system prx_system; /* opaque, library-owned */
 typedef struct prx_batch prx_batch;   /* opaque, library-owned (see below) */
@@ -113,7 +114,8 @@ typedef struct {
   uint32_t a, t;
   int64_t step;           /* step the bond formed; 0 for bonds given at creation */
   uint32_t style;
-  uint32_t reserved;
+  uint32_t reaction;      /* index in the scheme of the reaction that formed it
+                             (0 for initial bonds and single-reaction schemes) */
 } prx_bond;
 
 /* Counts of Table I for one reaction step.  With PRX_SELECT_NEAREST:
@@ -180,9 +182,30 @@ int prx_estimate_bytes(const prx_system_desc* desc, const prx_reaction_desc* rx,
 
 /* Sets (or, with rx == NULL, clears) the reaction scheme.  PRX_EINVAL when
  * the state windows of a type in both masks overlap, theta == 0, k < 0,
- * r_react <= 0, or a bond style is unknown.  If r_react exceeds the cell
- * list's cutoff the cell grid is rebuilt. */
+ * r_react <= 0, or a bond style or selection rule is unknown.  If r_react
+ * exceeds the cell list's cutoff the cell grid is rebuilt.  The same as
+ * prx_set_reactions(sys, rx, 1). */
 int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx);
+
+/* Sets n_rx concurrent reactions (1..PRX_MAX_REACTIONS; n_rx == 0 clears the
+ * scheme).  The paper names several concurrent reactions with different
+ * intrinsic rates as an extension of its algorithm (Secs. III.B, VII) without
+ * giving one; this library's rule:
+ *   - the reactions share Theta and the steps of Table I; a particle may be
+ *     an A of several reactions or a T of several, never an A of one and a T
+ *     of another, so each reaction step forms at most one bond per particle;
+ *   - a pair is a candidate of reaction r when A and T lie in r's windows,
+ *     r^2 < r_react,r^2 and they are not bonded; its candidate reactions
+ *     c_1 < ... < c_m share one acceptance draw u (Eq. 4): it is retained for
+ *     c_j, the first j with u < p_c1 + ... + p_cj (p_r = k_r dt Theta, summed
+ *     in FP64 in this order), else not retained;
+ *   - one T per A and one A per T are chosen among the retained pairs of all
+ *     reactions as in Table I; a bond takes the increments, style and valence
+ *     limits of its reaction, and its record names the reaction.
+ * PRX_EINVAL when a reaction is invalid (as prx_set_reaction), the thetas
+ * differ, a (type, state) is an A of one reaction and a T of another, or
+ * n_rx > 1 with the nearest-partner rule. */
+int prx_set_reactions(prx_system* sys, const prx_reaction_desc* rx, uint32_t n_rx);
 
 /* ---- execution --------------------------------------------------------- */
 

@@ -233,7 +233,7 @@ __global__ void k_na_apply(NaArgs a) {
         b.t = T;
         b.step = (int64_t)a.step;
         b.style = a.R.style;
-        b.reserved = 0u;
+        b.reaction = 0u;
         a.bonds[pos] = b;
       }
     }
@@ -300,6 +300,8 @@ extern "C" int prx_react_noalloc(const prx_reaction_desc* rx, const double* box,
   cudaStream_t st = (cudaStream_t)cuda_stream;
 
   NaArgs a;
+  a.R = RxParams{};
+  a.R.nr = 1;
   a.n = n;
   a.cap = adj_cap;
   for (int k = 0; k < 3; ++k) {

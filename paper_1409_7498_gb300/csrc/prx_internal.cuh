@@ -56,7 +56,7 @@ struct SoA {
 struct BondRec {
   uint32_t a, t;
   int64_t step;
-  uint32_t style, reserved;
+  uint32_t style, reaction;
 };
 static_assert(sizeof(BondRec) == sizeof(prx_bond), "bond record layout");
 
@@ -87,6 +87,16 @@ struct Ctl {
                                // position, 2 outside the box, 3 type >= 8)
 };
 
+constexpr int MAX_RX = PRX_MAX_REACTIONS;
+
+// The scheme's reactions.  The scalar fields describe reaction 0 and serve
+// the single-reaction kernels as before; with nr > 1 (concurrent reactions)
+// the kernels take the per-reaction arrays.  A particle is an A of the
+// reactions whose A window holds it, a T of those whose T window holds it
+// (never both kinds, checked at set-up); a candidate pair's reactions
+// partition one acceptance draw: reaction c_j of its candidate set m is taken
+// when the draw's 53-bit word is below p53c[m][j] = ceil(P_j 2^53),
+// P_j = p_c1 + ... + p_cj summed in FP64 in the scheme's order.
 struct RxParams {
   uint32_t mask_A, mask_T;
   int32_t a_lo, a_hi, t_lo, t_hi, dA, dT;
@@ -98,7 +108,30 @@ struct RxParams {
   uint32_t style;
   int32_t rule;     // PRX_SELECT_RANDOM or PRX_SELECT_NEAREST
   uint8_t maxval[PRX_MAX_TYPES];
+  // concurrent reactions (nr > 1)
+  int32_t nr;
+  uint32_t mA[MAX_RX], mT[MAX_RX];
+  int32_t alo[MAX_RX], ahi[MAX_RX], tlo[MAX_RX], thi[MAX_RX], dAr[MAX_RX], dTr[MAX_RX];
+  uint32_t styler[MAX_RX];
+  uint8_t maxvalr[MAX_RX][PRX_MAX_TYPES];
+  double rr2r[MAX_RX];
+  uint64_t p53c[1 << MAX_RX][MAX_RX];
 };
+
+// Reactions (bit r) whose A window holds a particle of type t in state s,
+// and likewise for T.
+__device__ __forceinline__ uint32_t rx_elig_A(const RxParams& R, uint32_t t, int s) {
+  uint32_t m = 0;
+  for (int r = 0; r < R.nr; ++r)
+    m |= (((R.mA[r] >> t) & 1u) && s >= R.alo[r] && s <= R.ahi[r]) ? (1u << r) : 0u;
+  return m;
+}
+__device__ __forceinline__ uint32_t rx_elig_T(const RxParams& R, uint32_t t, int s) {
+  uint32_t m = 0;
+  for (int r = 0; r < R.nr; ++r)
+    m |= (((R.mT[r] >> t) & 1u) && s >= R.tlo[r] && s <= R.thi[r]) ? (1u << r) : 0u;
+  return m;
+}
 
 // A particle class of the pair histogram: type in the mask, state in [lo, hi].
 struct PairClass {
@@ -153,6 +186,7 @@ struct Sys {
   uint32_t *count, *fill;
   uint32_t *key, *tmp, *new_of_old;
   uint32_t *win, *blk_count, *blk_off;
+  uint8_t* wch;             // reaction of each A's chosen pair (concurrent reactions)
   BondRec* bonds;
   unsigned long long bond_cap;
   HistRec* hist;

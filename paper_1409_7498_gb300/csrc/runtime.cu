@@ -41,7 +41,9 @@ struct ProfEvent {
 struct prx_system {
   prx_system_desc d{};
   int has_rx = 0;
-  prx_reaction_desc rxd{};
+  prx_reaction_desc rxd{};  // reaction 0 of the scheme (its Theta is the scheme's)
+  prx_reaction_desc rxs[PRX_MAX_REACTIONS]{};
+  uint32_t nrx = 0;         // reactions in the scheme
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t cap = nullptr;
@@ -202,6 +204,31 @@ int validate_rx(prx_system* sys, const prx_reaction_desc* r) {
   if ((r->type_mask_A & r->type_mask_T) && !(r->a_hi < r->t_lo || r->t_hi < r->a_lo))
     return fail(sys, PRX_EINVAL, "A and T state windows overlap for a type in both masks");
   return PRX_OK;
+}
+
+// A set of concurrent reactions: each valid alone, one Theta, the random
+// selection rule when there are several, and no (type, state) that is an A
+// of one reaction and a T of another.
+int validate_rxs(prx_system* sys, const prx_reaction_desc* r, uint32_t n) {
+  if (n < 1 || n > PRX_MAX_REACTIONS) return fail(sys, PRX_EINVAL, "1 to 4 reactions");
+  for (uint32_t q = 0; q < n; ++q) {
+    int rc = validate_rx(sys, &r[q]);
+    if (rc) return rc;
+    if (r[q].theta != r[0].theta) return fail(sys, PRX_EINVAL, "concurrent reactions need one Theta");
+    if (n > 1 && r[q].selection != PRX_SELECT_RANDOM)
+      return fail(sys, PRX_EINVAL, "concurrent reactions use the random selection rule");
+  }
+  for (uint32_t q = 0; q < n; ++q)
+    for (uint32_t w = 0; w < n; ++w)
+      if ((r[q].type_mask_A & r[w].type_mask_T) && !(r[q].a_hi < r[w].t_lo || r[w].t_hi < r[q].a_lo))
+        return fail(sys, PRX_EINVAL, "a (type, state) is an A of one reaction and a T of another");
+  return PRX_OK;
+}
+
+double max_r_react(const prx_system* sys) {
+  double r = 0.0;
+  for (uint32_t q = 0; q < sys->nrx; ++q) r = std::max(r, sys->rxs[q].r_react);
+  return r;
 }
 
 void destroy_graphs(prx_system* s) {
@@ -586,7 +613,7 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
     A.add(&B->adj, (size_t)n * S.cap);
   }
   A.add(&S.P0, n), A.add(&S.P1, n), A.add(&S.key, n), A.add(&S.tmp, n), A.add(&S.new_of_old, n);
-  A.add(&S.win, n), A.add(&S.bonds, (size_t)S.bond_cap);
+  A.add(&S.win, n), A.add(&S.wch, n), A.add(&S.bonds, (size_t)S.bond_cap);
   A.add(&S.hist, (size_t)S.hist_cap + 1), A.add(&S.ctl, 1);
   A.add(&S.red, 4 * ((size_t)(n + RX_THREADS - 1) / RX_THREADS + 1));
   A.add(&S.fout, 3 * (size_t)n), A.add(&S.eout, (size_t)n);
@@ -940,7 +967,7 @@ uint64_t estimate_bytes(const prx_system_desc& d, double r_react) {
   const uint64_t allocs = 40;  // separate cudaMalloc calls, each rounded up
   return 2 * per_set + n * (2 * 16 + 4 * 4) + (n * cap / 2 + 1) * sizeof(prx_bond) +
            (kHistCap + 1ull) * sizeof(prx_history_record) + sizeof(Ctl) + 32 * (n / RX_THREADS + 2) +
-           32 * n + ncell * 12 + 8 * nblk + list_cap * n * nl_bytes + n + allocs * 4096;
+           32 * n + ncell * 12 + 8 * nblk + list_cap * n * nl_bytes + 2 * n + allocs * 4096;
 }
 
 
@@ -1012,19 +1039,27 @@ void prx_destroy(prx_system* sys) {
 }
 
 int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx) {
+  return prx_set_reactions(sys, rx, rx ? 1u : 0u);
+}
+
+int prx_set_reactions(prx_system* sys, const prx_reaction_desc* rx, uint32_t n_rx) {
   if (!sys) return PRX_EINVAL;
   if (sys->batch) return refuse_member(sys);
-  if (!rx) {
+  if (!rx || n_rx == 0) {
     sys->has_rx = 0;
     sys->S.has_rx = 0;
+    sys->nrx = 0;
     destroy_graphs(sys);
     return PRX_OK;
   }
-  int rc = validate_rx(sys, rx);
+  int rc = validate_rxs(sys, rx, n_rx);
   if (rc) return rc;
   CK(cudaStreamSynchronize(sys->stream));
-  sys->rxd = *rx;
+  sys->rxd = rx[0];
+  sys->nrx = n_rx;
+  for (uint32_t q = 0; q < n_rx; ++q) sys->rxs[q] = rx[q];
   RxParams& R = sys->S.R;
+  R = RxParams{};
   R.mask_A = rx->type_mask_A;
   R.mask_T = rx->type_mask_T;
   R.a_lo = rx->a_lo;
@@ -1036,7 +1071,8 @@ int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx) {
   R.p = rx->k * sys->d.dt * (double)rx->theta;
   R.p53 = p53_of(R.p);
   R.rr2 = rx->r_react * rx->r_react;
-  R.rr2_pre = (float)((rx->r_react + 1e-3) * (rx->r_react + 1e-3));
+  const double rmax = max_r_react(sys);
+  R.rr2_pre = (float)((rmax + 1e-3) * (rmax + 1e-3));
   {
     // bound on |r^2(FP32, fixed point) - r^2(FP64)| near the cutoff: the
     // fixed-point positions are within 3 units of L / 2^32, the conversion
@@ -1049,10 +1085,39 @@ int prx_set_reaction(prx_system* sys, const prx_reaction_desc* rx) {
   R.style = (uint32_t)rx->bond_style;
   R.rule = rx->selection;
   for (int t = 0; t < PRX_MAX_TYPES; ++t) R.maxval[t] = rx->max_valence[t];
+  // concurrent reactions: per-reaction parameters and, for every candidate
+  // set m (bit q: reaction q), the cumulative acceptance bounds of its
+  // members in the scheme's order, P_j summed in FP64
+  R.nr = (int32_t)n_rx;
+  double p_r[PRX_MAX_REACTIONS];
+  for (uint32_t q = 0; q < n_rx; ++q) {
+    const prx_reaction_desc& x = rx[q];
+    R.mA[q] = x.type_mask_A;
+    R.mT[q] = x.type_mask_T;
+    R.alo[q] = x.a_lo;
+    R.ahi[q] = x.a_hi;
+    R.tlo[q] = x.t_lo;
+    R.thi[q] = x.t_hi;
+    R.dAr[q] = x.dA;
+    R.dTr[q] = x.dT;
+    R.styler[q] = (uint32_t)x.bond_style;
+    for (int t = 0; t < PRX_MAX_TYPES; ++t) R.maxvalr[q][t] = x.max_valence[t];
+    R.rr2r[q] = x.r_react * x.r_react;
+    p_r[q] = x.k * sys->d.dt * (double)x.theta;
+  }
+  for (uint32_t m = 1; m < (1u << n_rx); ++m) {
+    double P = 0.0;
+    int j = 0;
+    for (uint32_t q = 0; q < n_rx; ++q) {
+      if (!((m >> q) & 1u)) continue;
+      P = P + p_r[q];
+      R.p53c[m][j++] = p53_of(P);
+    }
+  }
   sys->has_rx = 1;
   sys->S.has_rx = 1;
   destroy_graphs(sys);
-  const double need = std::max(wca_rc(sys->d), rx->r_react);
+  const double need = std::max(wca_rc(sys->d), rmax);
   if (need > sys->grid_rcut) {
     if ((rc = setup_grid(sys, need))) return rc;
     if ((rc = full_rebin(sys, 1))) return rc;
@@ -1417,8 +1482,12 @@ int prx_save(prx_system* sys, const char* path) {
   const uint64_t magic = kCkptMagic, step = sys->ctl_host->step;
   W(&magic, 8);
   W(&sys->d, sizeof(sys->d));
-  W(&sys->has_rx, sizeof(int));
+  // the reaction count (0 or 1 in files with at most one reaction), then
+  // the first reaction and, with several, the others
+  const int nrx = sys->has_rx ? (int)sys->nrx : 0;
+  W(&nrx, sizeof(int));
   W(&sys->rxd, sizeof(sys->rxd));
+  for (int q = 1; q < nrx; ++q) W(&sys->rxs[q], sizeof(sys->rxs[q]));
   W(&step, 8);
   W(&nb, 8);
   W(&sys->grid_rcut, 8);
@@ -1453,7 +1522,7 @@ int prx_load(const char* path, void* cuda_stream, prx_system** out) {
   };
   uint64_t magic = 0, step = 0, nb = 0;
   prx_system_desc d;
-  prx_reaction_desc rxd;
+  prx_reaction_desc rxs[PRX_MAX_REACTIONS];
   int has_rx = 0;
   double grid_rcut = 0.0;
   R(&magic, 8);
@@ -1463,7 +1532,9 @@ int prx_load(const char* path, void* cuda_stream, prx_system** out) {
   }
   R(&d, sizeof(d));
   R(&has_rx, sizeof(int));
-  R(&rxd, sizeof(rxd));
+  if (has_rx < 0 || has_rx > PRX_MAX_REACTIONS) ok = false;
+  R(&rxs[0], sizeof(rxs[0]));
+  for (int q = 1; ok && q < has_rx; ++q) R(&rxs[q], sizeof(rxs[q]));
   R(&step, 8);
   R(&nb, 8);
   R(&grid_rcut, 8);
@@ -1523,7 +1594,7 @@ int prx_load(const char* path, void* cuda_stream, prx_system** out) {
                        wref.data(), nn.data(), nl.data(), lcap, &sys);
   if (rc) return rc;
   if (has_rx) {
-    rc = prx_set_reaction(sys, &rxd);
+    rc = prx_set_reactions(sys, rxs, (uint32_t)has_rx);
     if (rc) {
       prx_destroy(sys);
       return rc;
@@ -1813,7 +1884,7 @@ int prx_batch_add(prx_batch* b, prx_system* sys) {
   if (cudaStreamSynchronize(sys->stream) != cudaSuccess)
     return bfail(b, PRX_ECUDA, "synchronising the system's stream failed");
   if (b->max_slots || b->mem_budget) {
-    if ((rc = take_slot(b, sys, estimate_bytes(sys->d, sys->has_rx ? sys->rxd.r_react : 0.0), false, 0)))
+    if ((rc = take_slot(b, sys, estimate_bytes(sys->d, max_r_react(sys)), false, 0)))
       return rc;
   }
   join(b, sys);
@@ -1825,7 +1896,7 @@ int prx_batch_admit(prx_batch* b, prx_system* sys, uint64_t nsteps, int32_t* slo
   *slot = -1;
   int rc = check_member(b, sys);
   if (rc) return rc;
-  if ((rc = take_slot(b, sys, estimate_bytes(sys->d, sys->has_rx ? sys->rxd.r_react : 0.0), true, nsteps)))
+  if ((rc = take_slot(b, sys, estimate_bytes(sys->d, max_r_react(sys)), true, nsteps)))
     return rc;
   // the system's queued work (creation, earlier runs) comes before the batch's
   if (!sys->join_ev && cudaEventCreateWithFlags(&sys->join_ev, cudaEventDisableTiming) != cudaSuccess) {

@@ -79,7 +79,8 @@ __device__ __forceinline__ void rx_compact_body(const Sys& S, const Blk blk) {
   bool el = false;
   if (i < S.n) {
     S.win[i] = NONE;
-    el = in_window(R.mask_A, R.a_lo, R.a_hi, B.type[i], B.state[i]);
+    el = R.nr > 1 ? rx_elig_A(R, B.type[i], B.state[i]) != 0u
+                  : in_window(R.mask_A, R.a_lo, R.a_hi, B.type[i], B.state[i]);
   }
   // one atomic per block: warp ballots, block prefix in shared memory
   __shared__ uint32_t wcnt[RX_THREADS / 32];
@@ -177,6 +178,67 @@ __device__ __forceinline__ void rx_accept_and_key(const Sys& S, const SoA& B,
   }
 }
 
+// Steps 1-5 for one eligible A of a scheme of concurrent reactions: its
+// candidate pairs, each with its set m of candidate reactions (A and T in the
+// reaction's windows, exact FP64 r^2 below the reaction's cutoff, not
+// bonded), one acceptance draw against the cumulative bounds of m, and the
+// retained pair of smallest selection key.  `ch` receives the chosen pair's
+// reaction.
+template <bool NL16>
+__device__ __forceinline__ uint32_t rx_find_multi(const Sys& S, const SoA& B, const uint4* P,
+                                                  unsigned long long step, uint32_t i,
+                                                  long long& ncand, long long& nret, uint32_t& ch) {
+  const RxParams& R = S.R;
+  const uint32_t elA = rx_elig_A(R, B.type[i], B.state[i]);
+  const uint4 pi = P[i];
+  const uint32_t idi = B.id[i];
+  const uint32_t nb = B.nadj[i];
+  uint32_t best = NONE, bestid = 0u;
+  unsigned long long bestkey = 0ull;
+  const int cnt = S.nn[i];
+  for (int k = 0; k < cnt; ++k) {
+    const uint32_t j = nl_get_rx<NL16>(S, k, i);
+    const uint4 pj = P[j];
+    const float ex = __int2float_rn(pdiff(pj.x, pi.x)) * S.scale[0];
+    const float ey = __int2float_rn(pdiff(pj.y, pi.y)) * S.scale[1];
+    const float ez = __int2float_rn(pdiff(pj.z, pi.z)) * S.scale[2];
+    if (!(fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < R.rr2_pre)) continue;  // beyond every cutoff
+    const uint32_t el = elA & rx_elig_T(R, B.type[j], B.state[j]);
+    if (!el) continue;
+    const double ddx = min_image(__dsub_rn(B.x[j], B.x[i]), S.L[0], S.halfL[0]);
+    const double ddy = min_image(__dsub_rn(B.y[j], B.y[i]), S.L[1], S.halfL[1]);
+    const double ddz = min_image(__dsub_rn(B.z[j], B.z[i]), S.L[2], S.halfL[2]);
+    const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
+    uint32_t m = 0u;
+    for (int r = 0; r < R.nr; ++r)
+      if (((el >> r) & 1u) && r2 < R.rr2r[r]) m |= 1u << r;
+    if (!m) continue;
+    bool bonded = false;
+    for (uint32_t b = 0; b < nb; ++b) bonded |= (B.adj[(size_t)i * S.cap + b] & SLOT_MASK) == j;
+    if (bonded) continue;
+    ++ncand;
+    const uint32_t idj = B.id[j];
+    const uint4 wa = keyed_draw(S.seed, step, idi, idj, TAG_ACCEPT);
+    const unsigned long long u53 = (((unsigned long long)wa.x << 32) | wa.y) >> 11;
+    int c = -1, q = 0;
+    for (int r = 0; r < R.nr && c < 0; ++r) {
+      if (!((m >> r) & 1u)) continue;
+      if (u53 < R.p53c[m][q]) c = r;
+      ++q;
+    }
+    if (c < 0) continue;
+    ++nret;
+    const unsigned long long key = key64(keyed_draw(S.seed, step, idi, idj, TAG_SEL_A));
+    if (best == NONE || key < bestkey || (key == bestkey && idj < bestid)) {
+      best = j;
+      bestkey = key;
+      bestid = idj;
+      ch = (uint32_t)c;
+    }
+  }
+  return best;
+}
+
 template <bool NL16>
 __device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long long step_arg) {
   const RxParams& R = S.R;
@@ -192,6 +254,10 @@ __device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long l
     uint32_t best = NONE;
     if (R.rule == PRX_SELECT_NEAREST) {
       best = nearest_partner<NL16>(S, B, P, i, true, ncand);
+    } else if (R.nr > 1) {
+      uint32_t ch = 0u;
+      best = rx_find_multi<NL16>(S, B, P, step, i, ncand, nret, ch);
+      S.wch[i] = (uint8_t)ch;
     } else {
       const uint4 pi = P[i];
       const uint32_t idi = B.id[i];
@@ -368,12 +434,16 @@ __device__ __forceinline__ void rx_select_apply_body(const Sys& S, const Blk blk
       nwin += winner ? 1 : 0;
     }
     bool form = false;
-    uint32_t na = 0, nt = 0;
+    uint32_t na = 0, nt = 0, ch = 0;
     if (T != NONE) {
       ++nfin;
       const uint32_t ta = B.type[i], tt = B.type[T];
-      const uint32_t capA = R.maxval[ta] < S.cap ? R.maxval[ta] : S.cap;
-      const uint32_t capT = R.maxval[tt] < S.cap ? R.maxval[tt] : S.cap;
+      // the pair's reaction sets the valence limits, increments and style
+      ch = R.nr > 1 ? (uint32_t)S.wch[i] : 0u;
+      const uint32_t mva = R.nr > 1 ? R.maxvalr[ch][ta] : R.maxval[ta];
+      const uint32_t mvt = R.nr > 1 ? R.maxvalr[ch][tt] : R.maxval[tt];
+      const uint32_t capA = mva < S.cap ? mva : S.cap;
+      const uint32_t capT = mvt < S.cap ? mvt : S.cap;
       na = B.nadj[i];
       nt = B.nadj[T];
       form = na < capA && nt < capT;
@@ -391,19 +461,20 @@ __device__ __forceinline__ void rx_select_apply_body(const Sys& S, const Blk blk
       set_status(ctl, PRX_ECAPACITY);
       continue;
     }
-    const uint32_t sbit = R.style << 31;
+    const uint32_t style = R.nr > 1 ? R.styler[ch] : R.style;
+    const uint32_t sbit = style << 31;
     B.adj[(size_t)i * S.cap + na] = T | sbit;
     B.nadj[i] = (uint8_t)(na + 1);
     B.adj[(size_t)T * S.cap + nt] = i | sbit;
     B.nadj[T] = (uint8_t)(nt + 1);
-    B.state[i] = (int8_t)(B.state[i] + R.dA);
-    B.state[T] = (int8_t)(B.state[T] + R.dT);
+    B.state[i] = (int8_t)(B.state[i] + (R.nr > 1 ? R.dAr[ch] : R.dA));
+    B.state[T] = (int8_t)(B.state[T] + (R.nr > 1 ? R.dTr[ch] : R.dT));
     BondRec rec;
     rec.a = B.id[i];
     rec.t = B.id[T];
     rec.step = (int64_t)step;
-    rec.style = R.style;
-    rec.reserved = 0u;
+    rec.style = style;
+    rec.reaction = ch;
     S.bonds[pos] = rec;
   }
   const long long cw = block_sum_ll(nwin);

@@ -49,11 +49,11 @@ class prx_reaction_desc(C.Structure):
 
 class prx_bond(C.Structure):
     _fields_ = [("a", C.c_uint32), ("t", C.c_uint32), ("step", C.c_int64), ("style", C.c_uint32),
-                ("reserved", C.c_uint32)]
+                ("reaction", C.c_uint32)]
 
 
 BOND_DTYPE = np.dtype([("a", "<u4"), ("t", "<u4"), ("step", "<i8"), ("style", "<u4"),
-                       ("reserved", "<u4")])
+                       ("reaction", "<u4")])
 
 
 class prx_rx_trace(C.Structure):
@@ -111,6 +111,7 @@ def lib():
         "prx_destroy": ([VP], None),
         "prx_estimate_bytes": ([P(prx_system_desc), P(prx_reaction_desc), P(U64)], I),
         "prx_set_reaction": ([VP, P(prx_reaction_desc)], I),
+        "prx_set_reactions": ([VP, P(prx_reaction_desc), C.c_uint32], I),
         "prx_run": ([VP, U64], I),
         "prx_sync": ([VP], I),
         "prx_react_once": ([VP, U64, P(prx_rx_trace)], I),
@@ -223,6 +224,13 @@ def prx_estimate_bytes(desc: prx_system_desc, rx: prx_reaction_desc | None = Non
 
 def prx_set_reaction(h, rx):
     _check(lib().prx_set_reaction(h, C.byref(rx) if rx is not None else None), h)
+
+
+def prx_set_reactions(h, rxs):
+    """Sets the concurrent reactions `rxs` (a sequence of prx_reaction_desc;
+    empty clears the scheme)."""
+    arr = (prx_reaction_desc * max(1, len(rxs)))(*rxs)
+    _check(lib().prx_set_reactions(h, arr, len(rxs)), h)
 
 
 def prx_run(h, nsteps: int):
@@ -578,6 +586,9 @@ class System:
 
     def set_reaction(self, rx):
         prx_set_reaction(self.h, rx)
+
+    def set_reactions(self, rxs):
+        prx_set_reactions(self.h, list(rxs))
 
     def run(self, nsteps):
         prx_run(self.h, nsteps)

@@ -31,6 +31,7 @@ TYPE_B = 0
 TYPE_A = 1
 TYPE_E = 2   # chain end unit E of an E-P_n-E chain (Sec. II.B)
 TYPE_P = 3   # repeat unit P of an E-P_n-E chain (does not react)
+TYPE_X6 = 4  # second crosslinker type (functionality 6) of the concurrent-reaction inputs
 DENSITY = 0.85
 BASE_SEED = 14097498
 
@@ -232,6 +233,33 @@ def chain_growth_scheme(k: float, theta: int = 10, r_react: float = 1.1,
     return dict(mask_A=(1 << TYPE_A) | (1 << TYPE_B), mask_T=1 << TYPE_B, a_lo=2, a_hi=2, t_lo=0,
                 t_hi=0, dA=-1, dT=+2, k=k, theta=theta, r_react=r_react, bond_style=bond_style,
                 max_valence=tuple(mv), selection=selection)
+
+
+def step_growth_mixed(n_B: int, n_A: int, n_X6: int, seed: int, **kw) -> Inputs:
+    """Step growth with two crosslinker types: n_A of functionality 4 (type A,
+    state 4) and n_X6 of functionality 6 (type X6, state 6), with difunctional
+    B targets; the input of the concurrent-reaction scheme below."""
+    inp = step_growth(n_B, n_A + n_X6, 4, seed, **kw)
+    rng = np.random.default_rng(seed + 1)
+    x6 = rng.permutation(np.flatnonzero(inp.type == TYPE_A))[:n_X6]
+    inp.type[x6] = TYPE_X6
+    inp.state[x6] = 6
+    return inp
+
+
+def concurrent_schemes(k_first: float, k_later: float, k_x6: float, theta: int = 10,
+                       r_react: float = 1.1, r_react_x6: float = 1.05) -> list:
+    """Three concurrent reactions on the same B targets (a substitution
+    effect and a second crosslinker type): a 4-functional crosslinker's first
+    bond at k_first, its later bonds at k_later, and the 6-functional
+    crosslinker's bonds at k_x6 with its own cutoff."""
+    mv = [0] * 8
+    mv[TYPE_B], mv[TYPE_A], mv[TYPE_X6] = 2, 4, 6
+    base = dict(mask_T=1 << TYPE_B, t_lo=0, t_hi=1, dA=-1, dT=+1, theta=theta, bond_style=0,
+                max_valence=tuple(mv), selection=0)
+    return [dict(base, mask_A=1 << TYPE_A, a_lo=4, a_hi=4, k=k_first, r_react=r_react),
+            dict(base, mask_A=1 << TYPE_A, a_lo=1, a_hi=3, k=k_later, r_react=r_react),
+            dict(base, mask_A=1 << TYPE_X6, a_lo=1, a_hi=6, k=k_x6, r_react=r_react_x6)]
 
 
 CHAIN_PHI0 = 328 / 33_096  # initiator fraction of the chain-growth workload
