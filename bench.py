@@ -43,6 +43,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
+from paper_1409_7498_gb300.warmup import CAP_STEPS, F_CAP, FREE_STEPS, warmed_liquid  # noqa: E402
 
 WORKLOAD = "step_growth_1m"
 N_BEADS = 1_048_576
@@ -52,9 +53,6 @@ THETA = 10
 MD_STEPS = 20_000
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SKINS = (0.3, 0.35, 0.4, 0.45, 0.5)  # autotuner candidates
-# warm-up of the uniform placement (App. A protocol): capped WCA, then uncapped
-F_CAP, CAP_STEPS, FREE_STEPS = 100.0, 2000, 1000
-WARM_SEED_OFFSET = 1_000_003  # the warm-up's thermostat draws differ from the run's
 
 
 def parse():
@@ -98,23 +96,6 @@ def inputs(rank: int, placement: str = "uniform"):
 
 def scheme():
     return synth.step_growth_scheme(FUNC, k=K_RATE, theta=THETA)
-
-
-def warmed_liquid(P, inp, adj_cap: int, seed: int, fp64: bool = False, stream=None):
-    """The workloads' start: the seeded uniform placement `inp` relaxed by
-    CAP_STEPS Langevin steps with the WCA pair force capped at F_CAP, then
-    FREE_STEPS uncapped steps, no reactions (App. A protocol), run by the
-    library on the GPU.  Returns host positions and half-step velocities by
-    particle id.  Untimed preparation of the input."""
-    ws = seed + WARM_SEED_OFFSET
-    d1 = P.make_desc(inp.n, inp.L, adj_cap=adj_cap, seed=ws, force_cap=F_CAP)
-    with P.System(d1, inp.x, inp.v, inp.type, inp.state, stream=stream) as g:
-        g.run(CAP_STEPS)
-        x, v = g.positions(), g.velocities()
-    d2 = P.make_desc(inp.n, inp.L, adj_cap=adj_cap, seed=ws + 1, fp64=fp64)
-    with P.System(d2, x, v, inp.type, inp.state, stream=stream) as g:
-        g.run(FREE_STEPS)
-        return g.positions(), g.velocities()
 
 
 class Clocks:

@@ -67,3 +67,28 @@ def force_errors(f_gpu: np.ndarray, f_ref: np.ndarray) -> dict:
     df = np.sqrt(((f_gpu - f_ref) ** 2).sum(1))
     rms = np.sqrt(((f_ref ** 2).sum(1)).mean())
     return dict(max_over_rms=float(df.max() / rms), rms_rel=float(np.sqrt((df ** 2).mean()) / rms))
+
+
+def chain_ree2(x, bonds, types, states, L):
+    """Squared end-to-end distances of the chains (initiator to active end),
+    bond vectors summed under the minimum image."""
+    n = len(types)
+    adj = [[] for _ in range(n)]
+    for a, t in bonds:
+        adj[a].append(t)
+        adj[t].append(a)
+    out = []
+    for s in np.nonzero(types == synth.TYPE_A)[0]:
+        if not adj[s]:
+            continue
+        prev, cur, r, length = -1, s, np.zeros(3), 0
+        while True:
+            nxt = [q for q in adj[cur] if q != prev]
+            if not nxt:
+                break
+            d = x[nxt[0]] - x[cur]
+            r += d - L * np.round(d / L)
+            prev, cur, length = cur, nxt[0], length + 1
+        if length >= 3:
+            out.append(float(r @ r))
+    return out

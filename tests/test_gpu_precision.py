@@ -17,7 +17,7 @@ import pytest
 
 import oracle as orc
 import synth
-from helpers import gpu, gpu_reaction, gpu_system
+from helpers import chain_ree2, gpu, gpu_reaction, gpu_system
 
 pytestmark = pytest.mark.gpu
 A, B = synth.TYPE_A, synth.TYPE_B
@@ -64,31 +64,6 @@ def test_nve_energy_drift_against_the_oracle(P):
          (("oracle", e_o), ("gpu_fp64", e_64), ("gpu_fp32", e_32))}
     assert d["gpu_fp64"] <= 2.0 * d["oracle"] + 1e-6, d
     assert d["gpu_fp32"] <= 5.0 * d["oracle"] + 2e-5, d
-
-
-def chain_ree2(x, bonds, types, states, L):
-    """Squared end-to-end distances of the chains (initiator to active end),
-    bond vectors summed under the minimum image."""
-    n = len(types)
-    adj = [[] for _ in range(n)]
-    for a, t in bonds:
-        adj[a].append(t)
-        adj[t].append(a)
-    out = []
-    for s in np.nonzero(types == A)[0]:
-        if not adj[s]:
-            continue
-        prev, cur, r, length = -1, s, np.zeros(3), 0
-        while True:
-            nxt = [q for q in adj[cur] if q != prev]
-            if not nxt:
-                break
-            d = x[nxt[0]] - x[cur]
-            r += d - L * np.round(d / L)
-            prev, cur, length = cur, nxt[0], length + 1
-        if length >= 3:
-            out.append(float(r @ r))
-    return out
 
 
 def oracle_chains(seed):
