@@ -353,6 +353,55 @@ int prx_autotune_skin(const prx_system_desc* desc, const double* pos, const doub
                       uint32_t steps, const double* skins, uint32_t n_skins, double* best_skin,
                       double* ms_per_step);
 
+/* Launch configuration of a system's kernels.  Every choice changes only the
+ * speed: a run gives the same result, bit for bit, under any of them (one
+ * thread computes each particle's forces and update whatever the block
+ * shape, and a graph replay of m intervals launches the same kernels as m
+ * replays of one). */
+typedef struct {
+  uint32_t step_threads;       /* threads per block of the step kernel: 128, 256 or 512 (0: 256) */
+  uint32_t step_blocks_per_sm; /* blocks per SM of its persistent grid (0: as many as fit) */
+  uint32_t chunk_intervals;    /* reaction intervals per CUDA-graph replay in prx_run, 1..64
+                                  (0: 1); without a scheme, chunks of 10 steps */
+  uint32_t reserved;           /* must be 0 */
+} prx_launch_config;
+
+/* PRX_EINVAL for values out of range, a batch member, or a FP64-force
+ * system with step_threads other than 0 or 256 (its kernels are fixed). */
+int prx_set_launch_config(prx_system* sys, const prx_launch_config* cfg);
+int prx_get_launch_config(prx_system* sys, prx_launch_config* cfg);
+
+/* One autotuner candidate: skin, launch configuration, measured time. */
+typedef struct {
+  double skin;
+  prx_launch_config launch;
+  double ms_per_step;     /* -1: the candidate could not run */
+  uint32_t stage;         /* 0 skin, 1 block shape, 2 interval batching */
+  uint32_t cached;        /* 1: taken from the cache, not timed in this call */
+} prx_tune_choice;
+
+/* The library's autotuner over the Verlet skin (cell size and rebuild
+ * interval), the step kernel's block shape and the reaction-interval
+ * batching, by coordinate search: every skin with the default launch, then
+ * every (threads, blocks per SM) pair at the best skin, then every chunk
+ * length at the best of those.  Each candidate is a temporary system built
+ * from the inputs (as prx_autotune_skin), timed with CUDA events over
+ * `steps` steps (rounded up to whole chunks) after a warm-up.  Empty lists
+ * (count 0) keep the default of that dimension.  *best receives the fastest
+ * candidate of the last stage; tried (may be NULL) up to tried_cap of the
+ * timed candidates, *n_tried their count.  Results are cached for the
+ * process, keyed by particle count, density, adjacency capacity, force
+ * precision and reaction scheme (cutoff, Theta, rate), and by the candidate
+ * lists; with cache_path non-NULL also in that text file (read before
+ * timing, appended after), so another run can reuse them.  A cached
+ * result comes back with best->cached = 1 and no candidate timed. */
+int prx_autotune(const prx_system_desc* desc, const double* pos, const double* vel,
+                 const uint8_t* type, const int8_t* state, const prx_reaction_desc* rx,
+                 uint32_t steps, const double* skins, uint32_t n_skins, const uint32_t* threads,
+                 const uint32_t* blocks_per_sm, uint32_t n_shapes, const uint32_t* chunks,
+                 uint32_t n_chunks, const char* cache_path, prx_tune_choice* best,
+                 prx_tune_choice* tried, uint32_t tried_cap, uint32_t* n_tried);
+
 /* ---- batched ensemble -------------------------------------------------------- */
 /* A batch advances many independent systems (replicas of different sizes,
  * schemes, rates and seeds) together: every MD step is ONE kernel launch

@@ -329,11 +329,14 @@ __device__ __forceinline__ void step_nl_body(const Sys& S, const Blk blk,
   if constexpr (!FORCES_ONLY) step_epilogue(S, ph, step, cond, use_cond, &warps_left, blk.nb);
 }
 
-// Single system: as many blocks as are resident at once, each warp taking
-// 32-slot chunks strided by the grid's warp count, so that every SM stays
-// fully occupied to the end instead of running a partial last wave.
-template <bool NL16, bool FORCES_ONLY, bool CUBIC>
-__global__ void __launch_bounds__(256, 6)
+// Single system: as many blocks as are resident at once (or the launch
+// configuration's blocks per SM), each warp taking 32-slot chunks strided by
+// the grid's warp count, so that every SM stays fully occupied to the end
+// instead of running a partial last wave.  BT threads per block, with the
+// register budget of 48 resident warps per SM for every BT; the block shape
+// changes only the scheduling, not any particle's arithmetic.
+template <bool NL16, bool FORCES_ONLY, bool CUBIC, int BT>
+__global__ void __launch_bounds__(BT, 1536 / BT)
     k_step_nl(Sys S, cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ unsigned int warps_left;
   if (threadIdx.x == 0) warps_left = blockDim.x >> 5;
@@ -1209,15 +1212,31 @@ void launch_stage_input(const Sys& S, cudaStream_t st, const double* buf, int wh
 }
 
 // Blocks of `threads` threads of kernel `kern` resident on the whole current
-// device at once (cached per device and kernel id: 0-7 the step kernel's
-// variants).
+// device at once (cached per device and kernel id: the step kernel's
+// variants and block sizes).
+// Multiprocessors of the current device (cached per device).
+unsigned device_sms() {
+  static unsigned cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1u;
+  if (!cache[dev]) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      return 1u;
+    }
+    cache[dev] = (unsigned)sms;
+  }
+  return cache[dev];
+}
+
 unsigned resident_blocks(int variant, const void* kern, int threads) {
   static std::mutex mu;
-  static unsigned cache[64][16];
+  static unsigned cache[64][64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1u;
   std::lock_guard<std::mutex> lk(mu);
-  unsigned& c = cache[dev][variant & 15];
+  unsigned& c = cache[dev][variant & 63];
   if (!c) {
     int sms = 0, per = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -1238,13 +1257,30 @@ void launch_step(const Sys& S, cudaStream_t st, int fp64, int forces_only,
     else k_forces64<false><<<g, STEP_THREADS, 0, st>>>(S);
     if (!forces_only) k_integrate64<<<g, STEP_THREADS, 0, st>>>(S, h, use_cond);
   } else {
-    const unsigned g0 = blocks_for(S.n, 256) > 0 ? blocks_for(S.n, 256) : 1;
+    // forces-only launches keep 256 threads; the step takes the launch
+    // configuration's block size and blocks per SM
+    const int bt = forces_only ? 256 : S.step_bt;
     auto K = [&](auto nl16, auto fo, auto cub) {
-      constexpr int v = (decltype(nl16)::value ? 4 : 0) + (decltype(fo)::value ? 2 : 0) +
-                        (decltype(cub)::value ? 1 : 0);
-      auto* kern = k_step_nl<decltype(nl16)::value, decltype(fo)::value, decltype(cub)::value>;
-      const unsigned r = resident_blocks(v, (const void*)kern, 256);
-      kern<<<(g0 < r ? g0 : r), 256, 0, st>>>(S, h, use_cond);
+      constexpr bool N16 = decltype(nl16)::value, FO = decltype(fo)::value, CU = decltype(cub)::value;
+      constexpr int v = (N16 ? 4 : 0) + (FO ? 2 : 0) + (CU ? 1 : 0);
+      auto go = [&](auto btc) {
+        constexpr int BT = decltype(btc)::value;
+        auto* kern = k_step_nl<N16, FO, CU, BT>;
+        const unsigned g0 = blocks_for(S.n, BT) > 0 ? blocks_for(S.n, BT) : 1;
+        unsigned r = resident_blocks(v + 8 * (BT == 128 ? 1 : (BT == 512 ? 2 : 0)), (const void*)kern, BT);
+        if (!FO && S.step_bpsm > 0) {
+          const unsigned want = (unsigned)S.step_bpsm * (unsigned)device_sms();
+          r = want < r ? want : r;
+        }
+        kern<<<(g0 < r ? g0 : r), BT, 0, st>>>(S, h, use_cond);
+      };
+      if constexpr (FO) {
+        go(std::integral_constant<int, 256>{});
+      } else {
+        if (bt == 128) go(std::integral_constant<int, 128>{});
+        else if (bt == 512) go(std::integral_constant<int, 512>{});
+        else go(std::integral_constant<int, 256>{});
+      }
     };
     using T_ = std::true_type;
     using F_ = std::false_type;

@@ -201,6 +201,9 @@ struct Sys {
   // batch's control block
   int in_batch;
   BatchCtl* batch;
+  // launch configuration of the single-system step kernel (host side)
+  int step_bt;              // threads per block: 128, 256 or 512
+  int step_bpsm;            // blocks per SM of the persistent grid (0: all that fit)
   unsigned int n_members;   // members of the batch (last-member detection)
 };
 

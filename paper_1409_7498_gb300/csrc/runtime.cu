@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -65,6 +66,8 @@ struct prx_system {
   uint64_t graph_rx_launches = 0;  // reaction sequences replayed inside graphs
   uint64_t other_launches = 0;     // other kernels launched directly (reaction, forces, observables)
   cudaGraphExec_t g_step = nullptr, g_chunk = nullptr, g_react = nullptr;
+  cudaGraphExec_t g_chunk1 = nullptr;  // one interval, when g_chunk holds several
+  uint32_t chunk_m = 1;                // reaction intervals per g_chunk replay
   bool graphs_valid = false;
   bool profiling = false;
   std::vector<ProfEvent> prof;
@@ -234,8 +237,9 @@ double max_r_react(const prx_system* sys) {
 void destroy_graphs(prx_system* s) {
   if (s->g_step) cudaGraphExecDestroy(s->g_step);
   if (s->g_chunk) cudaGraphExecDestroy(s->g_chunk);
+  if (s->g_chunk1) cudaGraphExecDestroy(s->g_chunk1);
   if (s->g_react) cudaGraphExecDestroy(s->g_react);
-  s->g_step = s->g_chunk = s->g_react = nullptr;
+  s->g_step = s->g_chunk = s->g_chunk1 = s->g_react = nullptr;
   s->graphs_valid = false;
 }
 
@@ -382,13 +386,15 @@ int full_rebin(prx_system* sys, int mode) {
 // reaction kernels into one executable graph.  `step(h)` launches the step
 // kernel(s) that set the conditional handle h; `rebuild()` and `rx()` the
 // rebuild and reaction sequences; all on the capture stream.
+// With reps > 1 the (steps, reaction) sequence is captured reps times.
 template <class StepF, class RebuildF, class RxF>
 cudaError_t capture_graph(cudaStream_t cap, int nsteps, bool with_rx, StepF step, RebuildF rebuild,
-                          RxF rx, cudaGraphExec_t* out) {
+                          RxF rx, cudaGraphExec_t* out, int reps = 1) {
   cudaGraph_t g;
   CE(cudaGraphCreate(&g, 0));
   std::vector<cudaGraph_t> bodies;
   CE(cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  for (int rep = 0; rep < reps; ++rep) {
   for (int s = 0; s < nsteps; ++s) {
     cudaGraphConditionalHandle h;
     CE(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
@@ -408,6 +414,7 @@ cudaError_t capture_graph(cudaStream_t cap, int nsteps, bool with_rx, StepF step
     CE(cudaStreamUpdateCaptureDependencies(cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
   }
   if (with_rx) rx();
+  }
   CE(cudaStreamEndCapture(cap, &g));
   for (cudaGraph_t body : bodies) {
     CE(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -420,13 +427,13 @@ cudaError_t capture_graph(cudaStream_t cap, int nsteps, bool with_rx, StepF step
   return cudaSuccess;
 }
 
-int build_graph(prx_system* sys, int nsteps, bool with_rx, cudaGraphExec_t* out) {
+int build_graph(prx_system* sys, int nsteps, bool with_rx, cudaGraphExec_t* out, int reps = 1) {
   const bool fp64 = sys->d.force_precision == PRX_FORCE_FP64;
   CK(capture_graph(
       sys->cap, nsteps, with_rx,
       [&](cudaGraphConditionalHandle h) { launch_step(sys->S, sys->cap, fp64, 0, h, 1); },
       [&] { launch_rebin(sys->S, sys->cap, 0, nullptr, nullptr); },
-      [&] { launch_rx(sys->S, sys->cap, -1, nullptr, nullptr); }, out));
+      [&] { launch_rx(sys->S, sys->cap, -1, nullptr, nullptr); }, out, reps));
   return PRX_OK;
 }
 
@@ -435,11 +442,14 @@ int ensure_graphs(prx_system* sys) {
   destroy_graphs(sys);
   int rc;
   if ((rc = build_graph(sys, 1, false, &sys->g_step))) return rc;
+  const int m = (int)sys->chunk_m;
   if (sys->has_rx) {
-    if ((rc = build_graph(sys, (int)sys->rxd.theta, true, &sys->g_chunk))) return rc;
+    if ((rc = build_graph(sys, (int)sys->rxd.theta, true, &sys->g_chunk, m))) return rc;
+    if (m > 1 && (rc = build_graph(sys, (int)sys->rxd.theta, true, &sys->g_chunk1))) return rc;
     if ((rc = build_graph(sys, 0, true, &sys->g_react))) return rc;
   } else {
-    if ((rc = build_graph(sys, kNoRxChunk, false, &sys->g_chunk))) return rc;
+    if ((rc = build_graph(sys, kNoRxChunk, false, &sys->g_chunk, m))) return rc;
+    if (m > 1 && (rc = build_graph(sys, kNoRxChunk, false, &sys->g_chunk1))) return rc;
   }
   sys->graphs_valid = true;
   return PRX_OK;
@@ -587,6 +597,8 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
   S.thermo = desc->gamma > 0.0 ? 1 : 0;
   S.seed = desc->seed;
   S.hist_cap = kHistCap;
+  S.step_bt = 256;
+  S.step_bpsm = 0;
   S.bond_cap = std::max<unsigned long long>(1ull, ((unsigned long long)n * S.cap) / 2ull);
 
   if (stream) {
@@ -1143,13 +1155,16 @@ int prx_run(prx_system* sys, uint64_t nsteps) {
   int rc = ensure_graphs(sys);
   if (rc) return rc;
   const uint64_t theta = sys->has_rx ? sys->rxd.theta : (uint64_t)kNoRxChunk;
+  const uint64_t m = sys->chunk_m;
   while (nsteps > 0) {
     if (sys->host_step % theta == 0 && nsteps >= theta) {
-      CK(cudaGraphLaunch(sys->g_chunk, sys->stream));
-      sys->host_step += theta;
-      sys->step_launches += theta;
-      if (sys->has_rx) sys->graph_rx_launches++;
-      nsteps -= theta;
+      const bool many = m > 1 && nsteps >= m * theta;
+      const uint64_t k = many || m == 1 ? m : 1;  // intervals in this replay
+      CK(cudaGraphLaunch(many || m == 1 ? sys->g_chunk : sys->g_chunk1, sys->stream));
+      sys->host_step += k * theta;
+      sys->step_launches += k * theta;
+      if (sys->has_rx) sys->graph_rx_launches += k;
+      nsteps -= k * theta;
     } else {
       CK(cudaGraphLaunch(sys->g_step, sys->stream));
       sys->host_step++;
@@ -1685,6 +1700,198 @@ int prx_autotune_skin(const prx_system_desc* desc, const double* pos, const doub
     return PRX_EINVAL;
   }
   *best_skin = best;
+  return PRX_OK;
+}
+
+int prx_set_launch_config(prx_system* sys, const prx_launch_config* cfg) {
+  if (!sys || !cfg) return PRX_EINVAL;
+  if (sys->batch) return refuse_member(sys);
+  const uint32_t bt = cfg->step_threads ? cfg->step_threads : 256u;
+  if ((bt != 128u && bt != 256u && bt != 512u) || cfg->reserved || cfg->chunk_intervals > 64u ||
+      cfg->step_blocks_per_sm > 32u)
+    return fail(sys, PRX_EINVAL, "launch configuration out of range");
+  if (sys->d.force_precision == PRX_FORCE_FP64 && bt != 256u)
+    return fail(sys, PRX_EINVAL, "the FP64 force mode has fixed kernels");
+  CK(cudaStreamSynchronize(sys->stream));
+  sys->S.step_bt = (int)bt;
+  sys->S.step_bpsm = (int)cfg->step_blocks_per_sm;
+  sys->chunk_m = cfg->chunk_intervals ? cfg->chunk_intervals : 1u;
+  destroy_graphs(sys);
+  return PRX_OK;
+}
+
+int prx_get_launch_config(prx_system* sys, prx_launch_config* cfg) {
+  if (!sys || !cfg) return PRX_EINVAL;
+  cfg->step_threads = (uint32_t)sys->S.step_bt;
+  cfg->step_blocks_per_sm = (uint32_t)sys->S.step_bpsm;
+  cfg->chunk_intervals = sys->chunk_m;
+  cfg->reserved = 0u;
+  return PRX_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, prx_tune_choice> g_tune_cache;
+
+// The cache key: what the timing depends on.
+std::string tune_key(const prx_system_desc& d, const prx_reaction_desc* rx, uint32_t steps,
+                     const double* skins, uint32_t n_skins, const uint32_t* threads,
+                     const uint32_t* bpsm, uint32_t n_shapes, const uint32_t* chunks,
+                     uint32_t n_chunks) {
+  char buf[512];
+  const double V = d.box[0] * d.box[1] * d.box[2];
+  snprintf(buf, sizeof(buf), "n=%u rho=%.4f cap=%u fp64=%d gamma=%.3g rx=%d rr=%.4g theta=%u k=%.4g steps=%u|",
+           d.n, d.n / V, d.adj_cap, d.force_precision, d.gamma, rx ? 1 : 0, rx ? rx->r_react : 0.0,
+           rx ? rx->theta : 0u, rx ? rx->k : 0.0, steps);
+  std::string k(buf);
+  for (uint32_t q = 0; q < n_skins; ++q) k += std::to_string(skins[q]) + ",";
+  k += "|";
+  for (uint32_t q = 0; q < n_shapes; ++q) k += std::to_string(threads[q]) + "x" + std::to_string(bpsm[q]) + ",";
+  k += "|";
+  for (uint32_t q = 0; q < n_chunks; ++q) k += std::to_string(chunks[q]) + ",";
+  for (char& c : k)
+    if (c == '\t' || c == '\n') c = ' ';
+  return k;
+}
+
+bool tune_file_lookup(const char* path, const std::string& key, prx_tune_choice* out) {
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[2048];
+  bool found = false;
+  while (fgets(line, sizeof(line), f)) {
+    char* tab = strchr(line, '\t');
+    if (!tab) continue;
+    *tab = 0;
+    if (key != line) continue;
+    prx_tune_choice c{};
+    unsigned t = 0, b = 0, m = 0;
+    if (sscanf(tab + 1, "%lf %u %u %u %lf", &c.skin, &t, &b, &m, &c.ms_per_step) == 5) {
+      c.launch.step_threads = t;
+      c.launch.step_blocks_per_sm = b;
+      c.launch.chunk_intervals = m;
+      *out = c;
+      found = true;  // the last line for a key wins
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void tune_file_store(const char* path, const std::string& key, const prx_tune_choice& c) {
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s\t%.17g %u %u %u %.9g\n", key.c_str(), c.skin, c.launch.step_threads,
+          c.launch.step_blocks_per_sm, c.launch.chunk_intervals, c.ms_per_step);
+  fclose(f);
+}
+
+// Times one candidate on a temporary system: warm-up, then `steps` steps
+// rounded up to whole graph chunks; -1 when it cannot run.
+double time_candidate(const prx_system_desc* desc, const double* pos, const double* vel,
+                      const uint8_t* type, const int8_t* state, const prx_reaction_desc* rx,
+                      uint32_t steps, double skin, const prx_launch_config& lc) {
+  prx_system_desc d = *desc;
+  d.skin = skin;
+  prx_system* sys = nullptr;
+  if (prx_create(&d, pos, vel, type, state, nullptr, 0, nullptr, &sys) != PRX_OK) return -1.0;
+  bool ok = !rx || prx_set_reaction(sys, rx) == PRX_OK;
+  ok = ok && prx_set_launch_config(sys, &lc) == PRX_OK;
+  const uint64_t chunk = (uint64_t)(rx ? rx->theta : kNoRxChunk) * (lc.chunk_intervals ? lc.chunk_intervals : 1u);
+  const uint64_t n = (steps + chunk - 1) / chunk * chunk;
+  cudaEvent_t a = nullptr, b = nullptr;
+  float ms = 0.f;
+  ok = ok && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+  ok = ok && prx_run(sys, n / 4 / chunk * chunk + chunk) == PRX_OK && prx_sync(sys) == PRX_OK;
+  ok = ok && cudaEventRecord(a, sys->stream) == cudaSuccess;
+  ok = ok && prx_run(sys, n) == PRX_OK;
+  ok = ok && cudaEventRecord(b, sys->stream) == cudaSuccess;
+  ok = ok && prx_sync(sys) == PRX_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  prx_destroy(sys);
+  return ok ? (double)ms / (double)n : -1.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int prx_autotune(const prx_system_desc* desc, const double* pos, const double* vel,
+                 const uint8_t* type, const int8_t* state, const prx_reaction_desc* rx,
+                 uint32_t steps, const double* skins, uint32_t n_skins, const uint32_t* threads,
+                 const uint32_t* blocks_per_sm, uint32_t n_shapes, const uint32_t* chunks,
+                 uint32_t n_chunks, const char* cache_path, prx_tune_choice* best,
+                 prx_tune_choice* tried, uint32_t tried_cap, uint32_t* n_tried) {
+  if (n_tried) *n_tried = 0;
+  if (!desc || !best || steps == 0 || (n_skins && !skins) || (n_shapes && (!threads || !blocks_per_sm)) ||
+      (n_chunks && !chunks))
+    return PRX_EINVAL;
+  const std::string key = tune_key(*desc, rx, steps, skins, n_skins, threads, blocks_per_sm, n_shapes,
+                                   chunks, n_chunks);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    prx_tune_choice c{};
+    if (it != g_tune_cache.end()) {
+      c = it->second;
+    } else if (cache_path && tune_file_lookup(cache_path, key, &c)) {
+      g_tune_cache[key] = c;
+    } else {
+      c.ms_per_step = -2.0;
+    }
+    if (c.ms_per_step != -2.0) {
+      *best = c;
+      best->cached = 1u;
+      best->stage = 2u;
+      return PRX_OK;
+    }
+  }
+  uint32_t nt = 0;
+  auto record = [&](const prx_tune_choice& c) {
+    if (tried && nt < tried_cap) tried[nt] = c;
+    ++nt;
+  };
+  prx_tune_choice cur{};
+  cur.skin = desc->skin;
+  cur.launch.step_threads = 256u;
+  cur.launch.chunk_intervals = 1u;
+  cur.ms_per_step = -1.0;
+  auto stage = [&](uint32_t st, uint32_t count, auto apply) {
+    prx_tune_choice stage_best{};
+    stage_best.ms_per_step = -1.0;
+    for (uint32_t q = 0; q < count; ++q) {
+      prx_tune_choice c = cur;
+      apply(c, q);
+      c.stage = st;
+      c.cached = 0u;
+      c.ms_per_step = time_candidate(desc, pos, vel, type, state, rx, steps, c.skin, c.launch);
+      record(c);
+      if (c.ms_per_step >= 0.0 && (stage_best.ms_per_step < 0.0 || c.ms_per_step < stage_best.ms_per_step))
+        stage_best = c;
+    }
+    if (stage_best.ms_per_step >= 0.0) cur = stage_best;
+  };
+  stage(0u, n_skins, [&](prx_tune_choice& c, uint32_t q) { c.skin = skins[q]; });
+  stage(1u, n_shapes, [&](prx_tune_choice& c, uint32_t q) {
+    c.launch.step_threads = threads[q];
+    c.launch.step_blocks_per_sm = blocks_per_sm[q];
+  });
+  stage(2u, n_chunks, [&](prx_tune_choice& c, uint32_t q) { c.launch.chunk_intervals = chunks[q]; });
+  if (n_tried) *n_tried = nt;
+  if (cur.ms_per_step < 0.0) {
+    g_create_error = "no autotuner candidate could run";
+    return PRX_EINVAL;
+  }
+  *best = cur;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = cur;
+    if (cache_path) tune_file_store(cache_path, key, cur);
+  }
   return PRX_OK;
 }
 

@@ -86,6 +86,16 @@ class prx_batch_stats(C.Structure):
                 ("epochs", C.c_uint64)]
 
 
+class prx_launch_config(C.Structure):
+    _fields_ = [("step_threads", C.c_uint32), ("step_blocks_per_sm", C.c_uint32),
+                ("chunk_intervals", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class prx_tune_choice(C.Structure):
+    _fields_ = [("skin", C.c_double), ("launch", prx_launch_config), ("ms_per_step", C.c_double),
+                ("stage", C.c_uint32), ("cached", C.c_uint32)]
+
+
 class prx_class(C.Structure):
     _fields_ = [("type_mask", C.c_uint32), ("s_lo", C.c_int32), ("s_hi", C.c_int32)]
 
@@ -139,6 +149,12 @@ def lib():
         "prx_autotune_skin": ([P(prx_system_desc), VP, VP, VP, VP, P(prx_reaction_desc),
                                C.c_uint32, P(C.c_double), C.c_uint32, P(C.c_double),
                                P(C.c_double)], I),
+        "prx_set_launch_config": ([VP, P(prx_launch_config)], I),
+        "prx_get_launch_config": ([VP, P(prx_launch_config)], I),
+        "prx_autotune": ([P(prx_system_desc), VP, VP, VP, VP, P(prx_reaction_desc), C.c_uint32,
+                          P(C.c_double), C.c_uint32, P(C.c_uint32), P(C.c_uint32), C.c_uint32,
+                          P(C.c_uint32), C.c_uint32, C.c_char_p, P(prx_tune_choice),
+                          P(prx_tune_choice), C.c_uint32, P(C.c_uint32)], I),
         "prx_batch_create": ([C.c_uint32, U64, VP, P(VP)], I),
         "prx_batch_admit": ([VP, VP, U64, P(C.c_int32)], I),
         "prx_batch_step_epoch": ([VP, U64, P(U64)], I),
@@ -411,6 +427,54 @@ def prx_autotune_skin(desc: prx_system_desc, pos, vel, type_, state, rx=None, st
     return best.value, {float(skins[q]): ms[q] for q in range(len(skins))}
 
 
+def _choice(c: prx_tune_choice) -> dict:
+    return dict(skin=c.skin, step_threads=c.launch.step_threads,
+                step_blocks_per_sm=c.launch.step_blocks_per_sm,
+                chunk_intervals=c.launch.chunk_intervals, ms_per_step=c.ms_per_step,
+                stage=c.stage, cached=bool(c.cached))
+
+
+def prx_set_launch_config(h, step_threads=0, step_blocks_per_sm=0, chunk_intervals=0):
+    cfg = prx_launch_config(int(step_threads), int(step_blocks_per_sm), int(chunk_intervals), 0)
+    _check(lib().prx_set_launch_config(h, C.byref(cfg)), h)
+
+
+def prx_get_launch_config(h) -> dict:
+    cfg = prx_launch_config()
+    _check(lib().prx_get_launch_config(h, C.byref(cfg)), h)
+    return dict(step_threads=cfg.step_threads, step_blocks_per_sm=cfg.step_blocks_per_sm,
+                chunk_intervals=cfg.chunk_intervals)
+
+
+def prx_autotune(desc: prx_system_desc, pos, vel, type_, state, rx=None, steps: int = 100,
+                 skins=(0.3, 0.35, 0.4, 0.45, 0.5), shapes=((128, 0), (256, 0), (512, 0)),
+                 chunks=(1, 2, 4), cache_path=None):
+    """The library's autotuner (skin, step-kernel block shape as (threads,
+    blocks per SM), reaction intervals per graph replay).  Returns
+    (best, tried): dicts with skin, step_threads, step_blocks_per_sm,
+    chunk_intervals, ms_per_step, stage and cached."""
+    n = desc.n
+    pos = np.ascontiguousarray(pos, np.float64).reshape(n, 3)
+    vel = None if vel is None else np.ascontiguousarray(vel, np.float64).reshape(n, 3)
+    type_ = np.ascontiguousarray(type_, np.uint8)
+    state = np.ascontiguousarray(state, np.int8)
+    sk = (C.c_double * max(1, len(skins)))(*skins)
+    th = (C.c_uint32 * max(1, len(shapes)))(*[int(a) for a, _ in shapes])
+    bp = (C.c_uint32 * max(1, len(shapes)))(*[int(b) for _, b in shapes])
+    ch = (C.c_uint32 * max(1, len(chunks)))(*chunks)
+    cap = len(skins) + len(shapes) + len(chunks)
+    tried = (prx_tune_choice * max(1, cap))()
+    best = prx_tune_choice()
+    nt = C.c_uint32()
+    rc = lib().prx_autotune(C.byref(desc), _ptr(pos), _ptr(vel), _ptr(type_), _ptr(state),
+                            C.byref(rx) if rx is not None else None, int(steps), sk, len(skins),
+                            th, bp, len(shapes), ch, len(chunks),
+                            cache_path.encode() if cache_path else None, C.byref(best), tried,
+                            cap, C.byref(nt))
+    _check(rc, None)
+    return _choice(best), [_choice(tried[q]) for q in range(min(nt.value, cap))]
+
+
 def _bcheck(rc: int, b=None):
     if rc != PRX_OK:
         msg = lib().prx_batch_last_error(b)
@@ -589,6 +653,12 @@ class System:
 
     def set_reactions(self, rxs):
         prx_set_reactions(self.h, list(rxs))
+
+    def set_launch_config(self, step_threads=0, step_blocks_per_sm=0, chunk_intervals=0):
+        prx_set_launch_config(self.h, step_threads, step_blocks_per_sm, chunk_intervals)
+
+    def launch_config(self) -> dict:
+        return prx_get_launch_config(self.h)
 
     def run(self, nsteps):
         prx_run(self.h, nsteps)
