@@ -56,7 +56,8 @@ THETA = 10
 MD_STEPS = 20_000
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SKINS = (0.3, 0.35, 0.4, 0.45, 0.5)  # autotuner candidates: Verlet skin,
-SHAPES = ((128, 0), (256, 0), (512, 0), (256, 5), (256, 4))  # step-kernel (threads, blocks/SM),
+SHAPES = ((128, 0, 1), (256, 0, 1), (512, 0, 1), (256, 5, 1), (256, 0, 4), (512, 0, 4))
+# (step-kernel threads per block, blocks per SM, lanes per particle),
 CHUNKS = (1, 2, 5, 10)  # reaction intervals per graph replay
 
 
@@ -278,10 +279,21 @@ def small_config(P, torch, name: str, inp, sch: dict, cap: int, fp64: bool, md_s
     is flushed once before it), its step kernel's roofline over ten further
     intervals, and the oracle timed on the same start."""
     xw, vw = warmed_liquid(P, inp, cap, seed, fp64=fp64, stream=stream.cuda_stream)
-    desc = P.make_desc(inp.n, inp.L, adj_cap=cap, seed=seed, fp64=fp64)
+    rx = P.make_reaction(**sch)
+    if fp64:  # the FP64 force mode has fixed kernels: skin and interval batching only
+        tune, _ = P.prx_autotune(P.make_desc(inp.n, inp.L, adj_cap=cap, seed=seed, fp64=True), xw,
+                                 vw, inp.type, inp.state, rx, steps=200, skins=SKINS, shapes=(),
+                                 chunks=CHUNKS)
+    else:
+        tune, _ = P.prx_autotune(P.make_desc(inp.n, inp.L, adj_cap=cap, seed=seed), xw, vw,
+                                 inp.type, inp.state, rx, steps=200, skins=SKINS, shapes=SHAPES,
+                                 chunks=CHUNKS)
+    desc = P.make_desc(inp.n, inp.L, adj_cap=cap, seed=seed, fp64=fp64, skin=tune["skin"])
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=stream.device)
     with P.System(desc, xw, vw, inp.type, inp.state, stream=stream.cuda_stream) as g:
-        g.set_reaction(P.make_reaction(**sch))
+        g.set_reaction(rx)
+        g.set_launch_config(tune["step_threads"], tune["step_blocks_per_sm"],
+                            tune["chunk_intervals"], tune["step_lanes"])
         g.run(0)  # graphs captured before the timed region
         st0 = g.stats()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -300,6 +312,7 @@ def small_config(P, torch, name: str, inp, sch: dict, cap: int, fp64: bool, md_s
     line = {"workload": name, "metric": "particle-steps/s",
             "value": inp.n * md_steps / (ms * 1e-3), "unit": "particle-steps/s",
             "md_steps": md_steps, "ms": ms, "beads": inp.n, "k": sch["k"],
+            "autotune": {k: v for k, v in tune.items() if k not in ("stage", "cached")},
             "dtype": "f64" if fp64 else "f32 forces / f64 integration",
             "bonds_end": int(obs["bonds"]), "gpu_launches": int(st1["kernel_launches"]
                                                                - st0["kernel_launches"]),
@@ -607,7 +620,8 @@ def main():
     # the library's autotuner picks the Verlet skin for this workload (timed
     # on temporary copies of the warmed system, outside the timed region)
     if args.skin > 0:
-        tune = dict(skin=args.skin, step_threads=256, step_blocks_per_sm=0, chunk_intervals=1)
+        tune = dict(skin=args.skin, step_threads=256, step_blocks_per_sm=0, chunk_intervals=1,
+                    step_lanes=1)
         tried = []
     else:
         tune, tried = P.prx_autotune(
@@ -616,7 +630,8 @@ def main():
     skin = tune["skin"]
     desc = P.make_desc(inp.n, inp.L, adj_cap=FUNC, seed=seed, skin=skin)
     g = P.System(desc, xw, vw, inp.type, inp.state, stream=stream.cuda_stream)
-    g.set_launch_config(tune["step_threads"], tune["step_blocks_per_sm"], tune["chunk_intervals"])
+    g.set_launch_config(tune["step_threads"], tune["step_blocks_per_sm"], tune["chunk_intervals"],
+                        tune["step_lanes"])
     # untimed warm-up bench steps: MD on the warmed liquid; then the reaction
     # scheme is set and its graphs are captured, so the timed region is the
     # whole reaction run
@@ -677,7 +692,7 @@ def main():
         ge = P.System(desc, pin["x"], pin["v"], pin["t"], pin["s"], stream=stream.cuda_stream)
         ge.set_reaction(P.make_reaction(**sch))
         ge.set_launch_config(tune["step_threads"], tune["step_blocks_per_sm"],
-                             tune["chunk_intervals"])
+                             tune["chunk_intervals"], tune["step_lanes"])
         d2h = 0
         ke = max(args.steps, 1)  # the same number of steps as the device-timed region
         ob = None

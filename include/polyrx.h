@@ -353,21 +353,28 @@ int prx_autotune_skin(const prx_system_desc* desc, const double* pos, const doub
                       uint32_t steps, const double* skins, uint32_t n_skins, double* best_skin,
                       double* ms_per_step);
 
-/* Launch configuration of a system's kernels.  Every choice changes only the
- * speed: a run gives the same result, bit for bit, under any of them (one
- * thread computes each particle's forces and update whatever the block
- * shape, and a graph replay of m intervals launches the same kernels as m
- * replays of one). */
+/* Launch configuration of a system's kernels.  The block shape and the
+ * interval batching change only the speed: a run gives the same result, bit
+ * for bit, under any of them (one thread computes each particle's forces and
+ * update whatever the block shape, and a graph replay of m intervals
+ * launches the same kernels as m replays of one).  The lanes per particle
+ * change, like the skin, only the order of the FP32 force sums: with 4 a
+ * particle's list is split over four lanes whose partial sums are combined
+ * in a fixed order (more warps in flight for systems too small to fill the
+ * GPU). */
 typedef struct {
   uint32_t step_threads;       /* threads per block of the step kernel: 128, 256 or 512 (0: 256) */
   uint32_t step_blocks_per_sm; /* blocks per SM of its persistent grid (0: as many as fit) */
   uint32_t chunk_intervals;    /* reaction intervals per CUDA-graph replay in prx_run, 1..64
                                   (0: 1); without a scheme, chunks of 10 steps */
-  uint32_t reserved;           /* must be 0 */
+  uint32_t step_lanes;         /* lanes per particle of the FP32 step: 1 or 4 (0: 1) */
 } prx_launch_config;
 
 /* PRX_EINVAL for values out of range, a batch member, or a FP64-force
- * system with step_threads other than 0 or 256 (its kernels are fixed). */
+ * system with step_threads other than 0 or 256 or step_lanes other than
+ * 0 or 1 (its kernels are fixed).  A system with step_lanes 4 cannot join a
+ * batch (batched members run the one-lane kernel, so that each computes
+ * exactly what it computes alone). */
 int prx_set_launch_config(prx_system* sys, const prx_launch_config* cfg);
 int prx_get_launch_config(prx_system* sys, prx_launch_config* cfg);
 
@@ -383,8 +390,8 @@ typedef struct {
 /* The library's autotuner over the Verlet skin (cell size and rebuild
  * interval), the step kernel's block shape and the reaction-interval
  * batching, by coordinate search: every skin with the default launch, then
- * every (threads, blocks per SM) pair at the best skin, then every chunk
- * length at the best of those.  Each candidate is a temporary system built
+ * every (threads, blocks per SM, lanes per particle) shape at the best
+ * skin, then every chunk length at the best of those.  Each candidate is a temporary system built
  * from the inputs (as prx_autotune_skin), timed with CUDA events over
  * `steps` steps (rounded up to whole chunks) after a warm-up.  Empty lists
  * (count 0) keep the default of that dimension.  *best receives the fastest
@@ -398,9 +405,10 @@ typedef struct {
 int prx_autotune(const prx_system_desc* desc, const double* pos, const double* vel,
                  const uint8_t* type, const int8_t* state, const prx_reaction_desc* rx,
                  uint32_t steps, const double* skins, uint32_t n_skins, const uint32_t* threads,
-                 const uint32_t* blocks_per_sm, uint32_t n_shapes, const uint32_t* chunks,
-                 uint32_t n_chunks, const char* cache_path, prx_tune_choice* best,
-                 prx_tune_choice* tried, uint32_t tried_cap, uint32_t* n_tried);
+                 const uint32_t* blocks_per_sm, const uint32_t* lanes, uint32_t n_shapes,
+                 const uint32_t* chunks, uint32_t n_chunks, const char* cache_path,
+                 prx_tune_choice* best, prx_tune_choice* tried, uint32_t tried_cap,
+                 uint32_t* n_tried);
 
 /* ---- batched ensemble -------------------------------------------------------- */
 /* A batch advances many independent systems (replicas of different sizes,

@@ -67,6 +67,7 @@ __device__ __forceinline__ bool bond32(const Sys& S, uint32_t style, float dx, f
 }
 
 // FP64 versions, arithmetic written as in the plain definitions.
+template <bool ENERGY = true>
 __device__ __forceinline__ void wca64(const Sys& S, double dx, double dy, double dz, double r2,
                                       double& fx, double& fy, double& fz, double& e) {
   const double sr2 = __ddiv_rn(S.sig2, r2);
@@ -80,9 +81,11 @@ __device__ __forceinline__ void wca64(const Sys& S, double dx, double dy, double
   fx = __dsub_rn(fx, __dmul_rn(g, dx));
   fy = __dsub_rn(fy, __dmul_rn(g, dy));
   fz = __dsub_rn(fz, __dmul_rn(g, dz));
-  e = __dadd_rn(e, __dmul_rn(0.5, __dmul_rn(S.eps4, __dadd_rn(__dsub_rn(sr12, sr6), 0.25))));
+  if constexpr (ENERGY)
+    e = __dadd_rn(e, __dmul_rn(0.5, __dmul_rn(S.eps4, __dadd_rn(__dsub_rn(sr12, sr6), 0.25))));
 }
 
+template <bool ENERGY = true>
 __device__ __forceinline__ bool bond64(const Sys& S, uint32_t style, double dx, double dy,
                                        double dz, double& fx, double& fy, double& fz, double& e) {
   const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
@@ -91,7 +94,8 @@ __device__ __forceinline__ bool bond64(const Sys& S, uint32_t style, double dx, 
     if (!(r2 < S.fr02)) return false;
     const double q = __dsub_rn(1.0, __ddiv_rn(r2, S.fr02));
     g = __ddiv_rn(-S.fk, q);
-    e = __dadd_rn(e, __dmul_rn(0.5, __dmul_rn(__dmul_rn(__dmul_rn(-0.5, S.fk), S.fr02), log(q))));
+    if constexpr (ENERGY)
+      e = __dadd_rn(e, __dmul_rn(0.5, __dmul_rn(__dmul_rn(__dmul_rn(-0.5, S.fk), S.fr02), log(q))));
   } else {
     const double r = __dsqrt_rn(r2);
     if (!(r > S.rc && r < 2.0 * S.rc)) return true;
@@ -101,7 +105,8 @@ __device__ __forceinline__ bool bond64(const Sys& S, uint32_t style, double dx, 
     const double ss12 = __dmul_rn(ss6, ss6);
     const double dVdr = __ddiv_rn(__dmul_rn(S.eps24, __dsub_rn(__dmul_rn(2.0, ss12), ss6)), sd);
     g = __ddiv_rn(-dVdr, r);
-    e = __dadd_rn(e, __dmul_rn(0.5, __dmul_rn(S.eps4, __dadd_rn(__dsub_rn(ss12, ss6), 0.25))));
+    if constexpr (ENERGY)
+      e = __dadd_rn(e, __dmul_rn(0.5, __dmul_rn(S.eps4, __dadd_rn(__dsub_rn(ss12, ss6), 0.25))));
   }
   fx = __dsub_rn(fx, __dmul_rn(g, dx));
   fy = __dsub_rn(fy, __dmul_rn(g, dy));
@@ -360,6 +365,110 @@ __global__ void __launch_bounds__(BT, 1536 / BT)
   else run(S.s0);
   if constexpr (!FORCES_ONLY) step_epilogue(S, ph, step, cond, use_cond, &warps_left, gridDim.x);
 }
+// The same step with four lanes per slot, for systems too small to fill the
+// GPU with one thread per slot: a warp takes 8 consecutive slots; lane q of
+// a slot's group sums its list entries q, q + 4, ... and bonds q, q + 4, ...;
+// the four partial forces are combined by a fixed butterfly (the same order
+// every step), and lanes 0-7 then integrate the 8 slots as in the one-lane
+// kernel.  Four times as many warps per slot hide the dependent
+// list -> position gathers that a small grid leaves exposed.  The sum order
+// differs from the one-lane kernel's (FP32 rounding only).
+template <bool NL16, bool FORCES_ONLY, bool CUBIC, int BT>
+__global__ void __launch_bounds__(BT, 1536 / BT)
+    k_step_nl4(Sys S, cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ unsigned int warps_left;
+  if (threadIdx.x == 0) warps_left = blockDim.x >> 5;
+  __syncthreads();
+  Ctl* ctl = S.ctl;
+  const int ph = ctl->phase;
+  const unsigned long long step = ctl->step + 1ull;
+  const uint4* __restrict__ P = ph ? S.P1 : S.P0;
+  uint4* __restrict__ Pn = ph ? S.P0 : S.P1;
+  const uint32_t W = gridDim.x * (blockDim.x >> 5);
+  const int lane = threadIdx.x & 31, q = lane & 3;
+  auto run = [&](const SoA& B) {
+    for (uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c * 8u < S.n; c += W) {
+      const uint32_t i = c * 8u + (uint32_t)(lane >> 2);
+      float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+      uint32_t wref = 0u;
+      bool ok = true;
+      if (i < S.n) {
+        const int cnt = __ldg(S.nn + i);
+        const uint4 pi = __ldg(P + i);
+        wref = pi.w;
+        for (int k0 = q; k0 < cnt; k0 += 16) {
+          uint32_t rn[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) rn[u] = k0 + 4 * u < cnt ? nl_raw<NL16>(S, k0 + 4 * u, i) : i;
+          uint4 pj[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) pj[u] = __ldg(P + rn[u]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if constexpr (CUBIC) {
+              const float ux = __int2float_rn(pdiff(pj[u].x, pi.x));
+              const float uy = __int2float_rn(pdiff(pj[u].y, pi.y));
+              const float uz = __int2float_rn(pdiff(pj[u].z, pi.z));
+              const float r2u = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
+              if (r2u > 0.f && r2u < S.rc2u) wca32(S, ux, uy, uz, r2u * S.s2f, fx, fy, fz, e);
+            } else {
+              float dx, dy, dz;
+              disp(S, pj[u], pi, dx, dy, dz);
+              const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+              if (r2 > 0.f && r2 < S.rc2f) wca32(S, dx, dy, dz, r2, fx, fy, fz, e);
+            }
+          }
+        }
+        if constexpr (CUBIC) {
+          fx *= S.scale[0];
+          fy *= S.scale[0];
+          fz *= S.scale[0];
+        }
+        const uint32_t nb = __ldg(B.nadj + i);
+        for (uint32_t b = (uint32_t)q; b < nb; b += 4) {
+          const uint32_t ent = __ldg(B.adj + (size_t)i * S.cap + b);
+          const uint4 pj = __ldg(P + (ent & SLOT_MASK));
+          float dx, dy, dz;
+          disp(S, pj, pi, dx, dy, dz);
+          ok = bond32(S, ent >> 31, dx, dy, dz, fx, fy, fz, e) && ok;
+        }
+      }
+      if (!ok) set_status(ctl, PRX_EOVERSTRETCH);
+#pragma unroll
+      for (int o = 1; o < 4; o <<= 1) {
+        fx += __shfl_xor_sync(0xFFFFFFFFu, fx, o);
+        fy += __shfl_xor_sync(0xFFFFFFFFu, fy, o);
+        fz += __shfl_xor_sync(0xFFFFFFFFu, fz, o);
+        if constexpr (FORCES_ONLY) e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+      }
+      // lane g (< 8) takes slot c * 8 + g from the group's first lane
+      const int src = (lane & 7) * 4;
+      const float gx = __shfl_sync(0xFFFFFFFFu, fx, src);
+      const float gy = __shfl_sync(0xFFFFFFFFu, fy, src);
+      const float gz = __shfl_sync(0xFFFFFFFFu, fz, src);
+      const float ge = __shfl_sync(0xFFFFFFFFu, e, src);
+      const uint32_t gw = __shfl_sync(0xFFFFFFFFu, wref, src);
+      const uint32_t ii = c * 8u + (uint32_t)lane;
+      if (lane < 8 && ii < S.n) {
+        if constexpr (FORCES_ONLY) {
+          S.fout[3 * (size_t)ii + 0] = (double)gx;
+          S.fout[3 * (size_t)ii + 1] = (double)gy;
+          S.fout[3 * (size_t)ii + 2] = (double)gz;
+          S.eout[ii] = (double)ge;
+        } else {
+          const double xi = B.x[ii], yi = B.y[ii], zi = B.z[ii];
+          const double vx = B.vx[ii], vy = B.vy[ii], vz = B.vz[ii];
+          const uint32_t pid = __ldg(B.id + ii);
+          integrate32(S, ctl, B, Pn, ii, pid, gw, step, gx, gy, gz, xi, yi, zi, vx, vy, vz);
+        }
+      }
+    }
+  };
+  if (ctl->set) run(S.s1);
+  else run(S.s0);
+  if constexpr (!FORCES_ONLY) step_epilogue(S, ph, step, cond, use_cond, &warps_left, gridDim.x);
+}
+
 // Members of a batch may differ in list width and box shape: the batch step
 // runs one launch per (list width, cubic) variant present, each over the
 // blocks of its members, with the single-system kernel's register budget.
@@ -374,42 +483,61 @@ __global__ void __launch_bounds__(256, 5)
 
 // ---------------------------------------------------------------------------
 // FP64 force mode (small systems): conservative forces per slot from the
-// absolute positions over the same Verlet list, written to fout / eout; the
-// integration runs as a second kernel so that no thread reads a position
-// another thread updates.  Arithmetic in the order of the plain definitions.
+// absolute positions over the same Verlet list, written to fout (and, for
+// prx_compute_forces, the energies to eout); the integration runs as a second
+// kernel so that no thread reads a position another thread updates.
+// Arithmetic per pair in the order of the plain definitions.  FP64 issues
+// at about 1/64 of the FP32 rate on this part, so the few particles of an
+// FP64 system are spread over every SM: four lanes per slot (lane q takes
+// the list entries and bonds q, q + 4, ...), one warp per block, and the
+// four partial sums combined by a fixed butterfly (the same order every
+// step).
 // ---------------------------------------------------------------------------
-template <bool NL16>
-__global__ void __launch_bounds__(STEP_THREADS) k_forces64(Sys S) {
+constexpr int F64_LANES = 4;
+
+template <bool NL16, bool ENERGY>
+__global__ void __launch_bounds__(32) k_forces64(Sys S) {
   Ctl* ctl = S.ctl;
   const SoA B = ctl->set ? S.s1 : S.s0;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= S.n) return;
-  const double xi = B.x[i], yi = B.y[i], zi = B.z[i];
+  const int lane = threadIdx.x & 31, q = lane & (F64_LANES - 1);
+  const uint32_t i = blockIdx.x * (32 / F64_LANES) + (uint32_t)(lane / F64_LANES);
   double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0;
-  const int cnt = S.nn[i];
-  for (int k = 0; k < cnt; ++k) {
-    const uint32_t j = nl_get<NL16>(S, k, i);
-    const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
-    const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
-    const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-    if (r2 < S.rc2) wca64(S, ddx, ddy, ddz, r2, fx, fy, fz, e);
-  }
   bool ok = true;
-  const uint32_t nb = B.nadj[i];
-  for (uint32_t b = 0; b < nb; ++b) {
-    const uint32_t ent = B.adj[(size_t)i * S.cap + b];
-    const uint32_t j = ent & SLOT_MASK;
-    const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
-    const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
-    const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
-    ok = bond64(S, ent >> 31, ddx, ddy, ddz, fx, fy, fz, e) && ok;
+  if (i < S.n) {
+    const double xi = B.x[i], yi = B.y[i], zi = B.z[i];
+    const int cnt = S.nn[i];
+    for (int k = q; k < cnt; k += F64_LANES) {
+      const uint32_t j = nl_get<NL16>(S, k, i);
+      const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
+      const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
+      const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+      if (r2 < S.rc2) wca64<ENERGY>(S, ddx, ddy, ddz, r2, fx, fy, fz, e);
+    }
+    const uint32_t nb = B.nadj[i];
+    for (uint32_t b = (uint32_t)q; b < nb; b += F64_LANES) {
+      const uint32_t ent = B.adj[(size_t)i * S.cap + b];
+      const uint32_t j = ent & SLOT_MASK;
+      const double ddx = min_image(__dsub_rn(B.x[j], xi), S.L[0], S.halfL[0]);
+      const double ddy = min_image(__dsub_rn(B.y[j], yi), S.L[1], S.halfL[1]);
+      const double ddz = min_image(__dsub_rn(B.z[j], zi), S.L[2], S.halfL[2]);
+      ok = bond64<ENERGY>(S, ent >> 31, ddx, ddy, ddz, fx, fy, fz, e) && ok;
+    }
   }
   if (!ok) set_status(ctl, PRX_EOVERSTRETCH);
-  S.fout[3 * (size_t)i + 0] = fx;
-  S.fout[3 * (size_t)i + 1] = fy;
-  S.fout[3 * (size_t)i + 2] = fz;
-  S.eout[i] = e;
+#pragma unroll
+  for (int o = 1; o < F64_LANES; o <<= 1) {
+    fx = __dadd_rn(fx, __shfl_xor_sync(0xFFFFFFFFu, fx, o));
+    fy = __dadd_rn(fy, __shfl_xor_sync(0xFFFFFFFFu, fy, o));
+    fz = __dadd_rn(fz, __shfl_xor_sync(0xFFFFFFFFu, fz, o));
+    if constexpr (ENERGY) e = __dadd_rn(e, __shfl_xor_sync(0xFFFFFFFFu, e, o));
+  }
+  if (q == 0 && i < S.n) {
+    S.fout[3 * (size_t)i + 0] = fx;
+    S.fout[3 * (size_t)i + 1] = fy;
+    S.fout[3 * (size_t)i + 2] = fz;
+    if constexpr (ENERGY) S.eout[i] = e;
+  }
 }
 
 // FP64 integration in the oracle's order of operations:
@@ -1252,22 +1380,32 @@ unsigned resident_blocks(int variant, const void* kern, int threads) {
 void launch_step(const Sys& S, cudaStream_t st, int fp64, int forces_only,
                  cudaGraphConditionalHandle h, int use_cond) {
   if (fp64) {
-    const unsigned g = blocks_for(S.n, STEP_THREADS) > 0 ? blocks_for(S.n, STEP_THREADS) : 1;
-    if (S.nl16) k_forces64<true><<<g, STEP_THREADS, 0, st>>>(S);
-    else k_forces64<false><<<g, STEP_THREADS, 0, st>>>(S);
-    if (!forces_only) k_integrate64<<<g, STEP_THREADS, 0, st>>>(S, h, use_cond);
+    const unsigned gf = blocks_for(S.n, 32 / F64_LANES) > 0 ? blocks_for(S.n, 32 / F64_LANES) : 1;
+    if (forces_only) {
+      if (S.nl16) k_forces64<true, true><<<gf, 32, 0, st>>>(S);
+      else k_forces64<false, true><<<gf, 32, 0, st>>>(S);
+    } else {
+      if (S.nl16) k_forces64<true, false><<<gf, 32, 0, st>>>(S);
+      else k_forces64<false, false><<<gf, 32, 0, st>>>(S);
+      const unsigned gi = blocks_for(S.n, 32) > 0 ? blocks_for(S.n, 32) : 1;
+      k_integrate64<<<gi, 32, 0, st>>>(S, h, use_cond);
+    }
   } else {
     // forces-only launches keep 256 threads; the step takes the launch
-    // configuration's block size and blocks per SM
+    // configuration's block size and blocks per SM; both take its lanes per
+    // slot (so that prx_compute_forces sums as the step does)
     const int bt = forces_only ? 256 : S.step_bt;
     auto K = [&](auto nl16, auto fo, auto cub) {
       constexpr bool N16 = decltype(nl16)::value, FO = decltype(fo)::value, CU = decltype(cub)::value;
       constexpr int v = (N16 ? 4 : 0) + (FO ? 2 : 0) + (CU ? 1 : 0);
       auto go = [&](auto btc) {
         constexpr int BT = decltype(btc)::value;
-        auto* kern = k_step_nl<N16, FO, CU, BT>;
-        const unsigned g0 = blocks_for(S.n, BT) > 0 ? blocks_for(S.n, BT) : 1;
-        unsigned r = resident_blocks(v + 8 * (BT == 128 ? 1 : (BT == 512 ? 2 : 0)), (const void*)kern, BT);
+        const bool four = S.step_lanes == 4;
+        auto* kern = four ? k_step_nl4<N16, FO, CU, BT> : k_step_nl<N16, FO, CU, BT>;
+        const unsigned per = four ? BT / 4 : BT;  // slots per block
+        const unsigned g0 = blocks_for(S.n, per) > 0 ? blocks_for(S.n, per) : 1;
+        unsigned r = resident_blocks(v + 8 * (BT == 128 ? 1 : (BT == 512 ? 2 : 0)) + (four ? 32 : 0),
+                                     (const void*)kern, BT);
         if (!FO && S.step_bpsm > 0) {
           const unsigned want = (unsigned)S.step_bpsm * (unsigned)device_sms();
           r = want < r ? want : r;

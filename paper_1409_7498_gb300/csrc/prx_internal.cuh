@@ -204,6 +204,7 @@ struct Sys {
   // launch configuration of the single-system step kernel (host side)
   int step_bt;              // threads per block: 128, 256 or 512
   int step_bpsm;            // blocks per SM of the persistent grid (0: all that fit)
+  int step_lanes;           // lanes per slot: 1, or 4 (k_step_nl4, small systems)
   unsigned int n_members;   // members of the batch (last-member detection)
 };
 

@@ -599,6 +599,7 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
   S.hist_cap = kHistCap;
   S.step_bt = 256;
   S.step_bpsm = 0;
+  S.step_lanes = 1;
   S.bond_cap = std::max<unsigned long long>(1ull, ((unsigned long long)n * S.cap) / 2ull);
 
   if (stream) {
@@ -1707,13 +1708,15 @@ int prx_set_launch_config(prx_system* sys, const prx_launch_config* cfg) {
   if (!sys || !cfg) return PRX_EINVAL;
   if (sys->batch) return refuse_member(sys);
   const uint32_t bt = cfg->step_threads ? cfg->step_threads : 256u;
-  if ((bt != 128u && bt != 256u && bt != 512u) || cfg->reserved || cfg->chunk_intervals > 64u ||
-      cfg->step_blocks_per_sm > 32u)
+  const uint32_t lanes = cfg->step_lanes ? cfg->step_lanes : 1u;
+  if ((bt != 128u && bt != 256u && bt != 512u) || (lanes != 1u && lanes != 4u) ||
+      cfg->chunk_intervals > 64u || cfg->step_blocks_per_sm > 32u)
     return fail(sys, PRX_EINVAL, "launch configuration out of range");
-  if (sys->d.force_precision == PRX_FORCE_FP64 && bt != 256u)
+  if (sys->d.force_precision == PRX_FORCE_FP64 && (bt != 256u || lanes != 1u))
     return fail(sys, PRX_EINVAL, "the FP64 force mode has fixed kernels");
   CK(cudaStreamSynchronize(sys->stream));
   sys->S.step_bt = (int)bt;
+  sys->S.step_lanes = (int)lanes;
   sys->S.step_bpsm = (int)cfg->step_blocks_per_sm;
   sys->chunk_m = cfg->chunk_intervals ? cfg->chunk_intervals : 1u;
   destroy_graphs(sys);
@@ -1725,7 +1728,7 @@ int prx_get_launch_config(prx_system* sys, prx_launch_config* cfg) {
   cfg->step_threads = (uint32_t)sys->S.step_bt;
   cfg->step_blocks_per_sm = (uint32_t)sys->S.step_bpsm;
   cfg->chunk_intervals = sys->chunk_m;
-  cfg->reserved = 0u;
+  cfg->step_lanes = (uint32_t)sys->S.step_lanes;
   return PRX_OK;
 }
 
@@ -1739,8 +1742,8 @@ std::map<std::string, prx_tune_choice> g_tune_cache;
 // The cache key: what the timing depends on.
 std::string tune_key(const prx_system_desc& d, const prx_reaction_desc* rx, uint32_t steps,
                      const double* skins, uint32_t n_skins, const uint32_t* threads,
-                     const uint32_t* bpsm, uint32_t n_shapes, const uint32_t* chunks,
-                     uint32_t n_chunks) {
+                     const uint32_t* bpsm, const uint32_t* lanes, uint32_t n_shapes,
+                     const uint32_t* chunks, uint32_t n_chunks) {
   char buf[512];
   const double V = d.box[0] * d.box[1] * d.box[2];
   snprintf(buf, sizeof(buf), "n=%u rho=%.4f cap=%u fp64=%d gamma=%.3g rx=%d rr=%.4g theta=%u k=%.4g steps=%u|",
@@ -1749,7 +1752,8 @@ std::string tune_key(const prx_system_desc& d, const prx_reaction_desc* rx, uint
   std::string k(buf);
   for (uint32_t q = 0; q < n_skins; ++q) k += std::to_string(skins[q]) + ",";
   k += "|";
-  for (uint32_t q = 0; q < n_shapes; ++q) k += std::to_string(threads[q]) + "x" + std::to_string(bpsm[q]) + ",";
+  for (uint32_t q = 0; q < n_shapes; ++q)
+    k += std::to_string(threads[q]) + "x" + std::to_string(bpsm[q]) + "x" + std::to_string(lanes[q]) + ",";
   k += "|";
   for (uint32_t q = 0; q < n_chunks; ++q) k += std::to_string(chunks[q]) + ",";
   for (char& c : k)
@@ -1769,10 +1773,12 @@ bool tune_file_lookup(const char* path, const std::string& key, prx_tune_choice*
     if (key != line) continue;
     prx_tune_choice c{};
     unsigned t = 0, b = 0, m = 0;
-    if (sscanf(tab + 1, "%lf %u %u %u %lf", &c.skin, &t, &b, &m, &c.ms_per_step) == 5) {
+    unsigned l = 1;
+    if (sscanf(tab + 1, "%lf %u %u %u %u %lf", &c.skin, &t, &b, &m, &l, &c.ms_per_step) == 6) {
       c.launch.step_threads = t;
       c.launch.step_blocks_per_sm = b;
       c.launch.chunk_intervals = m;
+      c.launch.step_lanes = l;
       *out = c;
       found = true;  // the last line for a key wins
     }
@@ -1784,8 +1790,8 @@ bool tune_file_lookup(const char* path, const std::string& key, prx_tune_choice*
 void tune_file_store(const char* path, const std::string& key, const prx_tune_choice& c) {
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s\t%.17g %u %u %u %.9g\n", key.c_str(), c.skin, c.launch.step_threads,
-          c.launch.step_blocks_per_sm, c.launch.chunk_intervals, c.ms_per_step);
+  fprintf(f, "%s\t%.17g %u %u %u %u %.9g\n", key.c_str(), c.skin, c.launch.step_threads,
+          c.launch.step_blocks_per_sm, c.launch.chunk_intervals, c.launch.step_lanes, c.ms_per_step);
   fclose(f);
 }
 
@@ -1823,15 +1829,16 @@ extern "C" {
 int prx_autotune(const prx_system_desc* desc, const double* pos, const double* vel,
                  const uint8_t* type, const int8_t* state, const prx_reaction_desc* rx,
                  uint32_t steps, const double* skins, uint32_t n_skins, const uint32_t* threads,
-                 const uint32_t* blocks_per_sm, uint32_t n_shapes, const uint32_t* chunks,
-                 uint32_t n_chunks, const char* cache_path, prx_tune_choice* best,
-                 prx_tune_choice* tried, uint32_t tried_cap, uint32_t* n_tried) {
+                 const uint32_t* blocks_per_sm, const uint32_t* lanes, uint32_t n_shapes,
+                 const uint32_t* chunks, uint32_t n_chunks, const char* cache_path,
+                 prx_tune_choice* best, prx_tune_choice* tried, uint32_t tried_cap,
+                 uint32_t* n_tried) {
   if (n_tried) *n_tried = 0;
-  if (!desc || !best || steps == 0 || (n_skins && !skins) || (n_shapes && (!threads || !blocks_per_sm)) ||
-      (n_chunks && !chunks))
+  if (!desc || !best || steps == 0 || (n_skins && !skins) ||
+      (n_shapes && (!threads || !blocks_per_sm || !lanes)) || (n_chunks && !chunks))
     return PRX_EINVAL;
-  const std::string key = tune_key(*desc, rx, steps, skins, n_skins, threads, blocks_per_sm, n_shapes,
-                                   chunks, n_chunks);
+  const std::string key = tune_key(*desc, rx, steps, skins, n_skins, threads, blocks_per_sm, lanes,
+                                   n_shapes, chunks, n_chunks);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -1859,6 +1866,7 @@ int prx_autotune(const prx_system_desc* desc, const double* pos, const double* v
   cur.skin = desc->skin;
   cur.launch.step_threads = 256u;
   cur.launch.chunk_intervals = 1u;
+  cur.launch.step_lanes = 1u;
   cur.ms_per_step = -1.0;
   auto stage = [&](uint32_t st, uint32_t count, auto apply) {
     prx_tune_choice stage_best{};
@@ -1879,6 +1887,7 @@ int prx_autotune(const prx_system_desc* desc, const double* pos, const double* v
   stage(1u, n_shapes, [&](prx_tune_choice& c, uint32_t q) {
     c.launch.step_threads = threads[q];
     c.launch.step_blocks_per_sm = blocks_per_sm[q];
+    c.launch.step_lanes = lanes[q];
   });
   stage(2u, n_chunks, [&](prx_tune_choice& c, uint32_t q) { c.launch.chunk_intervals = chunks[q]; });
   if (n_tried) *n_tried = nt;
@@ -1966,6 +1975,8 @@ int check_member(prx_batch* b, prx_system* sys) {
   if (sys->d.force_precision != PRX_FORCE_FP32)
     return bfail(b, PRX_EINVAL, "batches run PRX_FORCE_FP32 systems only");
   if (sys->profiling) return bfail(b, PRX_EINVAL, "system is being profiled");
+  if (sys->S.step_lanes != 1)
+    return bfail(b, PRX_EINVAL, "batch members run the one-lane step kernel (step_lanes 1)");
   if (sys->has_rx) {
     const uint64_t th = sys->rxd.theta;
     if (b->theta && th != b->theta)

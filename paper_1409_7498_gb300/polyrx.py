@@ -88,7 +88,7 @@ class prx_batch_stats(C.Structure):
 
 class prx_launch_config(C.Structure):
     _fields_ = [("step_threads", C.c_uint32), ("step_blocks_per_sm", C.c_uint32),
-                ("chunk_intervals", C.c_uint32), ("reserved", C.c_uint32)]
+                ("chunk_intervals", C.c_uint32), ("step_lanes", C.c_uint32)]
 
 
 class prx_tune_choice(C.Structure):
@@ -152,8 +152,9 @@ def lib():
         "prx_set_launch_config": ([VP, P(prx_launch_config)], I),
         "prx_get_launch_config": ([VP, P(prx_launch_config)], I),
         "prx_autotune": ([P(prx_system_desc), VP, VP, VP, VP, P(prx_reaction_desc), C.c_uint32,
-                          P(C.c_double), C.c_uint32, P(C.c_uint32), P(C.c_uint32), C.c_uint32,
-                          P(C.c_uint32), C.c_uint32, C.c_char_p, P(prx_tune_choice),
+                          P(C.c_double), C.c_uint32, P(C.c_uint32), P(C.c_uint32),
+                          P(C.c_uint32), C.c_uint32, P(C.c_uint32), C.c_uint32, C.c_char_p,
+                          P(prx_tune_choice),
                           P(prx_tune_choice), C.c_uint32, P(C.c_uint32)], I),
         "prx_batch_create": ([C.c_uint32, U64, VP, P(VP)], I),
         "prx_batch_admit": ([VP, VP, U64, P(C.c_int32)], I),
@@ -430,12 +431,14 @@ def prx_autotune_skin(desc: prx_system_desc, pos, vel, type_, state, rx=None, st
 def _choice(c: prx_tune_choice) -> dict:
     return dict(skin=c.skin, step_threads=c.launch.step_threads,
                 step_blocks_per_sm=c.launch.step_blocks_per_sm,
-                chunk_intervals=c.launch.chunk_intervals, ms_per_step=c.ms_per_step,
-                stage=c.stage, cached=bool(c.cached))
+                chunk_intervals=c.launch.chunk_intervals, step_lanes=c.launch.step_lanes,
+                ms_per_step=c.ms_per_step, stage=c.stage, cached=bool(c.cached))
 
 
-def prx_set_launch_config(h, step_threads=0, step_blocks_per_sm=0, chunk_intervals=0):
-    cfg = prx_launch_config(int(step_threads), int(step_blocks_per_sm), int(chunk_intervals), 0)
+def prx_set_launch_config(h, step_threads=0, step_blocks_per_sm=0, chunk_intervals=0,
+                          step_lanes=0):
+    cfg = prx_launch_config(int(step_threads), int(step_blocks_per_sm), int(chunk_intervals),
+                            int(step_lanes))
     _check(lib().prx_set_launch_config(h, C.byref(cfg)), h)
 
 
@@ -443,24 +446,26 @@ def prx_get_launch_config(h) -> dict:
     cfg = prx_launch_config()
     _check(lib().prx_get_launch_config(h, C.byref(cfg)), h)
     return dict(step_threads=cfg.step_threads, step_blocks_per_sm=cfg.step_blocks_per_sm,
-                chunk_intervals=cfg.chunk_intervals)
+                chunk_intervals=cfg.chunk_intervals, step_lanes=cfg.step_lanes)
 
 
 def prx_autotune(desc: prx_system_desc, pos, vel, type_, state, rx=None, steps: int = 100,
                  skins=(0.3, 0.35, 0.4, 0.45, 0.5), shapes=((128, 0), (256, 0), (512, 0)),
                  chunks=(1, 2, 4), cache_path=None):
-    """The library's autotuner (skin, step-kernel block shape as (threads,
-    blocks per SM), reaction intervals per graph replay).  Returns
-    (best, tried): dicts with skin, step_threads, step_blocks_per_sm,
-    chunk_intervals, ms_per_step, stage and cached."""
+    """The library's autotuner (skin, step-kernel shape as (threads, blocks
+    per SM[, lanes per particle]), reaction intervals per graph replay).
+    Returns (best, tried): dicts with skin, step_threads, step_blocks_per_sm,
+    step_lanes, chunk_intervals, ms_per_step, stage and cached."""
+    shapes = [tuple(sh) + (1,) * (3 - len(sh)) for sh in shapes]
     n = desc.n
     pos = np.ascontiguousarray(pos, np.float64).reshape(n, 3)
     vel = None if vel is None else np.ascontiguousarray(vel, np.float64).reshape(n, 3)
     type_ = np.ascontiguousarray(type_, np.uint8)
     state = np.ascontiguousarray(state, np.int8)
     sk = (C.c_double * max(1, len(skins)))(*skins)
-    th = (C.c_uint32 * max(1, len(shapes)))(*[int(a) for a, _ in shapes])
-    bp = (C.c_uint32 * max(1, len(shapes)))(*[int(b) for _, b in shapes])
+    th = (C.c_uint32 * max(1, len(shapes)))(*[int(a) for a, _, _ in shapes])
+    bp = (C.c_uint32 * max(1, len(shapes)))(*[int(b) for _, b, _ in shapes])
+    ln = (C.c_uint32 * max(1, len(shapes)))(*[int(c) for _, _, c in shapes])
     ch = (C.c_uint32 * max(1, len(chunks)))(*chunks)
     cap = len(skins) + len(shapes) + len(chunks)
     tried = (prx_tune_choice * max(1, cap))()
@@ -468,7 +473,7 @@ def prx_autotune(desc: prx_system_desc, pos, vel, type_, state, rx=None, steps: 
     nt = C.c_uint32()
     rc = lib().prx_autotune(C.byref(desc), _ptr(pos), _ptr(vel), _ptr(type_), _ptr(state),
                             C.byref(rx) if rx is not None else None, int(steps), sk, len(skins),
-                            th, bp, len(shapes), ch, len(chunks),
+                            th, bp, ln, len(shapes), ch, len(chunks),
                             cache_path.encode() if cache_path else None, C.byref(best), tried,
                             cap, C.byref(nt))
     _check(rc, None)
@@ -654,8 +659,10 @@ class System:
     def set_reactions(self, rxs):
         prx_set_reactions(self.h, list(rxs))
 
-    def set_launch_config(self, step_threads=0, step_blocks_per_sm=0, chunk_intervals=0):
-        prx_set_launch_config(self.h, step_threads, step_blocks_per_sm, chunk_intervals)
+    def set_launch_config(self, step_threads=0, step_blocks_per_sm=0, chunk_intervals=0,
+                          step_lanes=0):
+        prx_set_launch_config(self.h, step_threads, step_blocks_per_sm, chunk_intervals,
+                              step_lanes)
 
     def launch_config(self) -> dict:
         return prx_get_launch_config(self.h)

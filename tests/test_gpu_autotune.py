@@ -89,3 +89,38 @@ def test_autotune_picks_the_fastest_of_each_stage_and_caches(tmp_path):
         (best["skin"], best["step_threads"], best["chunk_intervals"])
     lines = open(cache).read().strip().splitlines()
     assert len(lines) == 1 and "\t" in lines[0]
+
+
+def test_four_lanes_per_particle_forces_and_run():
+    """The four-lane step kernel: forces within the FP32 tolerance of the
+    oracle (prx_compute_forces takes the configured lanes), a short run that
+    stays close to the one-lane kernel's, and batches refuse such systems."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import numpy as np
+    import oracle as orc
+    from helpers import force_errors, md_params, oracle_system
+    P = gpu()
+    inp = synth.step_growth_sites(20000, 4, 13)
+    o = oracle_system(inp.x, inp.v, inp.type, inp.state, 4)
+    f_ref, e_ref = orc.forces(o, md_params(inp.L, 13), use_cells=True)
+    runs = []
+    for lanes in (1, 4):
+        desc = P.make_desc(inp.n, inp.L, adj_cap=4, seed=13)
+        with P.System(desc, inp.x, inp.v, inp.type, inp.state) as g:
+            g.set_launch_config(step_lanes=lanes)
+            assert g.launch_config()["step_lanes"] == lanes
+            f, e = g.forces()
+            err = force_errors(f, f_ref)
+            assert err["max_over_rms"] < 1e-5 and err["rms_rel"] < 1e-5, (lanes, err)
+            assert abs(e - e_ref) / abs(e_ref) < 1e-5
+            g.set_reaction(gpu_reaction(P, synth.step_growth_scheme(4, k=1.0)))
+            g.run(40)
+            runs.append(g.positions())
+            if lanes == 4:
+                with P.Batch() as b, pytest.raises(P.PolyrxError):
+                    b.add(g)
+    d = runs[0] - runs[1]
+    d -= inp.L * np.round(d / inp.L)
+    assert np.abs(d).max() < 1e-3  # FP32 sums in another order, 40 steps apart
