@@ -698,13 +698,14 @@ def main():
         ob = None
         for q in range(ke):
             ge.run(THETA)
-            # the step's result (populations, bonds, energy) copied into a
-            # pinned slot; the previous step's is read while this one runs
-            ge.observables_begin(q % 2)
+            # the step's result (the reaction record: populations per (type,
+            # state), bonds, step) copied into a pinned slot; the previous
+            # step's is read while this one runs
+            ge.history_begin(q % 2)
             if q:
-                ob = ge.observables_end((q - 1) % 2)
-            d2h += 8 * (2 + 8 * 16 + 4)
-        ob = ge.observables_end((ke - 1) % 2)
+                ob = ge.history_end((q - 1) % 2)
+            d2h += P.HISTORY_DTYPE.itemsize + 112  # the record and the 112-byte control block
+        ob = ge.history_end((ke - 1) % 2)
         stt = ge.states()
         bd = ge.bonds()
         d2h += stt.nbytes + bd.nbytes
@@ -713,8 +714,9 @@ def main():
         e2e = {"value": inp.n * THETA * ke / e_el, "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(h2d / ke), "d2h_bytes_per_step": int(d2h / ke),
                "steps": ke, "includes": "create from the warmed host state (upload + binning), "
-                                        "runs, per-step observables read-back (pipelined, one "
-                                        "step behind), final states and bonds, destroy"}
+                                        "runs, per-step read-back of the reaction record "
+                                        "(populations, bonds; pipelined, one step behind), "
+                                        "final states and bonds, destroy"}
         del ob
     g.close()
 

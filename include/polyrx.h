@@ -248,6 +248,20 @@ int prx_get_observables(prx_system* sys, prx_observables* out);
 #define PRX_OBS_SLOTS 4
 int prx_observables_begin(prx_system* sys, int slot);
 int prx_observables_end(prx_system* sys, int slot, prx_observables* out);
+/* Pipelined read of the newest reaction record (the populations per
+ * (type, state) of Secs. V-VI and the bond count after the latest reaction
+ * step, with its step): the reaction step itself leaves it at a fixed place,
+ * so prx_history_begin launches no kernel; it enqueues the copy into pinned
+ * host slot `slot` (0..PRX_OBS_SLOTS-1, shared with the observables calls)
+ * on the system's stream and returns at once; prx_history_end waits for
+ * that slot and fills *out (all zero before the first reaction step).
+ * States change only at reaction steps, so after a run of whole reaction
+ * intervals this is the run's current population record.  Not allowed for
+ * batch members.  PRX_EINVAL for a slot out of range or busy / not
+ * pending; a device error status is reported by the end call. */
+int prx_history_begin(prx_system* sys, int slot);
+int prx_history_end(prx_system* sys, int slot, prx_history_record* out);
+
 /* The last min(cap, recorded) per-reaction records, oldest first.  The
  * device keeps the most recent `history_cap` records (default 8192). */
 int prx_get_history(prx_system* sys, prx_history_record* out, uint64_t cap, uint64_t* n_out);

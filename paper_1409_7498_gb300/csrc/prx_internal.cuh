@@ -88,6 +88,7 @@ struct Ctl {
 };
 
 constexpr int MAX_RX = PRX_MAX_REACTIONS;
+constexpr int POP_REPLICAS = 32;
 
 // The scheme's reactions.  The scalar fields describe reaction 0 and serve
 // the single-reaction kernels as before; with nr > 1 (concurrent reactions)
@@ -191,6 +192,8 @@ struct Sys {
   unsigned long long bond_cap;
   HistRec* hist;
   unsigned int hist_cap;
+  int32_t* pop;             // particles per (type, state), kept current by the reaction
+                            // step: POP_REPLICAS arrays of 128 whose sum is the count
   double *fout, *eout;
   double* red;              // per-block partial sums (observables)
   Ctl* ctl;
@@ -356,6 +359,8 @@ void launch_rebin(const Sys& S, cudaStream_t st, int mode, void (*hook)(void*, c
 void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
                void (*hook)(void*, const char*, int), void* hook_ctx);
 void launch_observables(const Sys& S, cudaStream_t st, int nblocks);
+// Counts the populations per (type, state) into S.pop (creation).
+void launch_pop_init(const Sys& S, cudaStream_t st);
 void launch_pair_hist(const Sys& S, cudaStream_t st, const PairClass& a, const PairClass& b,
                       const double* e2, int nbins, unsigned long long* counts,
                       unsigned long long* nab);

@@ -627,7 +627,8 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
   }
   A.add(&S.P0, n), A.add(&S.P1, n), A.add(&S.key, n), A.add(&S.tmp, n), A.add(&S.new_of_old, n);
   A.add(&S.win, n), A.add(&S.wch, n), A.add(&S.bonds, (size_t)S.bond_cap);
-  A.add(&S.hist, (size_t)S.hist_cap + 1), A.add(&S.ctl, 1);
+  A.add(&S.hist, (size_t)S.hist_cap + 2), A.add(&S.ctl, 1);
+  A.add(&S.pop, (size_t)POP_REPLICAS * PRX_MAX_TYPES * PRX_MAX_STATES);
   A.add(&S.red, 4 * ((size_t)(n + RX_THREADS - 1) / RX_THREADS + 1));
   A.add(&S.fout, 3 * (size_t)n), A.add(&S.eout, (size_t)n);
   if ((rc = A.commit(sys, sys->dev_allocs))) return bail(rc);
@@ -762,7 +763,7 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
   c0.step = step0;
   if ((rc = up(S.ctl, &c0, sizeof(Ctl)))) return bail(rc);
   sys->host_step = step0;
-  if (cudaMemsetAsync(S.hist, 0, sizeof(HistRec) * (S.hist_cap + 1), sys->stream) != cudaSuccess)
+  if (cudaMemsetAsync(S.hist, 0, sizeof(HistRec) * (S.hist_cap + 2), sys->stream) != cudaSuccess)
     return bail(fail(sys, PRX_ECUDA, "memset failed"));
 
   if (slot_cells) {
@@ -775,6 +776,7 @@ int create_impl(const prx_system_desc* desc, const double* pos, const double* ve
   }
   // bin into set 1 (full keys from positions, or the restored cells)
   if ((rc = full_rebin(sys, slot_cells ? 2 : 1))) return bail(rc);
+  launch_pop_init(S, sys->stream);  // the running populations of the reaction records
   if ((rc = sync_status(sys))) return bail(rc);
   if (slot_cells && slot_w && slot_nn && slot_nl) {
     // a checkpoint also restores the displacement references and the exact
@@ -979,8 +981,8 @@ uint64_t estimate_bytes(const prx_system_desc& d, double r_react) {
   const uint64_t nblk = std::max<uint64_t>(n / RX_THREADS + 1, ncell / SCAN_TILE + 1) + 1;
   const uint64_t allocs = 40;  // separate cudaMalloc calls, each rounded up
   return 2 * per_set + n * (2 * 16 + 4 * 4) + (n * cap / 2 + 1) * sizeof(prx_bond) +
-           (kHistCap + 1ull) * sizeof(prx_history_record) + sizeof(Ctl) + 32 * (n / RX_THREADS + 2) +
-           32 * n + ncell * 12 + 8 * nblk + list_cap * n * nl_bytes + 2 * n + allocs * 4096;
+           (kHistCap + 2ull) * sizeof(prx_history_record) + sizeof(Ctl) + 32 * (n / RX_THREADS + 2) +
+           32 * n + ncell * 12 + 8 * nblk + list_cap * n * nl_bytes + 2 * n + 16384 + allocs * 4096;
 }
 
 
@@ -1365,6 +1367,40 @@ int prx_observables_end(prx_system* sys, int slot, prx_observables* out) {
   sys->obs_pending[slot] = false;
   CK(cudaEventSynchronize(sys->obs_ev[slot]));
   return fill_observables(sys, slot, out);
+}
+
+int prx_history_begin(prx_system* sys, int slot) {
+  if (!sys) return PRX_EINVAL;
+  if (sys->batch) return refuse_member(sys);
+  if (slot < 0 || slot >= PRX_OBS_SLOTS) return fail(sys, PRX_EINVAL, "slot out of range");
+  if (sys->obs_pending[slot]) return fail(sys, PRX_EINVAL, "slot still pending");
+  if (!sys->obs_ev[slot] && cudaEventCreateWithFlags(&sys->obs_ev[slot], cudaEventDisableTiming) != cudaSuccess)
+    return fail(sys, PRX_ECUDA, "event creation failed");
+  auto* oh = sys->obs_host + slot;
+  if (sys->S.n) {
+    CK(cudaMemcpyAsync(&oh->rec, &sys->S.hist[sys->S.hist_cap + 1], sizeof(HistRec), cudaMemcpyDeviceToHost,
+                       sys->stream));
+  } else {
+    memset(&oh->rec, 0, sizeof(HistRec));
+  }
+  CK(cudaMemcpyAsync(&oh->ctl, sys->S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, sys->stream));
+  CK(cudaEventRecord(sys->obs_ev[slot], sys->stream));
+  sys->obs_pending[slot] = true;
+  return PRX_OK;
+}
+
+int prx_history_end(prx_system* sys, int slot, prx_history_record* out) {
+  if (!sys || !out) return PRX_EINVAL;
+  if (slot < 0 || slot >= PRX_OBS_SLOTS || !sys->obs_pending[slot])
+    return fail(sys, PRX_EINVAL, "nothing pending in this slot");
+  sys->obs_pending[slot] = false;
+  CK(cudaEventSynchronize(sys->obs_ev[slot]));
+  const auto* oh = sys->obs_host + slot;
+  memcpy(out, &oh->rec, sizeof(*out));
+  *sys->ctl_host = oh->ctl;
+  const int st = oh->ctl.status;
+  if (st) return fail(sys, st, std::string("device reported ") + prx_status_string(st));
+  return PRX_OK;
 }
 
 int prx_get_history(prx_system* sys, prx_history_record* out, uint64_t cap, uint64_t* n_out) {

@@ -13,10 +13,10 @@
 //   rx_select_T  steps 6-7: each A winner scans the cells around its T for the
 //                other A's that picked the same T and keeps the pair only if
 //                its key Philox(step, id_T, id_A) is the smallest: one A per T.
-//   rx_scan      offsets of the surviving pairs in the bond list (block
-//                counts scanned in one block: ordered by slot, no atomics).
-//   rx_apply     step 9: append the bonds, both adjacency rows, shift states.
-//   obs_hist     populations per (type, state) into the history ring.
+//   rx_select_apply  steps 6-9 fused: one A per T, then the bonds, both
+//                adjacency rows and the states; the running populations per
+//                (type, state) move with each bond, and the last block writes
+//                the reaction's history record from them.
 #include <cuda_runtime.h>
 
 #include "prx_internal.cuh"
@@ -27,6 +27,14 @@ namespace {
 
 __device__ __forceinline__ bool in_window(uint32_t mask, int lo, int hi, uint32_t t, int s) {
   return ((mask >> t) & 1u) && s >= lo && s <= hi;
+}
+
+// One particle of type t moves from state s0 to s1 in the block's
+// population changes (states outside 0..15 are not counted).
+__device__ __forceinline__ void pop_move(int32_t* dpop, uint32_t t, int s0, int s1) {
+  if (t >= PRX_MAX_TYPES) return;
+  if (s0 >= 0 && s0 < PRX_MAX_STATES) atomicSub(&dpop[t * PRX_MAX_STATES + s0], 1);
+  if (s1 >= 0 && s1 < PRX_MAX_STATES) atomicAdd(&dpop[t * PRX_MAX_STATES + s1], 1);
 }
 
 __device__ __forceinline__ unsigned long long key64(uint4 w) {
@@ -70,10 +78,6 @@ __device__ __forceinline__ void rx_compact_body(const Sys& S, const Blk blk) {
   const RxParams& R = S.R;
 
   Ctl* ctl = S.ctl;
-  if (blk.b == 0) {  // clear the history record this reaction will fill
-    int32_t* cnt = &S.hist[ctl->hist_count % S.hist_cap].counts[0][0];
-    for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x) cnt[k] = 0;
-  }
   const SoA B = ctl->set ? S.s1 : S.s0;
   const uint32_t i = blk.b * blockDim.x + threadIdx.x;
   bool el = false;
@@ -423,6 +427,10 @@ __device__ __forceinline__ void rx_select_apply_body(const Sys& S, const Blk blk
   const uint32_t nact = ctl->n_active;
   const int lane = threadIdx.x & 31;
   long long nwin = 0, nfin = 0;
+  // population changes of this block's bonds, per (type, state)
+  __shared__ int32_t dpop[PRX_MAX_TYPES * PRX_MAX_STATES];
+  for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x) dpop[k] = 0;
+  __syncthreads();
   // block-strided over the eligible A's, warp-uniform trip count
   for (uint32_t base = blk.b * blockDim.x; base < nact; base += blk.nb * blockDim.x) {
     const uint32_t w = base + threadIdx.x;
@@ -467,8 +475,13 @@ __device__ __forceinline__ void rx_select_apply_body(const Sys& S, const Blk blk
     B.nadj[i] = (uint8_t)(na + 1);
     B.adj[(size_t)T * S.cap + nt] = i | sbit;
     B.nadj[T] = (uint8_t)(nt + 1);
-    B.state[i] = (int8_t)(B.state[i] + (R.nr > 1 ? R.dAr[ch] : R.dA));
-    B.state[T] = (int8_t)(B.state[T] + (R.nr > 1 ? R.dTr[ch] : R.dT));
+    const int sa = B.state[i], stt = B.state[T];
+    const int sa1 = (int8_t)(sa + (R.nr > 1 ? R.dAr[ch] : R.dA));
+    const int st1 = (int8_t)(stt + (R.nr > 1 ? R.dTr[ch] : R.dT));
+    B.state[i] = (int8_t)sa1;
+    B.state[T] = (int8_t)st1;
+    pop_move(dpop, B.type[i], sa, sa1);
+    pop_move(dpop, B.type[T], stt, st1);
     BondRec rec;
     rec.a = B.id[i];
     rec.t = B.id[T];
@@ -488,6 +501,39 @@ __device__ __forceinline__ void rx_select_apply_body(const Sys& S, const Blk blk
     }
     if (cf) atomicAdd((unsigned long long*)&ctl->trace[3], (unsigned long long)cf);
   }
+  // the block's population changes into its replica of the running counts
+  // (POP_REPLICAS copies, so that blocks do not all meet on the same few
+  // counters); the last block sums the replicas into the reaction record
+  // (populations, bonds, step)
+  __syncthreads();
+  int32_t* rep = S.pop + (size_t)(blk.b % POP_REPLICAS) * (PRX_MAX_TYPES * PRX_MAX_STATES);
+  for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x)
+    if (dpop[k]) atomicAdd(rep + k, dpop[k]);
+  __threadfence();
+  __shared__ bool is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(&ctl->done_rx, 1u) == blk.nb - 1;
+  __syncthreads();
+  if (is_last) {
+    const unsigned long long slot = ctl->hist_count % S.hist_cap;
+    HistRec* rec = &S.hist[slot];
+    HistRec* latest = &S.hist[S.hist_cap + 1];
+    for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x) {
+      int32_t c = 0;
+      for (int r = 0; r < POP_REPLICAS; ++r) c += __ldcg(S.pop + r * (PRX_MAX_TYPES * PRX_MAX_STATES) + k);
+      (&rec->counts[0][0])[k] = c;
+      (&latest->counts[0][0])[k] = c;
+    }
+    if (threadIdx.x == 0) {
+      ctl->done_rx = 0u;
+      const long long st = step_arg >= 0 ? step_arg : (long long)ctl->step;
+      const long long nb = (long long)atomicAdd(&ctl->nbonds, 0ull);
+      rec->step = latest->step = st;
+      rec->bonds = latest->bonds = nb;
+      ctl->hist_count += 1ull;
+      ctl->reactions += 1ull;
+    }
+  }
 }
 
 template <bool NL16>
@@ -503,14 +549,12 @@ __global__ void __launch_bounds__(RX_THREADS)
   else rx_select_apply_body<false>(S, Blk{m.b, m.nb}, -1LL);
 }
 
-// One block: exclusive scan of the per-block counts, bond-list base, and a
-// cleared history record for this reaction step.
-
-
-// Populations per (type, state) into history record hist_count % hist_cap
-// (integer atomics: the counts do not depend on their order).
-__device__ __forceinline__ void obs_hist_body(const Sys& S, const Blk blk, long long step_arg,
-                                              int record) {
+// Populations per (type, state) counted over every slot into out[128]
+// (integer atomics: the counts do not depend on their order).  With rec set,
+// the last block also stamps rec's step and bond count (on-demand
+// observables, into the spare history slot).
+__device__ __forceinline__ void pop_count_body(const Sys& S, const Blk blk, int32_t* out,
+                                               HistRec* rec) {
   Ctl* ctl = S.ctl;
   const SoA B = ctl->set ? S.s1 : S.s0;
   __shared__ int32_t h[PRX_MAX_TYPES * PRX_MAX_STATES];
@@ -531,30 +575,22 @@ __device__ __forceinline__ void obs_hist_body(const Sys& S, const Blk blk, long 
     if (key >= 0 && lane == __ffs(grp) - 1) atomicAdd(&h[key], __popc(grp));
   }
   __syncthreads();
-  const unsigned long long slot = record ? ctl->hist_count % S.hist_cap : S.hist_cap;
-  HistRec* rec = &S.hist[slot];
   for (int k = threadIdx.x; k < PRX_MAX_TYPES * PRX_MAX_STATES; k += blockDim.x)
-    if (h[k]) atomicAdd(&rec->counts[0][0] + k, h[k]);
+    if (h[k]) atomicAdd(out + k, h[k]);
+  if (!rec) return;
+  __threadfence();
   if (last_block_rx(&ctl->done_obs, blk.nb)) {
     ctl->done_obs = 0u;
-    rec->step = step_arg >= 0 ? step_arg : (long long)ctl->step;
+    rec->step = (long long)ctl->step;
     rec->bonds = (long long)ctl->nbonds;
-    if (record) {
-      ctl->hist_count += 1ull;
-      ctl->reactions += 1ull;
-    }
   }
 }
 
-__global__ void __launch_bounds__(RX_THREADS) k_obs_hist(Sys S, long long step_arg, int record) {
-  obs_hist_body(S, Blk{blockIdx.x, gridDim.x}, step_arg, record);
+__global__ void __launch_bounds__(RX_THREADS) k_obs_hist(Sys S) {
+  pop_count_body(S, Blk{blockIdx.x, gridDim.x}, &S.hist[S.hist_cap].counts[0][0], &S.hist[S.hist_cap]);
 }
-__global__ void __launch_bounds__(RX_THREADS)
-    kb_obs_hist(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
-  const BlkMap m = M[blockIdx.x];
-  const Sys& S = T[m.sys];
-  if (!S.has_rx) return;  // this member has no reaction scheme
-  obs_hist_body(S, Blk{m.b, m.nb}, -1LL, 1);
+__global__ void __launch_bounds__(RX_THREADS) k_pop_init(Sys S) {
+  pop_count_body(S, Blk{blockIdx.x, gridDim.x}, S.pop, nullptr);
 }
 
 // Per-block FP64 partial sums of m v^2 / 2 and m v (fixed-order tree).
@@ -677,7 +713,7 @@ inline unsigned blocks_rx(uint32_t n) { return n ? (n + RX_THREADS - 1) / RX_THR
 
 }  // namespace
 
-int rx_kernel_count(int rule) { return rule == PRX_SELECT_NEAREST ? 5 : 4; }
+int rx_kernel_count(int rule) { return rule == PRX_SELECT_NEAREST ? 4 : 3; }
 
 void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
                void (*hook)(void*, const char*, int), void* ctx) {
@@ -704,9 +740,6 @@ void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
   if (S.nl16) k_rx_select_apply<true><<<gf, RX_THREADS, 0, st>>>(S, step_arg);
   else k_rx_select_apply<false><<<gf, RX_THREADS, 0, st>>>(S, step_arg);
   H("rx_select_apply", 1);
-  H("obs_hist", 0);
-  k_obs_hist<<<gf, RX_THREADS, 0, st>>>(S, step_arg, 1);
-  H("obs_hist", 1);
 }
 
 void launch_pair_hist(const Sys& S, cudaStream_t st, const PairClass& a, const PairClass& b,
@@ -722,14 +755,19 @@ void launch_pair_hist(const Sys& S, cudaStream_t st, const PairClass& a, const P
 // populations; S.red the per-block sums and, after them, their totals.
 void launch_observables(const Sys& S, cudaStream_t st, int nblocks) {
   cudaMemsetAsync(&S.hist[S.hist_cap], 0, sizeof(HistRec), st);
-  k_obs_hist<<<nblocks, RX_THREADS, 0, st>>>(S, -1, 0);
+  k_obs_hist<<<nblocks, RX_THREADS, 0, st>>>(S);
   // the sums on at most 8 blocks per SM, strided over the slots
   const unsigned nsum = nblocks < 1216 ? (unsigned)nblocks : 1216u;
   k_obs_sums<<<nsum, RX_THREADS, 0, st>>>(S, S.mass);
   k_obs_final<<<1, RX_THREADS, 0, st>>>(S, nsum, (uint32_t)nblocks);
 }
 
-int batch_rx_kernel_count() { return 6; }
+void launch_pop_init(const Sys& S, cudaStream_t st) {
+  cudaMemsetAsync(S.pop, 0, sizeof(int32_t) * POP_REPLICAS * PRX_MAX_TYPES * PRX_MAX_STATES, st);
+  if (S.n) k_pop_init<<<blocks_rx(S.n) < 1216u ? blocks_rx(S.n) : 1216u, RX_THREADS, 0, st>>>(S);
+}
+
+int batch_rx_kernel_count() { return 5; }
 
 void launch_batch_rx(const BatchLaunch& L, cudaStream_t st) {
   kb_rx_begin<<<L.n_one, 32, 0, st>>>(L.T, L.one);
@@ -737,7 +775,6 @@ void launch_batch_rx(const BatchLaunch& L, cudaStream_t st) {
   kb_rx_find<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
   kb_rx_find_T<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
   kb_rx_select_apply<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
-  kb_obs_hist<<<L.n_part, RX_THREADS, 0, st>>>(L.T, L.part);
 }
 
 }  // namespace prx

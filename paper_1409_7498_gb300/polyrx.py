@@ -136,6 +136,8 @@ def lib():
         "prx_observables_begin": ([VP, I], I),
         "prx_observables_end": ([VP, I, P(prx_observables)], I),
         "prx_get_history": ([VP, VP, U64, P(U64)], I),
+        "prx_history_begin": ([VP, I], I),
+        "prx_history_end": ([VP, I, VP], I),
         "prx_get_stats": ([VP, P(prx_stats)], I),
         "prx_save": ([VP, C.c_char_p], I),
         "prx_load": ([C.c_char_p, VP, P(VP)], I),
@@ -340,6 +342,17 @@ def prx_get_history(h, cap: int = 1 << 20):
     out = np.zeros(cap, HISTORY_DTYPE)
     _check(lib().prx_get_history(h, _ptr(out), cap, C.byref(n)), h)
     return out[: n.value]
+
+
+def prx_history_begin(h, slot: int):
+    _check(lib().prx_history_begin(h, int(slot)), h)
+
+
+def prx_history_end(h, slot: int):
+    """The newest reaction record (step, bonds, counts) as a one-element array."""
+    out = np.zeros(1, HISTORY_DTYPE)
+    _check(lib().prx_history_end(h, int(slot), _ptr(out)), h)
+    return out[0]
 
 
 def prx_get_stats(h) -> dict:
@@ -710,6 +723,14 @@ class System:
 
     def history(self):
         return prx_get_history(self.h)
+
+    def history_begin(self, slot: int):
+        """Enqueues the copy of the newest reaction record into pinned slot `slot`."""
+        prx_history_begin(self.h, slot)
+
+    def history_end(self, slot: int):
+        """Waits for slot `slot`; returns the newest reaction record."""
+        return prx_history_end(self.h, slot)
 
     def stats(self):
         return prx_get_stats(self.h)

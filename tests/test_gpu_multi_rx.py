@@ -99,6 +99,13 @@ def test_fp32_graph_run_invariants_and_checkpoint(P, tmp_path):
         b = with_reactions(g.bonds())
         st = g.states()
         pos = g.positions()
+        # the reaction records' populations, kept by the reaction kernel one
+        # bond at a time, equal a full count of the states
+        last = g.history()[-1]
+        ty = g.types()
+        for t in (synth.TYPE_B, synth.TYPE_A, synth.TYPE_X6):
+            assert np.array_equal(np.bincount(st[ty == t], minlength=16)[:16], last["counts"][t])
+        assert last["bonds"] == len(b)
     ends = b[:, 1:3]
     for s_ in np.unique(b[:, 0]):
         e = ends[b[:, 0] == s_].ravel()

@@ -415,3 +415,29 @@ def test_ragged_sizes_profile_and_launch_counts(P):
             st = g.stats()
         assert prof["step"]["launches"] == 10 and prof["rx_find"]["launches"] == 1
         assert st["steps"] == 33 and st["kernel_launches"] >= 33
+
+
+def test_pipelined_newest_reaction_record(P):
+    """prx_history_begin / end return the newest reaction record (the same as
+    the last entry of prx_get_history), all zero before the first reaction
+    step, and the populations equal the states read back."""
+    seed = 8
+    inp = synth.step_growth(3000, 600, 4, seed)
+    with gpu_system(P, inp.L, inp.x, inp.v, inp.type, inp.state, cap=4, seed=seed) as g:
+        g.history_begin(0)
+        z = g.history_end(0)
+        assert z["step"] == 0 and z["bonds"] == 0 and (z["counts"] == 0).all()
+        g.set_reaction(gpu_reaction(P, synth.step_growth_scheme(4, k=2.0)))
+        for q in range(5):
+            g.run(30)
+            g.history_begin(q % 2)
+            if q:
+                prev = g.history_end((q - 1) % 2)
+                assert prev["step"] == 30 * q
+        last = g.history_end(4 % 2)
+        h = g.history()
+        assert last["step"] == 150 == h[-1]["step"] and last["bonds"] == h[-1]["bonds"] > 0
+        assert np.array_equal(last["counts"], h[-1]["counts"])
+        st, ty = g.states(), g.types()
+        for t in (synth.TYPE_A, synth.TYPE_B):
+            assert np.array_equal(np.bincount(st[ty == t], minlength=16)[:16], last["counts"][t])
