@@ -724,8 +724,14 @@ def main():
     if not args.no_ensemble:
         ens = ensemble(P, torch, args.ensemble_steps, rank, world, dist)
     srv = None
-    if world == 1 and not args.no_serving:
-        srv = serving(P, torch, args.serving_arrivals, args.serving_step_scale)
+    if not args.no_serving:
+        srv = serving(P, torch, args.serving_arrivals, args.serving_step_scale, rank, world)
+        if world > 1:  # every rank served its share of the arrivals: gather the summaries
+            parts = [None] * world
+            dist.all_gather_object(parts, srv)
+            srv = {"per_rank": parts, "ranks": world,
+                   "replica_steps_per_s": sum(p_["batched"]["replica_steps_per_s"] for p_ in parts),
+                   "p99_latency_s_max": max(p_["batched"]["p99_latency_s"] for p_ in parts)}
     cfgs = None
     if world == 1 and not args.no_configs:
         cfgs = configs_1_2(P, torch, args, stream)
