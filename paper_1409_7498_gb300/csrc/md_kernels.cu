@@ -1008,38 +1008,35 @@ __device__ __forceinline__ float4 build_coords(const uint4 p, const RowInfo& r, 
   return make_float4(xf, yf, zf, __uint_as_float(slot));
 }
 
-// One candidate: hit = r2 < rv2 and not the particle itself; a hit is
-// written to row `cnt` of the slot's column while cnt < cap, and cnt counts
-// every hit (cnt > cap afterwards means the list overflowed).  Predicated
-// PTX, so that the warp does not diverge on the (frequent) hits.
+// One candidate: hit = r2 < rv2; a hit is written to row `cnt` of the
+// slot's column while cnt < cap, and cnt counts every hit (cnt > cap
+// afterwards means the list overflowed).  The caller never passes the
+// particle itself.  Predicated PTX, so that the warp does not diverge on the
+// (frequent) hits.
 template <bool NL16>
 __device__ __forceinline__ void list_candidate(unsigned char* col, uint32_t stride, float r2,
-                                               float rv2, uint32_t qslot, uint32_t i, int cap,
-                                               int& cnt) {
+                                               float rv2, uint32_t qslot, int cap, int& cnt) {
   if constexpr (NL16) {
     asm volatile(
         "{\n\t.reg .pred h, w;\n\t.reg .u64 a;\n\t"
         "setp.lt.f32 h, %1, %2;\n\t"
-        "setp.ne.and.u32 h, %3, %4, h;\n\t"
-        "setp.lt.and.s32 w, %0, %5, h;\n\t"
-        "mad.wide.u32 a, %0, %6, %7;\n\t"
-        "@w st.global.u16 [a], %8;\n\t"
+        "setp.lt.and.s32 w, %0, %4, h;\n\t"
+        "mad.wide.u32 a, %0, %5, %6;\n\t"
+        "@w st.global.u16 [a], %7;\n\t"
         "@h add.s32 %0, %0, 1;\n\t}"
         : "+r"(cnt)
-        : "f"(r2), "f"(rv2), "r"(qslot), "r"(i), "r"(cap), "r"(stride), "l"(col),
-          "h"((uint16_t)qslot)
+        : "f"(r2), "f"(rv2), "r"(qslot), "r"(cap), "r"(stride), "l"(col), "h"((uint16_t)qslot)
         : "memory");
   } else {
     asm volatile(
         "{\n\t.reg .pred h, w;\n\t.reg .u64 a;\n\t"
         "setp.lt.f32 h, %1, %2;\n\t"
-        "setp.ne.and.u32 h, %3, %4, h;\n\t"
-        "setp.lt.and.s32 w, %0, %5, h;\n\t"
-        "mad.wide.u32 a, %0, %6, %7;\n\t"
+        "setp.lt.and.s32 w, %0, %4, h;\n\t"
+        "mad.wide.u32 a, %0, %5, %6;\n\t"
         "@w st.global.u32 [a], %3;\n\t"
         "@h add.s32 %0, %0, 1;\n\t}"
         : "+r"(cnt)
-        : "f"(r2), "f"(rv2), "r"(qslot), "r"(i), "r"(cap), "r"(stride), "l"(col)
+        : "f"(r2), "f"(rv2), "r"(qslot), "r"(cap), "r"(stride), "l"(col)
         : "memory");
   }
 }
@@ -1169,9 +1166,11 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
       win[w] = (uint32_t)lo | ((uint32_t)hi << 16);
     }
     float4 fi;
+    int kself0;  // the particle's own entry in the staged centre row
     {
       const RowInfo& r = ri[RY + yrel + 1];
       fi = build_coords(pi, r, r.padL + ((int)i - r.row_lo), i, sx, sy, sz, Lx);
+      kself0 = r.base + r.padL + ((int)i - r.row_lo);
     }
     int cnt = 0;
     const int cap = S.list_cap;
@@ -1185,16 +1184,27 @@ __device__ __forceinline__ void build_nlist_body(const Sys& S, const Blk blk, un
         __syncthreads();
       }
       if (act) {
+        // the particle itself is staged once, in the centre row's window
+        // (w = 4), whose walk skips it: no candidate needs a self test
+        const int kself = kself0 - c0;
 #pragma unroll
         for (int w = 0; w < 9; ++w) {
           const int lo = max((int)(win[w] & 0xFFFFu), c0) - c0;
           const int hi = min((int)(win[w] >> 16), c0 + cn) - c0;
+          auto walk = [&](int a, int b) {
 #pragma unroll 2
-          for (int k = lo; k < hi; ++k) {
-            const float4 q = sX[k];
-            const float dx = q.x - fi.x, dy = q.y - fi.y, dz = q.z - fi.z;
-            list_candidate<NL16>(col, stride, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), rv2,
-                                 __float_as_uint(q.w), i, cap, cnt);
+            for (int k = a; k < b; ++k) {
+              const float4 q = sX[k];
+              const float dx = q.x - fi.x, dy = q.y - fi.y, dz = q.z - fi.z;
+              list_candidate<NL16>(col, stride, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), rv2,
+                                   __float_as_uint(q.w), cap, cnt);
+            }
+          };
+          if (w == 4) {
+            walk(lo, min(hi, max(lo, kself)));
+            walk(max(lo, kself + 1), hi);
+          } else {
+            walk(lo, hi);
           }
         }
       }
