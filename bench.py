@@ -528,13 +528,10 @@ def serving(P, torch, arrivals: int, step_scale: float, rank: int = 0, world: in
 # ---------------------------------------------------------------------------
 # Reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
-def headline_config(steps: int) -> dict:
+def headline_config(world: int = 1) -> dict:
+    """The workload's identity, the same in both arms."""
     return {"workload": WORKLOAD, "beads": N_BEADS, "f": FUNC, "k": K_RATE, "theta": THETA,
-            "md_steps_per_bench_step": THETA, "md_steps_timed": steps * THETA,
-            "start": f"uniform placement, {CAP_STEPS} steps with the WCA force capped at "
-                     f"{F_CAP:g}, {FREE_STEPS} uncapped steps (untimed)",
-            "l2": "inputs larger than L2: every step streams the ~270 MB system state "
-                  "(129 MB L2); one 256 MB flush before the timed region"}
+            "density": synth.DENSITY, "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args, rank, world):
@@ -575,7 +572,9 @@ def run_reference(args, rank, world):
             "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": done, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / max(done, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": headline_config(args.steps),
+            "config": headline_config(world),
+            "run": {"md_steps_per_bench_step": 1, "md_steps_timed": done,
+                    "start": "the workload's lattice placement (no warm-up)"},
             "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": cores,
                              "kind": "oracle", "nproc": os.cpu_count(),
                              "sample": f"{done} MD steps of the {inp.n}-bead workload from its "
@@ -752,8 +751,13 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 forces / f64 integration", "data": "synthetic",
-            "config": dict(headline_config(args.steps), parallelism=f"replicas x{world}"),
-            "run": run_info, "clocks": clocks, "gpu_launches": launches, "roofline": roof,
+            "config": headline_config(world),
+            "run": dict(run_info, md_steps_per_bench_step=THETA, md_steps_timed=args.steps * THETA,
+                        start=f"uniform placement, {CAP_STEPS} steps with the WCA force capped at "
+                              f"{F_CAP:g}, {FREE_STEPS} uncapped steps (untimed)",
+                        l2="inputs larger than L2: every step streams the ~270 MB system state "
+                           "(129 MB L2); one 256 MB flush before the timed region"),
+            "clocks": clocks, "gpu_launches": launches, "roofline": roof,
             "e2e": e2e, "cpu_baseline": cpu, "configs": cfgs, "ensemble": ens,
             "serving": srv,
         }
