@@ -203,6 +203,17 @@ __device__ __forceinline__ bool moved_beyond_skin(const Sys& S, uint32_t X, uint
   return fmaf(ez, ez, fmaf(ey, ey, ex * ex)) > S.disp2_max;
 }
 
+// periodic_fx for the step kernel: the scaling by 2^32 added to the binary64
+// exponent field (exact for normal x; zero and subnormals stay below 1) and
+// the truncation done by the hardware FP64 -> s64 conversion, which costs
+// one FP64-pipe instruction instead of fx32's variable 64-bit shifts.  The
+// same value as periodic_fx for |x| < 2^29.
+__device__ __forceinline__ uint32_t periodic_fx_cvt(double x, long long Lfx, unsigned long long M) {
+  const double y = __longlong_as_double(__double_as_longlong(x) + (32LL << 52));
+  const unsigned long long a = (unsigned long long)(__double2ll_rz(y) + Lfx);
+  return (uint32_t)__umul64hi(a, M);
+}
+
 // End of an FP32-mode step for one slot: Langevin kick (friction applied
 // exactly in FP64), drift, new fixed-point position, rebuild trigger.
 //   v' = a v + b (F_c + R),  x' = x + dt v'
@@ -226,9 +237,9 @@ __device__ __forceinline__ void integrate32(const Sys& S, Ctl* ctl, const SoA& B
   const double nx = __fma_rn(S.dt, vx, xi);
   const double ny = __fma_rn(S.dt, vy, yi);
   const double nz = __fma_rn(S.dt, vz, zi);
-  const uint32_t X = periodic_fx(nx, S.Lfx[0], S.M64[0]);
-  const uint32_t Y = periodic_fx(ny, S.Lfx[1], S.M64[1]);
-  const uint32_t Z = periodic_fx(nz, S.Lfx[2], S.M64[2]);
+  const uint32_t X = periodic_fx_cvt(nx, S.Lfx[0], S.M64[0]);
+  const uint32_t Y = periodic_fx_cvt(ny, S.Lfx[1], S.M64[1]);
+  const uint32_t Z = periodic_fx_cvt(nz, S.Lfx[2], S.M64[2]);
   if (moved_beyond_skin(S, X, Y, Z, W)) raise_rebuild(S);
   B.vx[i] = vx;
   B.vy[i] = vy;
@@ -295,12 +306,20 @@ __device__ __forceinline__ void step_one(const Sys& S, Ctl* ctl, const SoA& B,
   }
   bool ok = true;
   const uint32_t nb = __ldg(B.nadj + i);
-  for (int b = 0; b < (int)nb; ++b) {
-    const uint32_t ent = __ldg(B.adj + (size_t)i * S.cap + b);
-    const uint4 pj = __ldg(P + (ent & SLOT_MASK));
+  // bonds two at a time: both entries, then both partners' positions, in
+  // flight together (half the dependent load chains)
+  for (int b = 0; b < (int)nb; b += 2) {
+    const uint32_t* arow = B.adj + (size_t)i * S.cap + b;
+    const bool two = b + 1 < (int)nb;
+    const uint32_t e0 = __ldg(arow), e1 = two ? __ldg(arow + 1) : i;
+    const uint4 p0 = __ldg(P + (e0 & SLOT_MASK)), p1 = __ldg(P + (e1 & SLOT_MASK));
     float dx, dy, dz;
-    disp(S, pj, pi, dx, dy, dz);
-    ok = bond32(S, ent >> 31, dx, dy, dz, fx, fy, fz, e) && ok;
+    disp(S, p0, pi, dx, dy, dz);
+    ok = bond32(S, e0 >> 31, dx, dy, dz, fx, fy, fz, e) && ok;
+    if (two) {
+      disp(S, p1, pi, dx, dy, dz);
+      ok = bond32(S, e1 >> 31, dx, dy, dz, fx, fy, fz, e) && ok;
+    }
   }
   if (!ok) set_status(ctl, PRX_EOVERSTRETCH);
   if constexpr (FORCES_ONLY) {

@@ -189,3 +189,31 @@ def test_list_build_fp32_radius_keeps_every_pair_within_the_list_radius():
             e = [np.float32(b - a) for a, b in zip(fi, fj)]
             r2 = fma32(e[2], e[2], fma32(e[1], e[1], np.float32(e[0] * e[0])))
             assert r2 < rv2_build, (L, xi, xj, float(r2), float(rv2_build))
+
+
+def test_exponent_field_scaling_then_truncation_equals_fx32():
+    """The step kernel forms trunc(x 2^32) by adding 32 to the binary64
+    exponent field and truncating with the hardware FP64 -> s64 conversion;
+    fx32 reads the same value off the fields with shifts.  Both equal the
+    exact trunc(x 2^32) for |x| < 2^29, including zero, -0, subnormals and
+    values next to integers and to multiples of 2^-32."""
+    rng = np.random.default_rng(7498)
+
+    def via_exponent(x: float) -> int:
+        b = int(np.array([x], dtype=np.float64).view(np.int64)[0])
+        y = float(np.array([b + (32 << 52)], dtype=np.int64).view(np.float64)[0])
+        return int(y)  # Python int() truncates toward zero, as cvt.rzi does
+
+    def exact(x: float) -> int:
+        q = Fraction(x) * (1 << 32)
+        return int(q)  # toward zero
+
+    xs = [0.0, -0.0, 5e-324, -5e-324, 2.2e-308, 2.0 ** -32, -(2.0 ** -32), 2.0 ** -33,
+          float(np.nextafter(2.0 ** -32, 0.0)), float(np.nextafter(1.0, 0.0)), 1.0, -1.0,
+          107.19, -107.19, float(np.nextafter(2.0 ** 29, 0.0)), -float(np.nextafter(2.0 ** 29, 0.0))]
+    xs += list(rng.uniform(-120.0, 240.0, 3000))
+    xs += list(10.0 ** rng.uniform(-12, 8.7, 2000) * rng.choice([-1.0, 1.0], 2000))
+    k = rng.integers(-(1 << 40), 1 << 40, 1000)
+    xs += [float(np.nextafter(float(v) * 2.0 ** -32, d)) for v, d in zip(k, rng.choice([-1e9, 1e9], 1000))]
+    for x in xs:
+        assert via_exponent(x) == exact(x), x
