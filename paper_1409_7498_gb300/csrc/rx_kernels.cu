@@ -160,9 +160,6 @@ __device__ __forceinline__ uint32_t nearest_partner(const Sys& S, const SoA& B, 
   return best;
 }
 
-// Steps 1-5 for one eligible A: its Verlet list holds every particle within
-// the force cutoff, hence every candidate within r_react <= r_c.  Grid-stride
-// over the work list of eligible A's.
 // Table I steps 2 and 5 for one candidate pair (A = idi, T = slot j):
 // retained when u < k dt Theta (Eq. 4), then the smallest selection key wins
 // (ties to the smaller id).
@@ -243,6 +240,89 @@ __device__ __forceinline__ uint32_t rx_find_multi(const Sys& S, const SoA& B, co
   return best;
 }
 
+// Steps 1-5 for the single-reaction random rule, over the work list of
+// eligible A's (grid-stride).  An A's Verlet list holds every particle within
+// the list cutoff, which includes r_react, hence every candidate.  Four lanes
+// per eligible A:
+// lane q of an A's group takes its list entries q, q + 4, ..., marks its
+// candidates, draws for them, and keeps its retained pair of smallest
+// (key, id); the group then takes the smallest of the four.  That pair is
+// the unique minimum over all of the A's retained pairs, the same one the
+// list walk of a single thread finds, so the choice does not depend on the
+// split; four lanes per A shorten each A's chain of dependent list ->
+// position -> type loads fourfold.  The loop's trip count is uniform over a
+// warp (8 A's per warp and pass), so the group shuffles see every lane.
+template <bool NL16>
+__device__ __forceinline__ void rx_find_random4(const Sys& S, const Blk blk, const SoA& B,
+                                                const uint4* P, unsigned long long step,
+                                                uint32_t nact, long long& ncand, long long& nret) {
+  const RxParams& R = S.R;
+  const uint32_t q = threadIdx.x & 3u;
+  const uint32_t gstride = (blk.nb * blockDim.x) >> 2;
+  for (uint32_t wb = (blk.b * blockDim.x + (threadIdx.x & ~31u)) >> 2; wb < nact; wb += gstride) {
+    const uint32_t w = wb + ((threadIdx.x & 31u) >> 2);
+    const bool valid = w < nact;
+    uint32_t best = NONE, bestid = 0u;
+    unsigned long long bestkey = 0ull;
+    const uint32_t i = valid ? S.tmp[w] : 0u;
+    if (valid) {
+      const uint4 pi = P[i];
+      const uint32_t idi = B.id[i];
+      const uint32_t nb = B.nadj[i];
+      const int cnt = S.nn[i];
+      // pass 1 marks this lane's candidates (bit k / 4 for list entry k);
+      // pass 2 draws for them
+      unsigned long long mask = 0ull;
+      for (int k = (int)q; k < cnt; k += 4) {
+        const uint32_t j = nl_get_rx<NL16>(S, k, i);
+        const uint4 pj = P[j];
+        const float ex = __int2float_rn(pdiff(pj.x, pi.x)) * S.scale[0];
+        const float ey = __int2float_rn(pdiff(pj.y, pi.y)) * S.scale[1];
+        const float ez = __int2float_rn(pdiff(pj.z, pi.z)) * S.scale[2];
+        const float r2f = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+        if (!(r2f < R.rr2_pre)) continue;
+        if (!in_window(R.mask_T, R.t_lo, R.t_hi, B.type[j], B.state[j])) continue;
+        if (!(r2f < R.rr2_in)) {  // near the cutoff: the exact FP64 test
+          const double ddx = min_image(__dsub_rn(B.x[j], B.x[i]), S.L[0], S.halfL[0]);
+          const double ddy = min_image(__dsub_rn(B.y[j], B.y[i]), S.L[1], S.halfL[1]);
+          const double ddz = min_image(__dsub_rn(B.z[j], B.z[i]), S.L[2], S.halfL[2]);
+          const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
+          if (!(r2 < R.rr2)) continue;
+        }
+        bool bonded = false;
+        for (uint32_t b = 0; b < nb; ++b) bonded |= (B.adj[(size_t)i * S.cap + b] & SLOT_MASK) == j;
+        if (bonded) continue;
+        const int m = k >> 2;
+        if (m < 64) {
+          mask |= 1ull << m;
+        } else {
+          ++ncand;
+          rx_accept_and_key(S, B, step, idi, j, R.p53, nret, best, bestkey, bestid);
+        }
+      }
+      while (mask) {
+        const int m = __ffsll((long long)mask) - 1;
+        mask &= mask - 1ull;
+        ++ncand;
+        rx_accept_and_key(S, B, step, idi, nl_get_rx<NL16>(S, 4 * m + (int)q, i), R.p53, nret,
+                          best, bestkey, bestid);
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < 4; off <<= 1) {
+      const unsigned long long ok = __shfl_xor_sync(0xFFFFFFFFu, bestkey, off);
+      const uint32_t oid = __shfl_xor_sync(0xFFFFFFFFu, bestid, off);
+      const uint32_t ob = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+      if (ob != NONE && (best == NONE || ok < bestkey || (ok == bestkey && oid < bestid))) {
+        best = ob;
+        bestkey = ok;
+        bestid = oid;
+      }
+    }
+    if (valid && q == 0u) S.win[i] = best;
+  }
+}
+
 template <bool NL16>
 __device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long long step_arg) {
   const RxParams& R = S.R;
@@ -253,71 +333,22 @@ __device__ __forceinline__ void rx_find_body(const Sys& S, const Blk blk, long l
   const uint4* P = ctl->phase ? S.P1 : S.P0;
   const uint32_t nact = ctl->n_active;
   long long ncand = 0, nret = 0;
-  for (uint32_t w = blk.b * blockDim.x + threadIdx.x; w < nact; w += blk.nb * blockDim.x) {
-    const uint32_t i = S.tmp[w];
-    uint32_t best = NONE;
-    if (R.rule == PRX_SELECT_NEAREST) {
-      best = nearest_partner<NL16>(S, B, P, i, true, ncand);
-    } else if (R.nr > 1) {
-      uint32_t ch = 0u;
-      best = rx_find_multi<NL16>(S, B, P, step, i, ncand, nret, ch);
-      S.wch[i] = (uint8_t)ch;
-    } else {
-      const uint4 pi = P[i];
-      const uint32_t idi = B.id[i];
-      const uint32_t nb = B.nadj[i];
-      unsigned long long bestkey = 0ull;
-      uint32_t bestid = 0u;
-      const int cnt = S.nn[i];
-      // Pass 1 marks the list positions of the candidates (steps 1 and the
-      // bond check); pass 2 draws for them.  The draws (two Philox calls per
-      // candidate) then run once per candidate of the busiest lane, not once
-      // per list position at which any lane of the warp has one.
-      unsigned long long mask = 0ull;
-      for (int k = 0; k < cnt; ++k) {
-        const uint32_t j = nl_get_rx<NL16>(S, k, i);
-        // FP32 prefilter on the fixed-point displacement (error ~1e-7): it can
-        // only widen the set that the exact FP64 test below decides on.  It
-        // comes before the T-window test: the position gather is one sector
-        // per entry either way, the type and state bytes are two more, and
-        // only a third of the entries lie within r_react.
-        const uint4 pj = P[j];
-        const float ex = __int2float_rn(pdiff(pj.x, pi.x)) * S.scale[0];
-        const float ey = __int2float_rn(pdiff(pj.y, pi.y)) * S.scale[1];
-        const float ez = __int2float_rn(pdiff(pj.z, pi.z)) * S.scale[2];
-        const float r2f = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-        if (!(r2f < R.rr2_pre)) continue;
-        if (!in_window(R.mask_T, R.t_lo, R.t_hi, B.type[j], B.state[j])) continue;
-        // exact test, Table I step 1: d = x_T - x_A under the minimum image,
-        // r^2 = fma(dz, dz, fma(dy, dy, dx dx)), strict r^2 < r_react^2.  The
-        // FP32 value from the fixed-point positions is within a known bound
-        // of it, so below rr2_in (the cutoff minus twice that bound) the FP64
-        // test cannot fail; only pairs near the cutoff take it.
-        if (!(r2f < R.rr2_in)) {  // A's FP64 position loaded only here (rare)
-          const double ddx = min_image(__dsub_rn(B.x[j], B.x[i]), S.L[0], S.halfL[0]);
-          const double ddy = min_image(__dsub_rn(B.y[j], B.y[i]), S.L[1], S.halfL[1]);
-          const double ddz = min_image(__dsub_rn(B.z[j], B.z[i]), S.L[2], S.halfL[2]);
-          const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
-          if (!(r2 < R.rr2)) continue;
-        }
-        bool bonded = false;
-        for (uint32_t b = 0; b < nb; ++b) bonded |= (B.adj[(size_t)i * S.cap + b] & SLOT_MASK) == j;
-        if (bonded) continue;
-        if (k < 64) {
-          mask |= 1ull << k;
-        } else {  // beyond 64 list entries (very dense systems): draw at once
-          ++ncand;
-          rx_accept_and_key(S, B, step, idi, j, R.p53, nret, best, bestkey, bestid);
-        }
+  if (R.rule != PRX_SELECT_NEAREST && R.nr <= 1) {
+    rx_find_random4<NL16>(S, blk, B, P, step, nact, ncand, nret);
+  } else {
+    // the nearest rule and concurrent reactions: one thread per eligible A
+    for (uint32_t w = blk.b * blockDim.x + threadIdx.x; w < nact; w += blk.nb * blockDim.x) {
+      const uint32_t i = S.tmp[w];
+      uint32_t best = NONE;
+      if (R.rule == PRX_SELECT_NEAREST) {
+        best = nearest_partner<NL16>(S, B, P, i, true, ncand);
+      } else {
+        uint32_t ch = 0u;
+        best = rx_find_multi<NL16>(S, B, P, step, i, ncand, nret, ch);
+        S.wch[i] = (uint8_t)ch;
       }
-      while (mask) {
-        const int k = __ffsll((long long)mask) - 1;
-        mask &= mask - 1ull;
-        ++ncand;
-        rx_accept_and_key(S, B, step, idi, nl_get_rx<NL16>(S, k, i), R.p53, nret, best, bestkey, bestid);
-      }
+      S.win[i] = best;
     }
-    S.win[i] = best;
   }
   const long long c = block_sum_ll(ncand);
   const long long r = block_sum_ll(nret);
