@@ -74,6 +74,9 @@ def parse():
                     help="seconds of oracle work per CPU timing")
     ap.add_argument("--direct", action="store_true",
                     help="launch kernels one by one instead of CUDA graphs (for ncu launch lists)")
+    ap.add_argument("--profile-roofline", action="store_true",
+                    help="bracket the headline's roofline leg with cudaProfilerStart / Stop "
+                         "(for ncu --profile-from-start off)")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the batched-ensemble measurement")
     ap.add_argument("--ensemble-steps", type=int, default=20,
@@ -676,7 +679,13 @@ def main():
                 "bonds_end": int(obs_end["bonds"]),
                 "conversion_end": obs_end["bonds"] / (FUNC * n_A),
                 "bonds_per_bead_end": 2.0 * obs_end["bonds"] / inp.n}
+    if args.profile_roofline:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
     roof = roofline_of(P, g, inp.n)
+    if args.profile_roofline:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     roof["traffic"] = step_kernel_traffic()
     del flush
 

@@ -305,10 +305,28 @@ __device__ __forceinline__ void step_one(const Sys& S, Ctl* ctl, const SoA& B,
     fz *= S.scale[0];
   }
   bool ok = true;
-  const uint32_t nb = __ldg(B.nadj + i);
   // bonds two at a time: both entries, then both partners' positions, in
-  // flight together (half the dependent load chains)
-  for (int b = 0; b < (int)nb; b += 2) {
+  // flight together (half the dependent load chains).  The first pair's
+  // entries load beside the bond count, and its gathers do not wait for it:
+  // entries past the count (stale or never written) are clamped to a valid
+  // slot and their terms skipped.
+  const uint32_t* arow0 = B.adj + (size_t)i * S.cap;
+  const uint32_t nb = __ldg(B.nadj + i);
+  {
+    const uint32_t e0 = __ldg(arow0), e1 = S.cap > 1 ? __ldg(arow0 + 1) : i;
+    const uint32_t s0 = min(e0 & SLOT_MASK, S.n - 1u), s1 = min(e1 & SLOT_MASK, S.n - 1u);
+    const uint4 p0 = __ldg(P + s0), p1 = __ldg(P + s1);
+    float dx, dy, dz;
+    if (nb > 0u) {
+      disp(S, p0, pi, dx, dy, dz);
+      ok = bond32(S, e0 >> 31, dx, dy, dz, fx, fy, fz, e) && ok;
+    }
+    if (nb > 1u) {
+      disp(S, p1, pi, dx, dy, dz);
+      ok = bond32(S, e1 >> 31, dx, dy, dz, fx, fy, fz, e) && ok;
+    }
+  }
+  for (int b = 2; b < (int)nb; b += 2) {
     const uint32_t* arow = B.adj + (size_t)i * S.cap + b;
     const bool two = b + 1 < (int)nb;
     const uint32_t e0 = __ldg(arow), e1 = two ? __ldg(arow + 1) : i;
