@@ -273,31 +273,48 @@ __device__ __forceinline__ void rx_find_random4(const Sys& S, const Blk blk, con
       // pass 1 marks this lane's candidates (bit k / 4 for list entry k);
       // pass 2 draws for them
       unsigned long long mask = 0ull;
-      for (int k = (int)q; k < cnt; k += 4) {
-        const uint32_t j = nl_get_rx<NL16>(S, k, i);
-        const uint4 pj = P[j];
-        const float ex = __int2float_rn(pdiff(pj.x, pi.x)) * S.scale[0];
-        const float ey = __int2float_rn(pdiff(pj.y, pi.y)) * S.scale[1];
-        const float ez = __int2float_rn(pdiff(pj.z, pi.z)) * S.scale[2];
-        const float r2f = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-        if (!(r2f < R.rr2_pre)) continue;
-        if (!in_window(R.mask_T, R.t_lo, R.t_hi, B.type[j], B.state[j])) continue;
-        if (!(r2f < R.rr2_in)) {  // near the cutoff: the exact FP64 test
-          const double ddx = min_image(__dsub_rn(B.x[j], B.x[i]), S.L[0], S.halfL[0]);
-          const double ddy = min_image(__dsub_rn(B.y[j], B.y[i]), S.L[1], S.halfL[1]);
-          const double ddz = min_image(__dsub_rn(B.z[j], B.z[i]), S.L[2], S.halfL[2]);
-          const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
-          if (!(r2 < R.rr2)) continue;
+      for (int k0 = (int)q; k0 < cnt; k0 += 16) {
+        // up to four of this lane's entries at once: their slots, then their
+        // positions, then the types and states of those within the prefilter
+        uint32_t jj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) jj[u] = k0 + 4 * u < cnt ? nl_get_rx<NL16>(S, k0 + 4 * u, i) : i;
+        float r2v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint4 pj = P[jj[u]];
+          const float ex = __int2float_rn(pdiff(pj.x, pi.x)) * S.scale[0];
+          const float ey = __int2float_rn(pdiff(pj.y, pi.y)) * S.scale[1];
+          const float ez = __int2float_rn(pdiff(pj.z, pi.z)) * S.scale[2];
+          r2v[u] = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
         }
-        bool bonded = false;
-        for (uint32_t b = 0; b < nb; ++b) bonded |= (B.adj[(size_t)i * S.cap + b] & SLOT_MASK) == j;
-        if (bonded) continue;
-        const int m = k >> 2;
-        if (m < 64) {
-          mask |= 1ull << m;
-        } else {
-          ++ncand;
-          rx_accept_and_key(S, B, step, idi, j, R.p53, nret, best, bestkey, bestid);
+        uint32_t tw = 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool near = k0 + 4 * u < cnt && r2v[u] < R.rr2_pre;
+          if (near && in_window(R.mask_T, R.t_lo, R.t_hi, B.type[jj[u]], B.state[jj[u]])) tw |= 1u << u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (!((tw >> u) & 1u)) continue;
+          const uint32_t j = jj[u];
+          if (!(r2v[u] < R.rr2_in)) {  // near the cutoff: the exact FP64 test
+            const double ddx = min_image(__dsub_rn(B.x[j], B.x[i]), S.L[0], S.halfL[0]);
+            const double ddy = min_image(__dsub_rn(B.y[j], B.y[i]), S.L[1], S.halfL[1]);
+            const double ddz = min_image(__dsub_rn(B.z[j], B.z[i]), S.L[2], S.halfL[2]);
+            const double r2 = __fma_rn(ddz, ddz, __fma_rn(ddy, ddy, __dmul_rn(ddx, ddx)));
+            if (!(r2 < R.rr2)) continue;
+          }
+          bool bonded = false;
+          for (uint32_t b = 0; b < nb; ++b) bonded |= (B.adj[(size_t)i * S.cap + b] & SLOT_MASK) == j;
+          if (bonded) continue;
+          const int m = (k0 + 4 * u) >> 2;
+          if (m < 64) {
+            mask |= 1ull << m;
+          } else {
+            ++ncand;
+            rx_accept_and_key(S, B, step, idi, j, R.p53, nret, best, bestkey, bestid);
+          }
         }
       }
       while (mask) {
