@@ -106,9 +106,66 @@ __device__ __forceinline__ void rx_compact_body(const Sys& S, const Blk blk) {
   if (el) S.tmp[bbase + wcnt[wid] + __popc(bal & ((1u << lane) - 1u))] = i;
 }
 
-__global__ void __launch_bounds__(RX_THREADS) k_rx_compact(Sys S) {
-  rx_compact_body(S, Blk{blockIdx.x, gridDim.x});
+// The compaction of a single system: four slots per thread (one 4-byte load
+// of types and one of states, one 16-byte clear of win), so a quarter of
+// the blocks and of the block-level atomics on the work-list counter.  The
+// list's order differs from rx_compact_body's, which does not matter.
+__global__ void __launch_bounds__(RX_THREADS) k_rx_compact4(Sys S) {
+  const RxParams& R = S.R;
+  Ctl* ctl = S.ctl;
+  const SoA B = ctl->set ? S.s1 : S.s0;
+  const uint32_t i0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4u;
+  uint32_t bits = 0u;
+  if (i0 + 3u < S.n) {
+    const uchar4 t4 = *reinterpret_cast<const uchar4*>(B.type + i0);
+    const char4 s4 = *reinterpret_cast<const char4*>(B.state + i0);
+    *reinterpret_cast<uint4*>(S.win + i0) = make_uint4(NONE, NONE, NONE, NONE);
+    const uint32_t tt[4] = {t4.x, t4.y, t4.z, t4.w};
+    const int ss[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool el = R.nr > 1 ? rx_elig_A(R, tt[u], ss[u]) != 0u
+                               : in_window(R.mask_A, R.a_lo, R.a_hi, tt[u], ss[u]);
+      bits |= (el ? 1u : 0u) << u;
+    }
+  } else {
+    for (uint32_t u = 0; u < 4u && i0 + u < S.n; ++u) {
+      const uint32_t i = i0 + u;
+      S.win[i] = NONE;
+      const bool el = R.nr > 1 ? rx_elig_A(R, B.type[i], B.state[i]) != 0u
+                               : in_window(R.mask_A, R.a_lo, R.a_hi, B.type[i], B.state[i]);
+      bits |= (el ? 1u : 0u) << u;
+    }
+  }
+  // warp inclusive scan of the counts, block prefix in shared memory, one
+  // atomic per block
+  const uint32_t c = __popc(bits);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  __shared__ uint32_t wcnt[RX_THREADS / 32];
+  __shared__ uint32_t bbase;
+  if (lane == 31) wcnt[wid] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < RX_THREADS / 32; ++w) {
+      const uint32_t v = wcnt[w];
+      wcnt[w] = t;
+      t += v;
+    }
+    bbase = t ? atomicAdd(&ctl->n_active, t) : 0u;
+  }
+  __syncthreads();
+  uint32_t pos = bbase + wcnt[wid] + x - c;
+  for (uint32_t u = 0; u < 4u; ++u)
+    if ((bits >> u) & 1u) S.tmp[pos++] = i0 + u;
 }
+
 __global__ void __launch_bounds__(RX_THREADS)
     kb_rx_compact(const Sys* __restrict__ T, const BlkMap* __restrict__ M) {
   const BlkMap m = M[blockIdx.x];
@@ -771,7 +828,10 @@ void launch_rx(const Sys& S, cudaStream_t st, long long step_arg,
   };
   cudaMemsetAsync(&S.ctl->trace[0], 0, sizeof(long long) * 4 + sizeof(unsigned int), st);
   H("rx_compact", 0);
-  k_rx_compact<<<g, RX_THREADS, 0, st>>>(S);
+  {
+    const unsigned g4 = blocks_rx((S.n + 3u) / 4u);
+    k_rx_compact4<<<g4, RX_THREADS, 0, st>>>(S);
+  }
   H("rx_compact", 1);
   const unsigned gf = g < 1216u ? g : 1216u;
   H("rx_find", 0);
