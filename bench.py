@@ -273,13 +273,15 @@ def cpu_baselines(inp, sch, cap, seed, budget_s, max_steps, what: str) -> dict:
 
 
 # ---------------------------------------------------------------------------
-# Smaller workloads: 1,250-bead FP64 step growth, 33,096-bead chain growth
+# The other workloads: 1,250-bead FP64 step growth, 33,096-bead chain growth,
+# 1M-bead step growth with crosslinkers of functionality 6
 # ---------------------------------------------------------------------------
 def small_config(P, torch, name: str, inp, sch: dict, cap: int, fp64: bool, md_steps: int,
-                 seed: int, args, stream) -> dict:
-    """One full run of a small workload from its warmed liquid: the whole
-    run timed as one region with CUDA events (the state fits in L2; the L2
-    is flushed once before it), its step kernel's roofline over ten further
+                 seed: int, args, stream,
+                 l2: str = "flushed once before the timed run (the whole state fits in L2)") -> dict:
+    """One full run of a workload other than the headline's from its warmed
+    liquid: the whole run timed as one region with CUDA events (the L2 is
+    flushed once before it), its step kernel's roofline over ten further
     intervals, and the oracle timed on the same start."""
     xw, vw = warmed_liquid(P, inp, cap, seed, fp64=fp64, stream=stream.cuda_stream)
     rx = P.make_reaction(**sch)
@@ -319,8 +321,7 @@ def small_config(P, torch, name: str, inp, sch: dict, cap: int, fp64: bool, md_s
             "dtype": "f64" if fp64 else "f32 forces / f64 integration",
             "bonds_end": int(obs["bonds"]), "gpu_launches": int(st1["kernel_launches"]
                                                                - st0["kernel_launches"]),
-            "rebins": int(st1["rebins"] - st0["rebins"]), "roofline": roof,
-            "l2": "flushed once before the timed run (the whole state fits in L2)"}
+            "rebins": int(st1["rebins"] - st0["rebins"]), "roofline": roof, "l2": l2}
     if not args.no_cpu_baseline:
         class _W:
             pass
@@ -346,6 +347,16 @@ def configs_1_2(P, torch, args, stream) -> dict:
         nm = f"chain_growth_33096_k{k:g}"
         out[nm] = small_config(P, torch, nm, inp, synth.chain_growth_scheme(k), 2, False,
                                W2["steps"], seed, args, stream)
+    # the 1M-bead step growth with crosslinkers of functionality 6 (the
+    # same 4:1 B:A site ratio), its full run
+    W3 = synth.WORKLOADS["step_growth_1m"]
+    seed = synth.BASE_SEED + 303
+    inp = synth.step_growth_sites(W3["n_total"], 6, seed, placement="uniform")
+    out["step_growth_1m_f6"] = small_config(
+        P, torch, "step_growth_1m_f6", inp, synth.step_growth_scheme(6, k=W3["k"], theta=THETA), 6,
+        False, W3["steps"], seed, args, stream,
+        l2="inputs larger than L2: every step streams the whole system state (129 MB L2); "
+           "one 256 MB flush before the timed run")
     return out
 
 
