@@ -48,7 +48,8 @@ extern "C" {
 #define PRX_EOVERSTRETCH (-4) /* a FENE bond reached r >= R0 */
 #define PRX_ENONFINITE (-5)   /* a position, velocity or force became non-finite,
                                  or a particle crossed more than one cell in a step */
-#define PRX_ETIMEOUT (-6)     /* a bounded device wait gave up */
+#define PRX_ETIMEOUT (-6)     /* a bounded device wait gave up (reserved: no kernel of
+                                 this version waits on a flag) */
 #define PRX_ECUDA (-7)        /* a CUDA runtime call failed */
 #define PRX_EIO (-8)          /* checkpoint file could not be read or written */
 
