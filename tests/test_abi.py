@@ -78,7 +78,7 @@ def test_library_has_no_cpu_fallback_path():
         if f.endswith(".cu"):
             kernels |= set(re.findall(r"__global__[^;{]*?\b(kb?_\w+)\s*\(", open(os.path.join(csrc, f)).read()))
     for k in ["k_step_nl", "kb_step_nl", "kb_build_nlist", "kb_rx_find", "k_build_nlist", "k_forces64", "k_integrate64", "k_rebin_keys", "k_rebin_permute", "k_rx_find", "k_rx_select_apply",
-              "k_rx_compact", "k_obs_hist"]:
+              "k_rx_compact4", "kb_rx_compact", "k_obs_hist"]:
         assert k in kernels
     binding = open(os.path.join(ROOT, "paper_1409_7498_gb300", "polyrx.py")).read()
     assert "import oracle" not in binding and "from oracle" not in binding
