@@ -186,6 +186,48 @@ def test_force_cap_and_mirror_lj(P):
         assert err["max_over_rms"] < (1e-12 if fp64 else 1e-5), (fp64, err)
 
 
+@pytest.mark.parametrize("cap", [1, 3, 6])
+def test_bond_forces_at_every_bond_count(P, cap):
+    """FENE bonds on a jittered lattice, each bead bonded to up to `cap` of
+    its lattice neighbours, so that every bond count from 0 to cap occurs
+    (odd counts, a single bond with an adjacency row of one entry, rows
+    longer than four): FP32 forces of the step kernel's code and the one
+    MD step after it against the oracle."""
+    rng = np.random.default_rng(100 + cap)
+    m = 12
+    n = m ** 3
+    L = synth.box_edge(n)
+    a = L / m
+    g3 = np.stack(np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij"), -1)
+    g3 = g3.reshape(-1, 3)
+    x = (g3 + 0.5) * a + rng.uniform(-0.03, 0.03, (n, 3))
+    o = oracle_system(x, np.zeros((n, 3)), np.zeros(n, np.uint8), np.zeros(n, np.int8), cap)
+    deg = np.zeros(n, int)
+    want = rng.integers(0, cap + 1, n)  # each bead's target bond count
+    idx = lambda c: int(((c[0] % m) * m + (c[1] % m)) * m + (c[2] % m))
+    for i in range(n):
+        for d in ((1, 0, 0), (0, 1, 0), (0, 0, 1), (-1, 0, 0), (0, -1, 0), (0, 0, -1)):
+            j = idx(g3[i] + np.array(d))
+            if i < j and deg[i] < want[i] and deg[j] < cap:
+                o.add_bond(i, j, orc.BOND_FENE)
+                deg[i] += 1
+                deg[j] += 1
+    assert set(range(cap + 1)) <= set(deg.tolist()), np.bincount(deg)
+    md = md_params(L, 7)
+    f_ref, _ = orc.forces(o, md, use_cells=True)
+    with gpu_system(P, L, x, None, o.type, o.state, cap=cap, seed=7,
+                    bonds=bonds_of_oracle(o)) as g:
+        f, _ = g.forces()
+        err = force_errors(f, f_ref)
+        assert err["max_over_rms"] < 1e-5, err
+        g.run(1)
+        xg = g.positions()
+    orc.step(o, md)
+    # FP32 force error (1e-5 of ~50) times dt^2, plus the kick's FP32 rounding:
+    # ~1e-8; a missing or doubled bond term would move a bead by ~1e-3
+    assert min_image_diff(xg, o.x, L) < 1e-7
+
+
 # ---------------------------------------------------------------------------
 # Trajectories (FP64 mode follows the oracle's arithmetic step for step)
 # ---------------------------------------------------------------------------
