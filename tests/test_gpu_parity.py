@@ -91,6 +91,26 @@ def test_react_once_bit_exact(P, kind, n, k, pre, sel):
     g.close()
 
 
+@pytest.mark.parametrize("sel", [0, 1])
+def test_react_once_bit_exact_wide_cutoff(P, sel):
+    """A reaction cutoff beyond the WCA cutoff (r_react = 1.6): the Verlet
+    lists grow to ~35 entries, so each lane of the four-lane search walks
+    several groups of four entries."""
+    n, seed = 4099, 77
+    inp, scheme, cap, o, md = seeded_state("step4", n, seed, pre_reactions=0)
+    sch = dict(scheme, k=0.5, selection=sel, r_react=1.6)
+    g = gpu_from_oracle_state(P, inp, o, cap, seed)
+    g.set_reaction(gpu_reaction(P, sch))
+    for step in (10, 20, 30):
+        tr_o = orc.react(o, md, orc_reaction(sch), step=step, use_cells=True)
+        tr_g = g.react_once(step)
+        assert tr_g == tr_o, (step, tr_g, tr_o)
+        assert (g.states() == o.state).all()
+        assert np.array_equal(canonical(g.bonds()), canonical(bonds_of_oracle(o)))
+    assert o.nb > 0
+    g.close()
+
+
 def test_react_once_edge_cases(P):
     # empty system
     d = P.make_desc(0, 10.0)
