@@ -17,7 +17,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libpolyrx.so")
-SOURCES = ["md_kernels.cu", "rx_kernels.cu", "runtime.cu", "noalloc.cu"]
+SOURCES = ["md_kernels.cu", "rx_kernels.cu", "runtime.cu", "noalloc.cu", "dg.cu"]
+# relocatable device code only where a kernel launches device graphs
+RDC = {"dg.cu"}
 HEADERS = [os.path.join(CSRC, "prx_internal.cuh"), os.path.join(ROOT, "include", "polyrx.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -52,7 +54,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def one(src):
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [cc, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *FLAGS, *extra_flags, *(["-rdc=true"] if src in RDC else []), "-c",
+               os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -65,7 +68,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    cmd = [cc, *ARCH, "-shared", "-rdc=true", "-cudart", "static", "-o", tmp, *objs, "-lcudadevrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

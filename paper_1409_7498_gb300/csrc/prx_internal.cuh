@@ -85,6 +85,10 @@ struct Ctl {
   unsigned int n_active;       // eligible A's of the current reaction step
   unsigned int input_err;      // creation: first bad input kind (1 non-finite
                                // position, 2 outside the box, 3 type >= 8)
+  // device-driven runs (dg.cu): steps left in the run, and the device graphs
+  // k_dg_next launches (as cudaGraphExec_t values)
+  unsigned long long steps_left;
+  unsigned long long dg_rebuild, dg_react;
 };
 
 constexpr int MAX_RX = PRX_MAX_REACTIONS;
@@ -377,5 +381,11 @@ void launch_stage_input(const Sys& S, cudaStream_t st, const double* buf, int wh
 // 0 states, 1 types, 2 positions wrapped into the box, 3 velocities.
 void launch_gather_by_id(const Sys& S, cudaStream_t st, int what, void* out);
 int configure_build_kernel(size_t smem_bytes);
+// Device-driven runs (dg.cu): k_dg_arm stores the run's step count and the
+// rebuild and reaction device graphs in the control block; k_dg_next, the
+// last kernel of the step's device graph, tail-launches what follows.
+void launch_dg_arm(const Sys& S, cudaStream_t st, unsigned long long steps,
+                   unsigned long long rebuild, unsigned long long react);
+void launch_dg_next(const Sys& S, cudaStream_t st, unsigned int theta);
 
 }  // namespace prx

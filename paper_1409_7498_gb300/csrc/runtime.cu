@@ -68,6 +68,10 @@ struct prx_system {
   cudaGraphExec_t g_step = nullptr, g_chunk = nullptr, g_react = nullptr;
   cudaGraphExec_t g_chunk1 = nullptr;  // one interval, when g_chunk holds several
   uint32_t chunk_m = 1;                // reaction intervals per g_chunk replay
+  // device graphs of device-driven runs (dg.cu): one step (+ k_dg_next), the
+  // rebuild, the reaction; dg_ok when all three instantiated
+  cudaGraphExec_t dg_step = nullptr, dg_rebuild = nullptr, dg_react = nullptr;
+  bool dg_ok = false;
   bool graphs_valid = false;
   bool profiling = false;
   std::vector<ProfEvent> prof;
@@ -240,6 +244,11 @@ void destroy_graphs(prx_system* s) {
   if (s->g_chunk1) cudaGraphExecDestroy(s->g_chunk1);
   if (s->g_react) cudaGraphExecDestroy(s->g_react);
   s->g_step = s->g_chunk = s->g_chunk1 = s->g_react = nullptr;
+  if (s->dg_step) cudaGraphExecDestroy(s->dg_step);
+  if (s->dg_rebuild) cudaGraphExecDestroy(s->dg_rebuild);
+  if (s->dg_react) cudaGraphExecDestroy(s->dg_react);
+  s->dg_step = s->dg_rebuild = s->dg_react = nullptr;
+  s->dg_ok = false;
   s->graphs_valid = false;
 }
 
@@ -437,9 +446,57 @@ int build_graph(prx_system* sys, int nsteps, bool with_rx, cudaGraphExec_t* out,
   return PRX_OK;
 }
 
+// One device-launchable graph of whatever `body()` launches on the capture
+// stream, uploaded to the device.
+template <class F>
+cudaError_t capture_device_graph(cudaStream_t cap, F body, cudaGraphExec_t* out) {
+  cudaGraph_t g;
+  CE(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  body();
+  CE(cudaStreamEndCapture(cap, &g));
+  const cudaError_t e = cudaGraphInstantiateWithFlags(out, g, cudaGraphInstantiateFlagDeviceLaunch);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return e;
+  }
+  return cudaGraphUpload(*out, cap);
+}
+
+// The device graphs of device-driven runs; on any failure the system keeps
+// the host-replayed graphs (the same kernels).
+void build_device_graphs(prx_system* sys) {
+  const bool fp64 = sys->d.force_precision == PRX_FORCE_FP64;
+  const unsigned theta = sys->has_rx ? (unsigned)sys->rxd.theta : 1u;
+  cudaError_t e = capture_device_graph(sys->cap, [&] {
+    launch_step(sys->S, sys->cap, fp64, 0, 0, 0);
+    launch_dg_next(sys->S, sys->cap, theta);
+  }, &sys->dg_step);
+  if (e == cudaSuccess)
+    e = capture_device_graph(sys->cap, [&] { launch_rebin(sys->S, sys->cap, 0, nullptr, nullptr); },
+                             &sys->dg_rebuild);
+  if (e == cudaSuccess && sys->has_rx)
+    e = capture_device_graph(sys->cap, [&] { launch_rx(sys->S, sys->cap, -1, nullptr, nullptr); },
+                             &sys->dg_react);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sys->cap);
+  sys->dg_ok = e == cudaSuccess;
+  if (!sys->dg_ok) {
+    cudaGetLastError();
+    if (sys->dg_step) cudaGraphExecDestroy(sys->dg_step);
+    if (sys->dg_rebuild) cudaGraphExecDestroy(sys->dg_rebuild);
+    if (sys->dg_react) cudaGraphExecDestroy(sys->dg_react);
+    sys->dg_step = sys->dg_rebuild = sys->dg_react = nullptr;
+  }
+}
+
 int ensure_graphs(prx_system* sys) {
   if (sys->graphs_valid) return PRX_OK;
   destroy_graphs(sys);
+  build_device_graphs(sys);
+  if (sys->dg_ok) {
+    sys->graphs_valid = true;
+    return PRX_OK;
+  }
   int rc;
   if ((rc = build_graph(sys, 1, false, &sys->g_step))) return rc;
   const int m = (int)sys->chunk_m;
@@ -1157,6 +1214,22 @@ int prx_run(prx_system* sys, uint64_t nsteps) {
   }
   int rc = ensure_graphs(sys);
   if (rc) return rc;
+  if (sys->dg_ok) {
+    // one device-driven chain of nsteps steps (with the rebuilds and the
+    // reaction steps it decides on) behind one host launch
+    if (nsteps == 0) return PRX_OK;
+    launch_dg_arm(sys->S, sys->stream, nsteps, (unsigned long long)sys->dg_rebuild,
+                  (unsigned long long)sys->dg_react);
+    CK(cudaGraphLaunch(sys->dg_step, sys->stream));
+    if (sys->has_rx) {
+      const uint64_t th = sys->rxd.theta;
+      sys->graph_rx_launches += (sys->host_step + nsteps) / th - sys->host_step / th;
+    }
+    sys->host_step += nsteps;
+    sys->step_launches += nsteps;
+    sys->other_launches += 1 + nsteps;  // the arm kernel, one k_dg_next per step
+    return PRX_OK;
+  }
   const uint64_t theta = sys->has_rx ? sys->rxd.theta : (uint64_t)kNoRxChunk;
   const uint64_t m = sys->chunk_m;
   while (nsteps > 0) {
