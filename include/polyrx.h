@@ -211,7 +211,13 @@ int prx_set_reactions(prx_system* sys, const prx_reaction_desc* rx, uint32_t n_r
 /* ---- execution --------------------------------------------------------- */
 
 /* Queues nsteps MD steps (with the reaction every Theta steps) on the
- * system's stream and returns without waiting. */
+ * system's stream and returns without waiting.  The run is one device-driven
+ * chain: after each step a kernel on the GPU launches the list rebuild when
+ * a particle moved more than skin/2, the reaction step when it is due, and
+ * the next step (device graph launches); where device graphs are not
+ * available the library replays host-launched CUDA graphs with a
+ * conditional rebuild node after each step instead, with the same kernels
+ * and the same result. */
 int prx_run(prx_system* sys, uint64_t nsteps);
 
 /* Waits for queued work; returns the sticky device status. */
@@ -381,7 +387,8 @@ typedef struct {
   uint32_t step_threads;       /* threads per block of the step kernel: 128, 256 or 512 (0: 256) */
   uint32_t step_blocks_per_sm; /* blocks per SM of its persistent grid (0: as many as fit) */
   uint32_t chunk_intervals;    /* reaction intervals per CUDA-graph replay in prx_run, 1..64
-                                  (0: 1); without a scheme, chunks of 10 steps */
+                                  (0: 1); without a scheme, chunks of 10 steps; used only
+                                  when runs fall back to host-replayed graphs */
   uint32_t step_lanes;         /* lanes per particle of the FP32 step: 1 or 4 (0: 1) */
 } prx_launch_config;
 
