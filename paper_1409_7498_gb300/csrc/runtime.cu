@@ -239,6 +239,9 @@ double max_r_react(const prx_system* sys) {
 }
 
 void destroy_graphs(prx_system* s) {
+  // a device-driven run in flight launches these graphs from the device:
+  // it must have finished before they go
+  if ((s->dg_step || s->dg_rebuild || s->dg_react) && s->stream) cudaStreamSynchronize(s->stream);
   if (s->g_step) cudaGraphExecDestroy(s->g_step);
   if (s->g_chunk) cudaGraphExecDestroy(s->g_chunk);
   if (s->g_chunk1) cudaGraphExecDestroy(s->g_chunk1);
