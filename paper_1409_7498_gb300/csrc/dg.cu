@@ -46,7 +46,48 @@ __global__ void k_dg_next(Ctl* ctl, int has_rx, unsigned int theta) {
   if (!ok) atomicCAS(&ctl->status, 0, PRX_ECUDA);
 }
 
+__global__ void k_dgb_arm(BatchCtl* c, unsigned long long steps, unsigned long long phase,
+                          unsigned long long theta, int any_rx, unsigned long long rebuild,
+                          unsigned long long react) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    c->steps_left = steps;
+    c->phase = phase;
+    c->theta = theta;
+    c->any_rx = any_rx;
+    c->dg_rebuild = rebuild;
+    c->dg_react = react;
+  }
+}
+
+// After a batch step (the last member's epilogue left its decision in
+// rebuild_now): the rebuild of the members that need one, the reaction step
+// when the batch's phase wraps, the next step.
+__global__ void k_dgb_next(BatchCtl* c) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  bool ok = true;
+  if (c->rebuild_now)
+    ok = cudaGraphLaunch((cudaGraphExec_t)c->dg_rebuild, cudaStreamGraphTailLaunch) == cudaSuccess;
+  c->phase = c->theta ? (c->phase + 1ull) % c->theta : 0ull;
+  if (ok && c->any_rx && c->phase == 0ull)
+    ok = cudaGraphLaunch((cudaGraphExec_t)c->dg_react, cudaStreamGraphTailLaunch) == cudaSuccess;
+  if (ok && c->steps_left > 1ull) {
+    c->steps_left -= 1ull;
+    ok = cudaGraphLaunch(cudaGetCurrentGraphExec(), cudaStreamGraphTailLaunch) == cudaSuccess;
+  } else {
+    c->steps_left = 0ull;
+  }
+  if (!ok) c->dg_err = 1;
+}
+
 }  // namespace
+
+void launch_dgb_arm(BatchCtl* c, cudaStream_t st, unsigned long long steps, unsigned long long phase,
+                    unsigned long long theta, int any_rx, unsigned long long rebuild,
+                    unsigned long long react) {
+  k_dgb_arm<<<1, 32, 0, st>>>(c, steps, phase, theta, any_rx, rebuild, react);
+}
+
+void launch_dgb_next(BatchCtl* c, cudaStream_t st) { k_dgb_next<<<1, 32, 0, st>>>(c); }
 
 void launch_dg_arm(const Sys& S, cudaStream_t st, unsigned long long steps,
                    unsigned long long rebuild, unsigned long long react) {

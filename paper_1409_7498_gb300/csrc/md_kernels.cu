@@ -160,6 +160,7 @@ __device__ __forceinline__ void step_epilogue(const Sys& S, int ph, unsigned lon
         S.batch->done_step = 0u;
         const int flag = atomicExch(&S.batch->any_rebuild, 0);
         if (flag) S.batch->rebuilds += 1ull;
+        S.batch->rebuild_now = flag;  // for a device-driven run (dg.cu)
         if (use_cond) cudaGraphSetConditional(cond, flag ? 1u : 0u);
       }
     }

@@ -149,6 +149,14 @@ struct BatchCtl {
   int any_rebuild;          // some member needs a rebuild after this step
   unsigned int done_step;   // members whose step finished (last-member detection)
   unsigned long long rebuilds;  // steps after which the rebuild pipeline ran
+  // device-driven batch runs (dg.cu): the last step's rebuild decision, the
+  // steps left, the reaction phase (steps mod theta) and the device graphs
+  int rebuild_now;
+  int any_rx;
+  int dg_err;                   // a device-side graph launch failed
+  int pad_;
+  unsigned long long steps_left, phase, theta;
+  unsigned long long dg_rebuild, dg_react;
 };
 
 struct Sys {
@@ -387,5 +395,10 @@ int configure_build_kernel(size_t smem_bytes);
 void launch_dg_arm(const Sys& S, cudaStream_t st, unsigned long long steps,
                    unsigned long long rebuild, unsigned long long react);
 void launch_dg_next(const Sys& S, cudaStream_t st, unsigned int theta);
+// The same for a batch: k_dgb_next follows the batch's step kernels.
+void launch_dgb_arm(BatchCtl* c, cudaStream_t st, unsigned long long steps, unsigned long long phase,
+                    unsigned long long theta, int any_rx, unsigned long long rebuild,
+                    unsigned long long react);
+void launch_dgb_next(BatchCtl* c, cudaStream_t st);
 
 }  // namespace prx

@@ -105,6 +105,9 @@ struct prx_batch {
   uint32_t n_active = 0;
   bool any_rx = false;
   cudaGraphExec_t g_step = nullptr, g_chunk = nullptr, g_react = nullptr;
+  // device graphs of device-driven batch runs (dg.cu); dg_ok when all built
+  cudaGraphExec_t dg_step = nullptr, dg_rebuild = nullptr, dg_react = nullptr;
+  bool dg_ok = false;
   bool valid = false;
   std::string err;
   // admission (prx_batch_admit / step_epoch / poll)
@@ -878,10 +881,17 @@ int bfail(prx_batch* b, int code, const std::string& msg) {
   } while (0)
 
 void batch_destroy_graphs(prx_batch* b) {
+  // a device-driven run in flight launches its graphs from the device
+  if ((b->dg_step || b->dg_rebuild || b->dg_react) && b->stream) cudaStreamSynchronize(b->stream);
   if (b->g_step) cudaGraphExecDestroy(b->g_step);
   if (b->g_chunk) cudaGraphExecDestroy(b->g_chunk);
   if (b->g_react) cudaGraphExecDestroy(b->g_react);
   b->g_step = b->g_chunk = b->g_react = nullptr;
+  if (b->dg_step) cudaGraphExecDestroy(b->dg_step);
+  if (b->dg_rebuild) cudaGraphExecDestroy(b->dg_rebuild);
+  if (b->dg_react) cudaGraphExecDestroy(b->dg_react);
+  b->dg_step = b->dg_rebuild = b->dg_react = nullptr;
+  b->dg_ok = false;
 }
 
 // Member table, block maps and graphs of a batch after its membership
@@ -1007,9 +1017,29 @@ int batch_prepare(prx_batch* b) {
   auto step = [&](cudaGraphConditionalHandle h) { launch_batch_step(L, b->cap, h, 1); };
   auto rebuild = [&] { launch_batch_rebuild(L, b->cap); };
   auto rx = [&] { launch_batch_rx(L, b->cap); };
-  CKB(capture_graph(b->cap, 1, false, step, rebuild, rx, &b->g_step));
-  CKB(capture_graph(b->cap, chunk, b->any_rx, step, rebuild, rx, &b->g_chunk));
-  if (b->any_rx) CKB(capture_graph(b->cap, 0, true, step, rebuild, rx, &b->g_react));
+  // device-driven runs first; the host-replayed graphs only if those fail
+  {
+    cudaError_t e = capture_device_graph(b->cap, [&] {
+      launch_batch_step(L, b->cap, 0, 0);
+      launch_dgb_next(b->bctl, b->cap);
+    }, &b->dg_step);
+    if (e == cudaSuccess) e = capture_device_graph(b->cap, rebuild, &b->dg_rebuild);
+    if (e == cudaSuccess && b->any_rx) e = capture_device_graph(b->cap, rx, &b->dg_react);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap);
+    b->dg_ok = e == cudaSuccess;
+    if (!b->dg_ok) {
+      cudaGetLastError();
+      if (b->dg_step) cudaGraphExecDestroy(b->dg_step);
+      if (b->dg_rebuild) cudaGraphExecDestroy(b->dg_rebuild);
+      if (b->dg_react) cudaGraphExecDestroy(b->dg_react);
+      b->dg_step = b->dg_rebuild = b->dg_react = nullptr;
+    }
+  }
+  if (!b->dg_ok) {
+    CKB(capture_graph(b->cap, 1, false, step, rebuild, rx, &b->g_step));
+    CKB(capture_graph(b->cap, chunk, b->any_rx, step, rebuild, rx, &b->g_chunk));
+    if (b->any_rx) CKB(capture_graph(b->cap, 0, true, step, rebuild, rx, &b->g_react));
+  }
   b->valid = true;
   return PRX_OK;
 }
@@ -2173,6 +2203,18 @@ int batch_launch(prx_batch* b, uint64_t nsteps) {
   int rc = batch_prepare(b);
   if (rc) return rc;
   const uint64_t total = nsteps;
+  if (b->n_active && b->dg_ok && nsteps) {
+    // one device-driven chain (dg.cu) behind one host launch
+    const uint64_t theta = b->any_rx ? b->theta : 0;
+    const uint64_t ph = b->any_rx ? b->phase : 0;
+    launch_dgb_arm(b->bctl, b->stream, nsteps, ph, theta, b->any_rx ? 1 : 0,
+                   (unsigned long long)b->dg_rebuild, (unsigned long long)b->dg_react);
+    const cudaError_t e = cudaGraphLaunch(b->dg_step, b->stream);
+    if (e != cudaSuccess) return bfail(b, PRX_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    b->graph_launches++;
+    if (b->any_rx) b->rx_runs += (ph + nsteps) / theta;
+    nsteps = 0;
+  }
   if (b->n_active) {
     const uint64_t theta = b->any_rx ? b->theta : (uint64_t)kNoRxChunk;
     uint64_t ph = b->any_rx ? b->phase : 0;
@@ -2198,7 +2240,10 @@ int batch_launch(prx_batch* b, uint64_t nsteps) {
   }
   b->steps += total;
   if (b->theta) b->phase = (b->phase + total) % b->theta;
-  if (b->n_active) b->kernel_steps += total * (uint64_t)b->n_step_variants;
+  if (b->n_active) {
+    b->kernel_steps += total * (uint64_t)b->n_step_variants;
+    if (b->dg_ok && total) b->kernel_steps += total + 1;  // k_dgb_next per step, the arm kernel
+  }
   for (prx_system* m : b->members) m->host_step += total;
   return PRX_OK;
 }
@@ -2345,8 +2390,12 @@ int prx_batch_sync(prx_batch* b, int32_t* failed) {
   for (prx_system* m : b->members)
     if (cudaMemcpyAsync(m->ctl_host, m->S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
       return bfail(b, PRX_ECUDA, "reading a member's control block failed");
+  if (b->dg_ok &&
+      cudaMemcpyAsync(b->bctl_host, b->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+    return bfail(b, PRX_ECUDA, "reading the batch's control block failed");
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bfail(b, PRX_ECUDA, std::string("batch stream: ") + cudaGetErrorString(e));
+  if (b->dg_ok && b->bctl_host->dg_err) return bfail(b, PRX_ECUDA, "a device-side graph launch failed");
   for (size_t q = 0; q < b->members.size(); ++q) {
     const int st = b->members[q]->ctl_host->status;
     if (st) {

@@ -88,8 +88,11 @@ def test_batch_members_match_alone_bit_for_bit(P):
     assert st["members"] == len(SPECS) and st["active"] == len(SPECS)
     assert st["particles"] == sum(s["n"] for s in SPECS)
     assert st["steps"] == sum(chunks) and st["reactions"] == sum(chunks) // 10
-    # one step kernel per step, ten per rebuild (a plan and nine), five per reaction step
-    assert st["kernel_launches"] == st["steps"] + 10 * st["rebuilds"] + 5 * st["reactions"]
+    # one step kernel per step, ten per rebuild (a plan and nine), five per
+    # reaction step; device-driven runs add the one-block kernel after each
+    # step and one arming kernel per run
+    base = st["steps"] + 10 * st["rebuilds"] + 5 * st["reactions"]
+    assert st["kernel_launches"] - base in (0, st["steps"] + len(chunks)), (st, base)
     # a rebuild of the batch happens at the union of the members' rebuild steps
     assert max(r["rebins"] for r in ref) - 1 <= st["rebuilds"] <= sum(r["rebins"] - 1 for r in ref)
 
